@@ -1,0 +1,717 @@
+/* CPU oracle: one unsplit corner-transport-upwind (CTU) PPM Godunov step for
+ * the gamma-law Euler equations on a ghost-zoned box.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * FP64 statement of the scheme that the CUDA path is checked against.  Only
+ * the test suite, the smoke check and the CPU-baseline leg of the benchmark
+ * load it; the product library never does, and the two share no code.
+ *
+ * The paper (Sec. 3.2, "Castro") names the method only: an unsplit piecewise
+ * parabolic method for compressible hydrodynamics, with a general equation of
+ * state (here gamma-law), conservative source terms (here constant gravity),
+ * run box by box on ghost-zoned patches handed to a kernel by an iterator
+ * (Sec. 3 intro; Sec. 4, GPU port paragraph).  Every step below is the
+ * textbook method it names:
+ *   - reconstruction and limiter: Colella & Woodward 1984 (CW84) eqs. 1.6-1.10
+ *   - flattening: CW84 appendix A (omega1 = 0.75, omega2 = 10, epsilon = 0.33)
+ *   - characteristic tracing: reference-state tracing (Miller & Colella 2002)
+ *   - transverse corrections: Colella 1990 (2-D), Saltzman 1994 (3-D, 12 solves)
+ *   - Riemann solver: HLLC (Toro, Spruce & Speares 1994), Davis wave speeds
+ *   - update: conservative flux difference + time-centred gravity source
+ * Where the scheme leaves a choice open, the choice made is stated at the
+ * point of use.  Arithmetic is FP64; compiled with -ffp-contract=off so that
+ * no multiply-add is fused behind the reader's back.
+ *
+ * Layout: a box is 5 conserved fields (rho, rho*u, rho*v, rho*w, rho*E),
+ * component-major, each a (gz, gy, gx) array with x fastest, over the grown
+ * box: interior n[a] zones plus ng = 4 ghost zones on each side of every
+ * active axis (z has no ghosts in 2-D, where n[2] = 1).
+ *
+ * Built twice: the normal build (real = double) and the counting build
+ * (-DORACLE_COUNT_FLOPS, real = counted) that tallies the arithmetic.
+ */
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#ifdef ORACLE_COUNT_FLOPS
+#include "flopcount.h"
+typedef counted real;
+op_tally g_tally;
+#else
+typedef double real;
+using std::isfinite;
+using std::sqrt;
+using std::fabs;
+using std::copysign;
+#endif
+
+#include "oracle.h"
+
+namespace {
+
+const int NG = 4;          /* ghost zones per side: the CTU-PPM stencil reaches 4 zones */
+const int NV = 5;          /* conserved / primitive variables */
+/* primitive fields on the grown box: rho, u, v, w, p, c and the zone's
+ * eigenvector coefficients rho/c, c/rho, 1/c^2 (shared by all directions) */
+enum { QRHO = 0, QU = 1, QV = 2, QW = 3, QP = 4, QC = 5, QRC = 6, QCR = 7, QIC2 = 8, NQ = 9 };
+
+/* CW84 appendix A flattening constants */
+const double FLAT_OMEGA1 = 0.75, FLAT_OMEGA2 = 10.0, FLAT_EPS = 0.33;
+const double SIXTH = 1.0 / 6.0, TWOTHIRDS = 2.0 / 3.0, THIRD = 1.0 / 3.0;
+
+/* min / max written as explicit comparisons (ties return the first argument) */
+inline real rmin(real a, real b) { return (b < a) ? b : a; }
+inline real rmax(real a, real b) { return (a < b) ? b : a; }
+
+struct Grid {
+  int dim, n[3], gx, gy, gz, ngz;
+  long sy, sz, sc, str[3];
+  Grid(const oracle_params& P) {
+    dim = P.dim;
+    for (int a = 0; a < 3; ++a) n[a] = P.n[a];
+    ngz = (dim == 3) ? NG : 0;
+    gx = n[0] + 2 * NG; gy = n[1] + 2 * NG; gz = n[2] + 2 * ngz;
+    sy = gx; sz = (long)gx * gy; sc = sz * gz;
+    str[0] = 1; str[1] = sy; str[2] = sz;
+  }
+  long id(int i, int j, int k) const { return (long)(k + ngz) * sz + (long)(j + NG) * sy + (i + NG); }
+};
+
+/* ---- Step 1: ghost-zone fill (outflow / reflect / periodic / prefilled) ---- */
+void fill_ghosts(real* W, const Grid& g, const oracle_params& P) {
+  for (int a = 0; a < g.dim; ++a) {
+    /* fill axis a over the interior range of later axes and the full grown
+     * range of earlier ones, so edges and corners are a product of the
+     * per-axis maps */
+    int lo[3], hi[3];
+    for (int b = 0; b < 3; ++b) {
+      int gb = (b == 2) ? g.ngz : NG;
+      if (b < a) { lo[b] = -gb; hi[b] = g.n[b] + gb; }
+      else { lo[b] = 0; hi[b] = g.n[b]; }
+    }
+    for (int side = 0; side < 2; ++side) {
+      int bc = P.bc[a][side];
+      if (bc == ORACLE_BC_PREFILLED) continue;
+      for (int m = 1; m <= NG; ++m) {
+        int dst = side == 0 ? -m : g.n[a] - 1 + m, src;
+        if (bc == ORACLE_BC_OUTFLOW) src = side == 0 ? 0 : g.n[a] - 1;
+        else if (bc == ORACLE_BC_REFLECT) src = side == 0 ? m - 1 : g.n[a] - m;
+        else src = side == 0 ? g.n[a] - m : m - 1; /* periodic */
+        int l0[3] = {lo[0], lo[1], lo[2]}, h0[3] = {hi[0], hi[1], hi[2]};
+        l0[a] = dst; h0[a] = dst + 1;
+        for (int k = l0[2]; k < h0[2]; ++k)
+          for (int j = l0[1]; j < h0[1]; ++j)
+            for (int i = l0[0]; i < h0[0]; ++i) {
+              int s[3] = {i, j, k};
+              s[a] = src;
+              long di = g.id(i, j, k), si = g.id(s[0], s[1], s[2]);
+              for (int c = 0; c < NV; ++c) {
+                real v = W[c * g.sc + si];
+                if (bc == ORACLE_BC_REFLECT && c == 1 + a) v = -v; /* mirror the normal momentum */
+                W[c * g.sc + di] = v;
+              }
+            }
+      }
+    }
+  }
+}
+
+/* ---- Step 2: conserved -> primitive with density / pressure floors (gamma-law EOS) ----
+ * q = (rho, u, v, w, p); flags a non-physical input (rho <= 0, p <= 0, non-finite). */
+void cons_to_prim(const real U[5], const oracle_params& P, real q[5], real* inv_out, int* bad) {
+  real rho = U[0];
+  if (bad && !(rho > 0.0 && isfinite(rho))) *bad = 1;
+  rho = rmax(rho, real(P.small_dens));
+  real inv = 1.0 / rho;
+  real u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
+  real ke = 0.5 * rho * ((u * u + v * v) + w * w);
+  real p = (P.gamma - 1.0) * (U[4] - ke);
+  if (bad && !(p > 0.0 && isfinite(p) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]))) *bad = 1;
+  p = rmax(p, real(P.small_pres));
+  q[0] = rho; q[1] = u; q[2] = v; q[3] = w; q[4] = p;
+  if (inv_out) *inv_out = inv;
+}
+
+/* sound speed c = sqrt(gamma p / rho), given inv = 1/rho */
+real sound_speed(real p, real inv, double gamma) { return sqrt(gamma * p * inv); }
+
+/* per-step constants */
+struct Consts {
+  double gamma;
+  real gm1inv; /* 1/(gamma - 1) */
+};
+
+/* primitive -> conserved, rho*E = p/(gamma-1) + rho |u|^2 / 2 */
+void prim_to_cons(const real q[5], const Consts& K, real U[5]) {
+  U[0] = q[0];
+  U[1] = q[0] * q[1]; U[2] = q[0] * q[2]; U[3] = q[0] * q[3];
+  U[4] = q[4] * K.gm1inv + 0.5 * q[0] * ((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
+}
+
+/* A face state as the Riemann solver consumes it: primitive variables, the
+ * total energy density rho*E and 1/rho. */
+enum { S_RHO = 0, S_P = 4, S_E = 5, S_INV = 6, NS = 7 };
+
+/* from a traced primitive state */
+void state_from_prim(const real q[5], const Consts& K, real s[NS]) {
+  for (int c = 0; c < 5; ++c) s[c] = q[c];
+  s[S_E] = q[4] * K.gm1inv + 0.5 * q[0] * ((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
+  s[S_INV] = 1.0 / q[0];
+}
+
+/* from a transversely corrected conserved state, with floors */
+void state_from_cons(const real U[5], const oracle_params& P, real s[NS]) {
+  real rho = rmax(U[0], real(P.small_dens));
+  real inv = 1.0 / rho;
+  real u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
+  real ke = 0.5 * rho * ((u * u + v * v) + w * w);
+  real p = (P.gamma - 1.0) * (U[4] - ke);
+  p = rmax(p, real(P.small_pres));
+  s[0] = rho; s[1] = u; s[2] = v; s[3] = w; s[4] = p;
+  s[S_E] = U[4];
+  s[S_INV] = inv;
+}
+
+/* ---- Step 4: CW84 flattening along one line ----
+ * a line holds 7 values at offsets -3..3 about the zone (index 3): flattening
+ * reaches 3 zones, the reconstruction 2.
+ * chi is the fraction of the reconstruction that is KEPT (1 = unflattened). */
+real flat_tilde(const real* p, const real* un, int m, double small_pres) {
+  real dp1 = p[m + 1] - p[m - 1];
+  real dp2 = p[m + 2] - p[m - 2];
+  /* shock detector: compression and a pressure jump larger than epsilon */
+  if (un[m - 1] - un[m + 1] > 0.0 && fabs(dp1) > FLAT_EPS * rmin(p[m + 1], p[m - 1])) {
+    real z = fabs(dp1) / rmax(fabs(dp2), real(small_pres));
+    real f = rmax(real(0.0), rmin(real(1.0), FLAT_OMEGA2 * (z - FLAT_OMEGA1)));
+    return 1.0 - f;
+  }
+  return 1.0;
+}
+real flat_coef(const real* p, const real* un, double small_pres) {
+  real dp1 = p[4] - p[2];
+  int s = (dp1 < 0.0) ? 1 : -1; /* the neighbour on the high-pressure side */
+  return rmin(flat_tilde(p, un, 3, small_pres), flat_tilde(p, un, 3 + s, small_pres));
+}
+
+/* ---- Step 5: PPM reconstruction (CW84 eqs. 1.6-1.10) ---- */
+/* monotonised centred slope delta_m a (CW84 eq. 1.8): zero unless a is
+ * strictly monotone through the zone */
+real mc_slope(const real* a, int m) {
+  real dl = a[m] - a[m - 1], dr = a[m + 1] - a[m];
+  bool mono = (dl > 0.0 && dr > 0.0) || (dl < 0.0 && dr < 0.0);
+  if (!mono) return 0.0;
+  real da = 0.5 * (a[m + 1] - a[m - 1]);
+  real lim = rmin(fabs(da), rmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
+  return copysign(lim, da);
+}
+/* interface value a_{m+1/2} (CW84 eq. 1.6 on a uniform grid) */
+real face_value(const real* a, int m) {
+  return 0.5 * (a[m] + a[m + 1]) - SIXTH * (mc_slope(a, m + 1) - mc_slope(a, m));
+}
+/* limited, flattened parabola of the zone at index 3: edge values am, ap and a6 */
+void ppm_parabola(const real* a, real chi, real* am, real* ap, real* a6) {
+  real ai = a[3];
+  real aP = face_value(a, 3), aM = face_value(a, 2);
+  /* CW84 eq. 1.10: local extremum -> constant; overshooting parabola -> steepen
+   * the opposite edge.  The two tests (a+-a)(a-a-) <= 0 and D*M > D^2/6 are
+   * written as sign tests, which are their exact-arithmetic meaning. */
+  bool same = ((aP - ai) > 0.0 && (ai - aM) > 0.0) || ((aP - ai) < 0.0 && (ai - aM) < 0.0);
+  if (!same) {
+    aP = ai; aM = ai;
+  } else {
+    real D = aP - aM, M = ai - 0.5 * (aM + aP);
+    real up = M - SIXTH * D; /* D*M > D^2/6   <=>  D*(M - D/6) > 0 */
+    real dn = M + SIXTH * D; /* -D^2/6 > D*M  <=>  D*(M + D/6) < 0 */
+    if ((D > 0.0 && up > 0.0) || (D < 0.0 && up < 0.0)) aM = 3.0 * ai - 2.0 * aP;
+    else if ((D > 0.0 && dn < 0.0) || (D < 0.0 && dn > 0.0)) aP = 3.0 * ai - 2.0 * aM;
+  }
+  /* flattening blends the edges toward the zone average */
+  aP = chi * aP + (1.0 - chi) * ai;
+  aM = chi * aM + (1.0 - chi) * ai;
+  *am = aM; *ap = aP; *a6 = 6.0 * (ai - 0.5 * (aM + aP));
+}
+/* averages of the parabola over the domains swept by a wave of Courant number
+ * sigma toward the high (I+) and low (I-) face (CW84 eqs. 1.12) */
+real integ_plus(real am, real ap, real a6, real s) {
+  return ap - 0.5 * s * ((ap - am) - (1.0 - TWOTHIRDS * s) * a6);
+}
+real integ_minus(real am, real ap, real a6, real s) {
+  return am + 0.5 * s * ((ap - am) + (1.0 - TWOTHIRDS * s) * a6);
+}
+
+/* ---- Steps 4-6 for one zone and direction d: flatten, reconstruct, trace ----
+ * Q holds the 6 primitive fields (rho,u,v,w,p,c) on the grown box.
+ * Outputs the primitive states at the zone's low face (qm) and high face (qp)
+ * at t^{n+1/2}, components in absolute order (rho, u, v, w, p). */
+void trace_zone(const std::vector<real>* Q, long id, long st, int d, const oracle_params& P,
+                real dtdx, real dt, real qm[5], real qp[5]) {
+  const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+  const int vmap[5] = {QRHO, QU + d, QU + t1, QU + t2, QP}; /* rho, un, ut1, ut2, p */
+  real line[5][7];
+  for (int v = 0; v < 5; ++v)
+    for (int m = 0; m < 7; ++m) line[v][m] = Q[vmap[v]][id + (m - 3) * st];
+  real chi = P.flatten ? flat_coef(line[4], line[1], P.small_pres) : real(1.0);
+  real am[5], ap[5], a6[5];
+  for (int v = 0; v < 5; ++v) ppm_parabola(line[v], chi, &am[v], &ap[v], &a6[v]);
+
+  real un = line[1][3], c = Q[QC][id];
+  /* eigenvectors of the primitive (rho, un, p) system at the zone state:
+   *   r- = (1, -c/rho, c^2), r0 = (1, 0, 0), r+ = (1, c/rho, c^2)
+   *   l- = (0, -rho/(2c), 1/(2c^2)), l0 = (1, 0, -1/c^2), l+ = (0, rho/(2c), 1/(2c^2)) */
+  real rho_c = Q[QRC][id], c_rho = Q[QCR][id], inv_c2 = Q[QIC2][id], c2 = c * c;
+  real lu = 0.5 * rho_c, lp = 0.5 * inv_c2;
+  real lam[3] = {un - c, un, un + c};
+  real sig[3];
+  for (int w = 0; w < 3; ++w) sig[w] = fabs(lam[w]) * dtdx;
+
+  for (int side = 0; side < 2; ++side) {
+    /* side 1: high face, waves moving right (lam > 0) reach it, averages I+;
+     * side 0: low face, waves moving left (lam < 0), averages I- */
+    bool reach[3];
+    for (int w = 0; w < 3; ++w) reach[w] = side ? (lam[w] > 0.0) : (lam[w] < 0.0);
+    int fast = side ? 2 : 0; /* fastest wave toward that face gives the reference state */
+    real I[3][5];
+    for (int w = 0; w < 3; ++w)
+      for (int v = 0; v < 5; ++v)
+        I[w][v] = side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
+    real ref[5];
+    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I[fast][v] : line[v][3];
+    /* wave strengths beta = l . (ref - I(sigma_nu)) of the waves that reach the face */
+    real bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
+    if (reach[0]) bm = -lu * (ref[1] - I[0][1]) + lp * (ref[4] - I[0][4]);
+    if (reach[1]) {
+      b0 = (ref[0] - I[1][0]) - inv_c2 * (ref[4] - I[1][4]);
+      bt1 = ref[2] - I[1][2];
+      bt2 = ref[3] - I[1][3];
+    }
+    if (reach[2]) bp = lu * (ref[1] - I[2][1]) + lp * (ref[4] - I[2][4]);
+    /* edge state = ref - sum beta_nu r_nu */
+    real s_rho = ref[0] - ((bm + b0) + bp);
+    real s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
+    real s_p = ref[4] - (bm * c2 + bp * c2);
+    real s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
+    /* half-step gravity on every velocity component, then floors */
+    real hdt = 0.5 * dt;
+    s_un = s_un + hdt * P.grav[d];
+    s_t1 = s_t1 + hdt * P.grav[t1];
+    s_t2 = s_t2 + hdt * P.grav[t2];
+    s_rho = rmax(s_rho, real(P.small_dens));
+    s_p = rmax(s_p, real(P.small_pres));
+    real* out = side ? qp : qm;
+    out[0] = s_rho; out[1 + d] = s_un; out[1 + t1] = s_t1; out[1 + t2] = s_t2; out[4] = s_p;
+  }
+}
+
+/* ---- Step 7: HLLC flux in direction d (Toro, Spruce & Speares 1994) ----
+ * sL, sR: face states (rho, u, v, w, p, rho*E, 1/rho) left and right of the face. */
+void hllc(const real sL[NS], const real sR[NS], int d, double gamma, real F[5]) {
+  real rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
+  real rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
+  real cl = sound_speed(pl, sL[S_INV], gamma), cr = sound_speed(pr, sR[S_INV], gamma);
+  /* Davis wave-speed estimates */
+  real sl = rmin(ul - cl, ur - cr);
+  real sr = rmax(ul + cl, ur + cr);
+  real ml = rl * (sl - ul), mr = rr * (sr - ur); /* mass fluxes through the outer waves */
+  real sstar = ((pr - pl) + ml * ul - mr * ur) / (ml - mr);
+  /* select the region containing x/t = 0, tested in this order:
+   * 0 <= sL -> L;  0 <= S* -> L*;  0 < sR -> R*;  else R */
+  int region = (sl >= 0.0) ? 0 : (sstar >= 0.0) ? 1 : (sr > 0.0) ? 2 : 3;
+  bool left = region <= 1;
+  const real* s = left ? sL : sR;
+  real rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];
+  /* physical flux of the chosen side */
+  real mass = rho * un;
+  real Fk[5];
+  Fk[0] = mass;
+  for (int k = 0; k < 3; ++k) Fk[1 + k] = (k == d) ? mass * un + p : mass * s[1 + k];
+  Fk[4] = un * (E + p);
+  if (region == 0 || region == 3) {
+    for (int c = 0; c < 5; ++c) F[c] = Fk[c];
+    return;
+  }
+  real sk = left ? sl : sr, mk = left ? ml : mr;
+  real Uk[5] = {rho, rho * s[1], rho * s[2], rho * s[3], E};
+  /* star state U*_K = f [1, S*, u_t, E/rho + (S* - u)(S* + p/(rho (S_K - u)))],
+   * f = rho (S_K - u)/(S_K - S*).  With r = 1/(S_K - S*), f p/(rho(S_K-u)) = p r,
+   * so the energy entry is f E/rho + (S* - u)(f S* + p r): one division fewer. */
+  real r = 1.0 / (sk - sstar);
+  real f = mk * r;
+  real Us[5];
+  Us[0] = f;
+  for (int k = 0; k < 3; ++k) Us[1 + k] = (k == d) ? f * sstar : f * s[1 + k];
+  Us[4] = f * (E * s[S_INV]) + (sstar - un) * (f * sstar + p * r);
+  for (int c = 0; c < 5; ++c) F[c] = Fk[c] + sk * (Us[c] - Uk[c]);
+}
+
+/* ---- Step 8 helper: transverse correction of a traced primitive state ----
+ * U(q) - coef_a (Fa_hi - Fa_lo) [- coef_b (Fb_hi - Fb_lo)], back to primitive with floors. */
+void correct_state(const real q[5], const oracle_params& P, const Consts& K, real ca, const real* Fa_hi,
+                   const real* Fa_lo, real cb, const real* Fb_hi, const real* Fb_lo, real out[NS]) {
+  real U[5];
+  prim_to_cons(q, K, U);
+  for (int c = 0; c < 5; ++c) {
+    U[c] = U[c] - ca * (Fa_hi[c] - Fa_lo[c]);
+    if (Fb_hi) U[c] = U[c] - cb * (Fb_hi[c] - Fb_lo[c]);
+  }
+  state_from_cons(U, P, out);
+}
+
+struct Fields {
+  /* 5-component arrays on the grown box */
+  std::vector<real> a;
+  long sc;
+  void init(long sc_) { sc = sc_; a.assign(5 * sc_, real(0.0)); }
+  void get(long id, real v[5]) const { for (int c = 0; c < 5; ++c) v[c] = a[c * sc + id]; }
+  void put(long id, const real v[5]) { for (int c = 0; c < 5; ++c) a[c * sc + id] = v[c]; }
+};
+
+bool valid_params(const oracle_params* P) {
+  if (!P || (P->dim != 2 && P->dim != 3)) return false;
+  for (int a = 0; a < 3; ++a) if (P->n[a] < 1) return false;
+  if (P->dim == 2 && P->n[2] != 1) return false;
+  for (int a = 0; a < P->dim; ++a) {
+    if (!(P->dx[a] > 0.0)) return false;
+    for (int s = 0; s < 2; ++s) if (P->bc[a][s] < 0 || P->bc[a][s] > 3) return false;
+    if ((P->bc[a][0] == ORACLE_BC_PERIODIC) != (P->bc[a][1] == ORACLE_BC_PERIODIC)) return false;
+    if (P->bc[a][0] != ORACLE_BC_PREFILLED && P->n[a] < NG) return false; /* a ghost layer is a copy of interior zones */
+  }
+  return P->gamma > 1.0;
+}
+
+} /* namespace */
+
+extern "C" {
+
+long long oracle_grown_size(const oracle_params* P) {
+  if (!valid_params(P)) return -1;
+  Grid g(*P);
+  return g.sc;
+}
+
+int oracle_fill_ghosts(double* U, const oracle_params* P) {
+  if (!valid_params(P)) return ORACLE_EINVAL;
+  Grid g(*P);
+  std::vector<real> W(U, U + 5 * g.sc);
+  fill_ghosts(W.data(), g, *P);
+  for (long i = 0; i < 5 * g.sc; ++i) U[i] = double(W[i]);
+  return ORACLE_OK;
+}
+
+/* CFL time step from the interior of U: cfl * min over zones and active
+ * directions of dx_d / (|u_d| + c).  (Sec. 3.1 notes that a compressible code's
+ * step is limited by the sound speed.) */
+int oracle_dt(const double* U, const oracle_params* P, double* dt_out) {
+  if (!valid_params(P) || !dt_out) return ORACLE_EINVAL;
+  Grid g(*P);
+  int bad = 0;
+  std::vector<double> kmin(g.n[2], HUGE_VAL);
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for reduction(| : bad)
+#endif
+  for (int k = 0; k < g.n[2]; ++k) {
+    int kbad = 0;
+    real m = HUGE_VAL;
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        long id = g.id(i, j, k);
+        real u[5], q[5];
+        for (int c = 0; c < 5; ++c) u[c] = U[c * g.sc + id];
+        real inv;
+        cons_to_prim(u, *P, q, &inv, &kbad);
+        real c = sound_speed(q[4], inv, P->gamma);
+        for (int d = 0; d < g.dim; ++d) m = rmin(m, P->dx[d] / (fabs(q[1 + d]) + c));
+      }
+    kmin[k] = double(m);
+    bad |= kbad;
+  }
+  double m = HUGE_VAL;
+  for (int k = 0; k < g.n[2]; ++k) m = kmin[k] < m ? kmin[k] : m;
+  *dt_out = P->cfl * m;
+  return bad ? ORACLE_EBADSTATE : ORACLE_OK;
+}
+
+int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double dt, oracle_debug* dbg) {
+  if (!valid_params(P) || !Uin || !Uout || !(dt > 0.0)) return ORACLE_EINVAL;
+  const Grid g(*P);
+  const int dim = g.dim;
+  const long N = g.sc;
+  int bad = 0;
+  Consts K;
+  K.gamma = P->gamma;
+  K.gm1inv = 1.0 / (P->gamma - 1.0);
+
+  /* Step 1: working copy with ghost zones filled */
+  std::vector<real> W(Uin, Uin + 5 * N);
+  fill_ghosts(W.data(), g, *P);
+
+  /* Step 2: primitive variables and sound speed on the whole grown box */
+  std::vector<real> Q[NQ];
+  for (int v = 0; v < NQ; ++v) Q[v].assign(N, real(0.0));
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for reduction(| : bad)
+#endif
+  for (long id = 0; id < N; ++id) {
+    real u[5], q[5];
+    for (int c = 0; c < 5; ++c) u[c] = W[c * N + id];
+    int zb = 0;
+    real inv;
+    cons_to_prim(u, *P, q, &inv, &zb);
+    bad |= zb;
+    for (int v = 0; v < 5; ++v) Q[v][id] = q[v];
+    real c = sound_speed(q[4], inv, P->gamma);
+    Q[QC][id] = c;
+    Q[QRC][id] = q[0] / c;
+    Q[QCR][id] = c / q[0];
+    Q[QIC2][id] = 1.0 / (c * c);
+  }
+
+  real dtdx[3];
+  for (int a = 0; a < 3; ++a) dtdx[a] = (a < dim) ? dt / P->dx[a] : 0.0;
+  const int kz0 = (dim == 3) ? -1 : 0, kz1 = (dim == 3) ? g.n[2] : 0; /* the [-1, n] range in z, 3-D only */
+
+  /* Steps 4-6: traced states of every zone in [-1, n] on all active axes */
+  Fields TM[3], TP[3];
+  for (int d = 0; d < dim; ++d) {
+    TM[d].init(N); TP[d].init(N);
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2)
+#endif
+    for (int k = kz0; k <= kz1; ++k)
+      for (int j = -1; j <= g.n[1]; ++j)
+        for (int i = -1; i <= g.n[0]; ++i) {
+          long id = g.id(i, j, k);
+          real qm[5], qp[5];
+          trace_zone(Q, id, g.str[d], d, *P, dtdx[d], dt, qm, qp);
+          TM[d].put(id, qm); TP[d].put(id, qp);
+        }
+  }
+
+  /* Step 7a: first Riemann solves on d-faces f in [0, n_d], transverse range [-1, n].
+   * Face f (between zones f-1 and f) is stored at zone index f. */
+  Fields F1[3];
+  for (int d = 0; d < dim; ++d) {
+    F1[d].init(N);
+    int lo[3] = {-1, -1, kz0}, hi[3] = {g.n[0], g.n[1], kz1};
+    lo[d] = 0; hi[d] = g.n[d];
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2)
+#endif
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          long id = g.id(i, j, k);
+          real qL[5], qR[5], sL[NS], sR[NS], F[5];
+          TP[d].get(id - g.str[d], qL);
+          TM[d].get(id, qR);
+          state_from_prim(qL, K, sL);
+          state_from_prim(qR, K, sR);
+          hllc(sL, sR, d, P->gamma, F);
+          F1[d].put(id, F);
+        }
+  }
+
+  /* Step 8 (3-D only): intermediate fluxes F^{d|t}: d-states corrected by the
+   * t-flux difference of their own zone with coefficient dt/(3 dx_t), on d-faces
+   * [0, n_d], t-range [0, n_t), third-axis range [-1, n]. */
+  Fields F2[3][3];
+  if (dim == 3) {
+    for (int d = 0; d < 3; ++d)
+      for (int t = 0; t < 3; ++t) {
+        if (t == d) continue;
+        F2[d][t].init(N);
+        int o = 3 - d - t;
+        int lo[3], hi[3];
+        lo[d] = 0; hi[d] = g.n[d];
+        lo[t] = 0; hi[t] = g.n[t] - 1;
+        lo[o] = -1; hi[o] = g.n[o];
+        real coef = dtdx[t] * THIRD;
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2)
+#endif
+        for (int k = lo[2]; k <= hi[2]; ++k)
+          for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int i = lo[0]; i <= hi[0]; ++i) {
+              long id = g.id(i, j, k), zl = id - g.str[d];
+              real qL[5], qR[5], sL[NS], sR[NS], F[5], a[5], b[5], c5[5], e[5];
+              TP[d].get(zl, qL);
+              TM[d].get(id, qR);
+              F1[t].get(zl + g.str[t], a); F1[t].get(zl, b);
+              correct_state(qL, *P, K, coef, a, b, 0.0, nullptr, nullptr, sL);
+              F1[t].get(id + g.str[t], c5); F1[t].get(id, e);
+              correct_state(qR, *P, K, coef, c5, e, 0.0, nullptr, nullptr, sR);
+              hllc(sL, sR, d, P->gamma, F);
+              F2[d][t].put(id, F);
+            }
+      }
+  }
+
+  /* Step 8 final: d-states corrected with coefficient dt/(2 dx_t) by the
+   * transverse flux differences (2-D: F^t; 3-D: F^{t1|t2} then F^{t2|t1}),
+   * then the final solves on d-faces [0, n_d], transverse interior. */
+  Fields F3[3];
+  for (int d = 0; d < dim; ++d) {
+    F3[d].init(N);
+    int lo[3] = {0, 0, 0}, hi[3] = {g.n[0] - 1, g.n[1] - 1, (dim == 3) ? g.n[2] - 1 : 0};
+    hi[d] = g.n[d];
+    int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2)
+#endif
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          long id = g.id(i, j, k), zl = id - g.str[d];
+          real qL[5], qR[5], sL[NS], sR[NS], F[5];
+          TP[d].get(zl, qL);
+          TM[d].get(id, qR);
+          for (int side = 0; side < 2; ++side) {
+            long z = side ? id : zl;
+            const real* q = side ? qR : qL;
+            real* s = side ? sR : sL;
+            real ah[5], al[5], bh[5], bl[5];
+            if (dim == 2) {
+              F1[t1].get(z + g.str[t1], ah); F1[t1].get(z, al);
+              correct_state(q, *P, K, 0.5 * dtdx[t1], ah, al, 0.0, nullptr, nullptr, s);
+            } else {
+              F2[t1][t2].get(z + g.str[t1], ah); F2[t1][t2].get(z, al);
+              F2[t2][t1].get(z + g.str[t2], bh); F2[t2][t1].get(z, bl);
+              correct_state(q, *P, K, 0.5 * dtdx[t1], ah, al, 0.5 * dtdx[t2], bh, bl, s);
+            }
+          }
+          hllc(sL, sR, d, P->gamma, F);
+          F3[d].put(id, F);
+        }
+  }
+
+  /* Step 9: conservative update, x then y then z flux differences;
+   * Step 10: time-centred constant-gravity source. */
+  const bool grav = P->grav[0] != 0.0 || P->grav[1] != 0.0 || P->grav[2] != 0.0;
+  std::vector<real> Out(W);
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) reduction(| : bad)
+#endif
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        long id = g.id(i, j, k);
+        real u0[5], u1[5];
+        for (int c = 0; c < 5; ++c) u0[c] = W[c * N + id];
+        for (int c = 0; c < 5; ++c) {
+          real v = u0[c];
+          for (int d = 0; d < dim; ++d) v = v - dtdx[d] * (F3[d].a[c * N + id + g.str[d]] - F3[d].a[c * N + id]);
+          u1[c] = v;
+        }
+        if (grav) {
+          real rho_mid = 0.5 * (u0[0] + u1[0]);
+          for (int k2 = 0; k2 < 3; ++k2) u1[1 + k2] = u1[1 + k2] + dt * rho_mid * P->grav[k2];
+          real e0 = 0.5 * (u0[1] + u1[1]) * P->grav[0];
+          real e1 = 0.5 * (u0[2] + u1[2]) * P->grav[1];
+          real e2 = 0.5 * (u0[3] + u1[3]) * P->grav[2];
+          u1[4] = u1[4] + dt * ((e0 + e1) + e2);
+        }
+        real q[5];
+        int zb = 0;
+        cons_to_prim(u1, *P, q, nullptr, &zb);
+        bad |= zb;
+        for (int c = 0; c < 5; ++c) Out[c * N + id] = u1[c];
+      }
+  for (long i = 0; i < 5 * N; ++i) Uout[i] = double(Out[i]);
+
+  if (dbg) {
+    for (int d = 0; d < dim; ++d)
+      for (long i = 0; i < 5 * N; ++i) {
+        if (dbg->trace_m[d]) dbg->trace_m[d][i] = double(TM[d].a[i]);
+        if (dbg->trace_p[d]) dbg->trace_p[d][i] = double(TP[d].a[i]);
+        if (dbg->flux1[d]) dbg->flux1[d][i] = double(F1[d].a[i]);
+        if (dbg->flux_final[d]) dbg->flux_final[d][i] = double(F3[d].a[i]);
+      }
+    if (dbg->prim)
+      for (int v = 0; v < 6; ++v)
+        for (long i = 0; i < N; ++i) dbg->prim[v * N + i] = double(Q[v][i]);
+  }
+  return bad ? ORACLE_EBADSTATE : ORACLE_OK;
+}
+
+/* ---- component entry points for unit pins ---- */
+void oracle_hllc(const double* qL, const double* qR, int d, double gamma, double* F) {
+  real l[5], r[5], sl[NS], sr[NS], f[5];
+  for (int c = 0; c < 5; ++c) { l[c] = qL[c]; r[c] = qR[c]; }
+  Consts K;
+  K.gamma = gamma;
+  K.gm1inv = 1.0 / (gamma - 1.0);
+  state_from_prim(l, K, sl);
+  state_from_prim(r, K, sr);
+  hllc(sl, sr, d, gamma, f);
+  for (int c = 0; c < 5; ++c) F[c] = double(f[c]);
+}
+
+void oracle_ppm_parabola(const double* line7, double chi, double* am_ap_a6) {
+  real a[7], am, ap, a6;
+  for (int m = 0; m < 7; ++m) a[m] = line7[m];
+  ppm_parabola(a, chi, &am, &ap, &a6);
+  am_ap_a6[0] = double(am); am_ap_a6[1] = double(ap); am_ap_a6[2] = double(a6);
+}
+
+double oracle_flatten(const double* p7, const double* un7, double small_pres) {
+  real p[7], u[7];
+  for (int m = 0; m < 7; ++m) { p[m] = p7[m]; u[m] = un7[m]; }
+  return double(flat_coef(p, u, small_pres));
+}
+
+double oracle_integ(const double* am_ap_a6, double sigma, int plus) {
+  real am = am_ap_a6[0], ap = am_ap_a6[1], a6 = am_ap_a6[2];
+  return double(plus ? integ_plus(am, ap, a6, sigma) : integ_minus(am, ap, a6, sigma));
+}
+
+/* Trace one zone from 7-point primitive lines along direction d (rho,u,v,w,p
+ * and c, each 7 values).  Used by the unit pins of the tracing step. */
+void oracle_trace_lines(const double* lines6x7, int d, const oracle_params* P, double dtdx, double dt,
+                        double* qm, double* qp) {
+  std::vector<real> Q[NQ];
+  for (int v = 0; v < 6; ++v) {
+    Q[v].resize(7);
+    for (int m = 0; m < 7; ++m) Q[v][m] = lines6x7[v * 7 + m];
+  }
+  for (int v = 6; v < NQ; ++v) Q[v].resize(7);
+  for (int m = 0; m < 7; ++m) {
+    real rho = Q[QRHO][m], c = Q[QC][m];
+    Q[QRC][m] = rho / c;
+    Q[QCR][m] = c / rho;
+    Q[QIC2][m] = 1.0 / (c * c);
+  }
+  real m5[5], p5[5];
+  /* the 7-point lines are laid out contiguously: stride 1 along d */
+  trace_zone(Q, 3, 1, d, *P, dtdx, dt, m5, p5);
+  for (int c = 0; c < 5; ++c) { qm[c] = double(m5[c]); qp[c] = double(p5[c]); }
+}
+
+void oracle_cons_to_prim(const double* U, const oracle_params* P, double* q, int* bad) {
+  real u[5], r[5];
+  for (int c = 0; c < 5; ++c) u[c] = U[c];
+  int b = 0;
+  cons_to_prim(u, *P, r, nullptr, &b);
+  for (int c = 0; c < 5; ++c) q[c] = double(r[c]);
+  if (bad) *bad = b;
+}
+
+void oracle_prim_to_cons(const double* q, double gamma, double* U) {
+  real r[5], u[5];
+  for (int c = 0; c < 5; ++c) r[c] = q[c];
+  Consts K;
+  K.gamma = gamma;
+  K.gm1inv = 1.0 / (gamma - 1.0);
+  prim_to_cons(r, K, u);
+  for (int c = 0; c < 5; ++c) U[c] = double(u[c]);
+}
+
+#ifdef ORACLE_COUNT_FLOPS
+void oracle_tally_reset(void) { g_tally = op_tally{0, 0, 0, 0, 0}; }
+void oracle_tally_get(long long* out5) {
+  out5[0] = g_tally.add; out5[1] = g_tally.mul; out5[2] = g_tally.div;
+  out5[3] = g_tally.sqrt; out5[4] = g_tally.cmp;
+}
+#endif
+
+} /* extern "C" */

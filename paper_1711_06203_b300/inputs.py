@@ -1,0 +1,141 @@
+"""Seeded synthetic initial data for the CTU-PPM hydro step.
+
+Problem set-up only: this module builds initial conditions from their
+primitive definitions (density, velocity, pressure) and converts them to the
+conserved fields with the ideal-gas relation rho*E = p/(gamma-1) + rho|u|^2/2.
+It holds none of the scheme's arithmetic and serves the CUDA path and the CPU
+oracle alike, so both always see the same bits.
+
+Arrays are float64, shape (5, gz, gy, gx): components (rho, rho*u, rho*v,
+rho*w, rho*E), x fastest, over the grown box (interior plus NG = 4 ghost zones
+per side of each active axis; 2-D boxes have gz = 1).  The shapes mirror the
+paper's workloads: Sedov blasts and stratified stellar atmospheres on
+block-structured boxes of uneven sizes (Sec. 4, Figs. 1, 3, 4), plus the
+textbook Sod shock tube.
+"""
+import numpy as np
+
+NG = 4
+BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
+
+
+def grown_shape(n, dim):
+    """(gz, gy, gx) of a box with interior n = (nx, ny, nz)."""
+    nx, ny, nz = n
+    gz = nz + 2 * NG if dim == 3 else 1
+    return (gz, ny + 2 * NG, nx + 2 * NG)
+
+
+def conserved(rho, u, v, w, p, gamma):
+    """Conserved fields from primitive ones (ideal gas)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    U = np.empty((5,) + rho.shape, dtype=np.float64)
+    U[0] = rho
+    U[1] = rho * u
+    U[2] = rho * v
+    U[3] = rho * w
+    U[4] = p / (gamma - 1.0) + 0.5 * rho * ((u * u + v * v) + w * w)
+    return U
+
+
+def zone_centres(n, dim, dx, lo=(0.0, 0.0, 0.0)):
+    """Zone-centre coordinates on the grown box (ghosts included)."""
+    gz, gy, gx = grown_shape(n, dim)
+    x = lo[0] + (np.arange(gx) - NG + 0.5) * dx[0]
+    y = lo[1] + (np.arange(gy) - NG + 0.5) * dx[1]
+    if dim == 3:
+        z = lo[2] + (np.arange(gz) - NG + 0.5) * dx[2]
+    else:
+        z = np.zeros(1)
+    return np.meshgrid(z, y, x, indexing="ij")[::-1]  # x, y, z arrays of shape (gz, gy, gx)
+
+
+def sod(n=64, dim=2, axis=0, gamma=1.4, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x0=0.5):
+    """Sod shock tube along `axis` on the unit square/cube: (rho, u_n, p) left/right of x0."""
+    nn = (n, n, n if dim == 3 else 1)
+    dx = (1.0 / n,) * 3
+    X = zone_centres(nn, dim, dx)[axis]
+    L = X < x0
+    rho = np.where(L, left[0], right[0])
+    un = np.where(L, left[1], right[1])
+    p = np.where(L, left[2], right[2])
+    vel = [np.zeros_like(rho) for _ in range(3)]
+    vel[axis] = un
+    return conserved(rho, vel[0], vel[1], vel[2], p, gamma)
+
+
+def sedov_deposit_mask(n, dim=3, radius_zones=4.0):
+    """Zones whose centre lies strictly within radius_zones * dx of the domain centre.
+
+    Decided in units of dx on half-integer offsets, so the set is exact."""
+    gz, gy, gx = grown_shape((n, n, n if dim == 3 else 1), dim)
+    ox = np.arange(gx) - NG + 0.5 - n / 2.0
+    oy = np.arange(gy) - NG + 0.5 - n / 2.0
+    oz = (np.arange(gz) - NG + 0.5 - n / 2.0) if dim == 3 else np.zeros(1)
+    Z, Y, X = np.meshgrid(oz, oy, ox, indexing="ij")
+    return (X * X + Y * Y + Z * Z) < radius_zones * radius_zones
+
+
+def sedov(n=128, dim=3, gamma=1.4, E=1.0, rho0=1.0, p_amb=1e-5, radius_zones=4.0):
+    """Sedov blast: energy E deposited uniformly as pressure in the zones within
+    radius_zones*dx of the centre of the unit cube; the deposit replaces the
+    ambient pressure there.  Returns (U, number of deposit zones)."""
+    dx = 1.0 / n
+    mask = sedov_deposit_mask(n, dim, radius_zones)
+    ndep = int(mask[:, NG:-NG, NG:-NG].sum()) if dim == 2 else int(mask[NG:-NG, NG:-NG, NG:-NG].sum())
+    vol = dx ** dim
+    p_dep = (gamma - 1.0) * E / (ndep * vol)
+    rho = np.full(mask.shape, rho0)
+    p = np.where(mask, p_dep, p_amb)
+    z = np.zeros_like(rho)
+    return conserved(rho, z, z, z, p, gamma), ndep
+
+
+def random_box(rng, n, dim=3, gamma=5.0 / 3.0, sigma_rho=0.5, sigma_u=0.1, sigma_p=0.3):
+    """Every zone (ghosts included): rho ~ LogNormal(0, sigma_rho), each velocity
+    component ~ N(0, sigma_u), p ~ LogNormal(0, sigma_p)."""
+    shape = grown_shape(n, dim)
+    rho = rng.lognormal(0.0, sigma_rho, shape)
+    u = rng.normal(0.0, sigma_u, shape)
+    v = rng.normal(0.0, sigma_u, shape)
+    w = rng.normal(0.0, sigma_u, shape) if dim == 3 else np.zeros(shape)
+    p = rng.lognormal(0.0, sigma_p, shape)
+    return conserved(rho, u, v, w, p, gamma)
+
+
+def stratified(n, dim=3, gamma=5.0 / 3.0, g=1.0, H=0.1, perturb=0.0, rng=None):
+    """Isothermal atmosphere in hydrostatic balance under gravity -g along the
+    last active axis: rho = exp(-z/H), p = rho g H at zone centres, optional
+    seeded relative pressure perturbation p *= 1 + perturb N(0,1)."""
+    nn = (n, n, n if dim == 3 else 1)
+    dx = (1.0 / n,) * 3
+    X = zone_centres(nn, dim, dx)
+    z = X[dim - 1]
+    rho = np.exp(-z / H)
+    p = rho * g * H
+    if perturb:
+        p = p * (1.0 + perturb * rng.normal(0.0, 1.0, p.shape))
+    zero = np.zeros_like(rho)
+    return conserved(rho, zero, zero, zero, p, gamma)
+
+
+LEVEL_SIDES = (16, 24, 32, 48, 64)
+
+
+def level_box_sizes(nbox=512, seed=1711, sides=LEVEL_SIDES):
+    """Interior sizes (nx, ny, nz) of an AMR level of uneven boxes: each side drawn
+    independently and uniformly from `sides`."""
+    rng = np.random.default_rng(seed)
+    return [tuple(int(s) for s in rng.choice(sides, 3)) for _ in range(nbox)]
+
+
+def level_boxes(nbox=512, seed=1711, gamma=5.0 / 3.0, sides=LEVEL_SIDES):
+    """The batched-level workload: sizes plus random prefilled states for every box."""
+    sizes = level_box_sizes(nbox, seed, sides)
+    rng = np.random.default_rng(seed + 1)
+    return sizes, [random_box(rng, s, 3, gamma) for s in sizes]
+
+
+def two_state(n, dim=3, gamma=1.4, rhoL=1.0, pL=1.0, rhoR=0.125, pR=0.1, x0=0.5):
+    """Planar two-state Riemann problem along x at rest (the served 'two-state' kind)."""
+    return sod(n, dim, 0, gamma, (rhoL, 0.0, pL), (rhoR, 0.0, pR), x0)
