@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300-native CTU-PPM hydro step: prints ONE JSON line.
+
+Workload: the 3-D Sedov blast on a single 128^3 FP64 box (unit cube, 4 ghost
+zones, outflow boundaries, gamma = 1.4, ambient rho = 1, p = 1e-5, E = 1
+deposited as pressure in the zones within 4 dx of the centre, CFL 0.5) — the
+pure-hydro Sedov problem of the paper's Castro scaling runs (Sec. 4, Fig. 3
+left; Fig. 4 left), at the size one box of such a run holds.  A step is one
+CTU-PPM advance of the whole box (primitive state, tracing, 12 Riemann solves
+per zone, update, CFL reduction) through the library's C ABI with the state
+resident in HBM; the next step uses the CFL step the library returns.
+
+--impl ours (default): the CUDA library.  --impl reference: the CPU oracle
+(test infrastructure, not the product) on the same workload, timed on the
+host cores.  Under torchrun each rank advances its own box (weak scaling, no
+collective on the data path); rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Algorithmic FP64 operations (+ - * / sqrt, each counted once) per unit of
+# each stage, tallied by the counting build of the CPU oracle on this
+# workload (Sedov 128^3 after 20 steps; python -m oracle.count_ops).  Units: grown-box zone (prim),
+# zone-direction (trace), Riemann solve (flux1, flux2, flux3), interior zone
+# (update).
+FLOPS_PER_UNIT = {"prim": 20.0, "trace": 337.8, "flux1": 80.0, "flux2": 140.0, "flux3": 174.0, "update": 58.0}
+LAUNCHES_PER_STEP_3D = {"prim": 1, "trace": 3, "flux1": 3, "flux2": 6, "flux3": 3, "update": 3}
+# FP64 peak derived from B300's unit counts and clock: 148 SMs x 2 FP64 FMA
+# lanes per SM per clock x 2 flops x 2032 MHz.  (A dependent-free DFMA stream
+# measured 476 G lane-FMA/s = 0.95 TFLOP/s on the B300s.)
+FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
+L2_FLUSH_BYTES = 256 << 20
+
+
+def units_per_step(n):
+    return {
+        "prim": (n + 8) ** 3,
+        "trace": 3 * (n + 2) ** 3,
+        "flux1": 3 * (n + 1) * (n + 2) ** 2,
+        "flux2": 6 * (n + 1) * n * (n + 2),
+        "flux3": 3 * (n + 1) * n * n,
+        "update": n ** 3,
+    }
+
+
+def algorithmic_bytes_per_step(n):
+    # read the 5 fields of the grown box once, write the 5 interior fields once
+    return 40 * ((n + 8) ** 3 + n ** 3)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hydro_clocks_{os.getpid()}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def cpu_oracle_rate(U, n, steps, budget_s=25.0):
+    """Oracle zone-updates/s on the host cores: up to `steps` full 128^3 steps
+    from U, stopping once budget_s is spent (at least one step)."""
+    import oracle
+    P = oracle.params(3, (n, n, n), bc=oracle.BC_OUTFLOW, gamma=1.4, cfl=0.5)
+    done, t_total = 0, 0.0
+    for _ in range(steps):
+        d, rc = oracle.dt(U, P)
+        t0 = time.perf_counter()
+        U, rc = oracle.step(U, P, d)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if t_total > budget_s:
+            break
+    return n ** 3 * done / t_total, done, t_total, U
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1711_06203_b300 import inputs
+    n = args.n
+    U, _ = inputs.sedov(n)
+    # warm-up steps advance the state; timed steps are bounded so the run ends in minutes
+    _, _, _, U = cpu_oracle_rate(U, n, args.warmup, budget_s=60.0)
+    rate, done, t, _ = cpu_oracle_rate(U, n, args.steps, budget_s=150.0)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "3D PPM zone-updates/s", "value": rate, "unit": "zone-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / done,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"sedov3d_{n}^3", "n": n, "gamma": 1.4, "cfl": 0.5, "bc": "outflow"},
+        "cpu_baseline": {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{done} full {n}^3 oracle steps after {args.warmup} warm-up steps"},
+        "e2e": {"value": rate, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    dx = (1.0 / n,) * 3
+    U0, ndep = inputs.sedov(n)
+    ctx = hb.Context(local_rank)
+    p = hb.params(3, gamma=1.4, cfl=0.5)
+    a = torch.from_numpy(U0).to(dev)
+    b = torch.empty_like(a)
+    stream = torch.cuda.current_stream(dev)
+
+    def box(t):
+        return hb.box(t, (n, n, n), dx, hb.BC_OUTFLOW)
+
+    dt = ctx.hydro_dt(box(a), p, stream)
+    for _ in range(args.warmup):
+        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+        a, b = b, a
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.hydro_ctx_set_profiling(True)
+    launches0 = ctx.hydro_ctx_launches()
+    gpu_id = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None else str(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+        ev[k][1].record(stream)
+        a, b = b, a
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        dist.barrier()
+    launches = ctx.hydro_ctx_launches() - launches0
+    stage_ms, calls = ctx.hydro_ctx_stage_times()
+    ctx.hydro_ctx_set_profiling(False)
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    zones = n ** 3
+    value = world * zones * args.steps / (total_ms * 1e-3)
+
+    # end to end: pinned host state in, result out, every step, copies inside the events
+    h_in = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
+    h_in.copy_(a)
+    h_out = torch.empty_like(h_in, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        a.copy_(h_in, non_blocking=True)
+        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+        h_out.copy_(b, non_blocking=True)
+        h_in, h_out = h_out, h_in
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    nbytes = a.numel() * a.element_size()
+
+    # roofline of the dominant stage (FP64 ALU bound: every stage is)
+    units = units_per_step(n)
+    per_step = {k: v / calls for k, v in stage_ms.items()}
+    dom = max(per_step, key=per_step.get)
+    flops = FLOPS_PER_UNIT[dom] * units[dom]
+    achieved = flops / (per_step[dom] * 1e-3) / 1e9
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    step_gbs = algorithmic_bytes_per_step(n) / (total_ms / args.steps * 1e-3) / 1e9
+    step_gflops = sum(FLOPS_PER_UNIT[k] * units[k] for k in units) / (total_ms / args.steps * 1e-3) / 1e9
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, done, t, _ = cpu_oracle_rate(U0, n, 50, budget_s=20.0)
+        cpu = {"value": rate, "unit": "zone-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done} full {n}^3 oracle steps from the initial Sedov state"}
+    line = {
+        "metric": "3D PPM zone-updates/s", "value": value, "unit": "zone-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"sedov3d_{n}^3", "n": n, "gamma": 1.4, "cfl": 0.5, "bc": "outflow",
+                   "deposit_zones": ndep, "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": f"replica x{world}"},
+        "roofline": {"bound": "alu", "kernel": f"{dom} stage ({LAUNCHES_PER_STEP_3D[dom]} launches/step)",
+                     "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "peak_note": "FP64 derived: 148 SMs x 2 FMA lanes x 2 flop x 2.032 GHz"},
+        "hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
+                "note": "algorithmic bytes of the whole step (read grown box, write interior) / step time, of measured"},
+        "step_gflops": step_gflops,
+        "stages_ms_per_step": per_step,
+        "cpu_baseline": cpu,
+        "e2e": {"value": zones / (e2e_ms * 1e-3) * world, "unit": "zone-updates/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "wall_s_timed": wall,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=128, help="box side (the workload is 128)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,157 @@
+/* hydro.h — C ABI of the B300-native CTU-PPM hydrodynamics step.
+ *
+ * One unsplit corner-transport-upwind (CTU) piecewise-parabolic (PPM) Godunov
+ * step of the gamma-law Euler equations, with an optional constant-gravity
+ * source, on block-structured boxes with ghost zones.  The paper (Sec. 3.2)
+ * names Castro's hydrodynamics scheme "an unsplit piecewise parabolic
+ * method"; its Sec. 4 GPU paragraph states the execution model kept here: an
+ * iterator hands each box's data pointer to a compute kernel that operates on
+ * data already resident on the device.  Every stage of the step runs in this
+ * library's CUDA kernels (sm_103a, FP64 throughout).
+ *
+ * Conventions shared by every call
+ *  - Pointers marked "device" are CUDA device pointers on the context's
+ *    device; "host" pointers are ordinary host memory.  The caller owns every
+ *    buffer it passes; the library never frees or retains them after return.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is enqueued on it in order; calls return before it
+ *    completes unless a host output (dt_next_host, bad_box_host) is requested,
+ *    in which case the call synchronises that stream.
+ *  - Return values are hydro_status codes; no call throws or aborts.
+ *    Argument errors are reported synchronously and enqueue nothing.
+ *  - A context is not thread-safe: use one per host thread.
+ *
+ * Box layout (hydro_box_t)
+ *  - 5 conserved FP64 fields U = (rho, rho*u, rho*v, rho*w, rho*E), each a 3-D
+ *    array over the GROWN box: n[a] interior zones plus ng = 4 ghost zones on
+ *    both sides of every active axis (x, y; and z when dim = 3).  In 2-D,
+ *    n[2] = 1 and z has no ghost zones.
+ *  - `u` points at field 0, zone (-4, -4, -4) (2-D: (-4, -4, 0)); zone (i,j,k)
+ *    of field c lives at u[c*stride[2] + (k+gz)*stride[1] + (j+4)*stride[0] + (i+4)]
+ *    with gz = 4 in 3-D and 0 in 2-D: x is contiguous, stride[0] is the row
+ *    pitch (>= n[0]+8), stride[1] the plane pitch (>= stride[0]*(n[1]+8)),
+ *    stride[2] the component pitch (>= stride[1]*(n[2]+2*gz)).  Strides are
+ *    in elements.
+ *  - Ghost zones of an input box are either filled by the caller
+ *    (HYDRO_BC_PREFILLED) or derived on the fly from the interior by the
+ *    boundary kind of that face; the input box is never written.
+ *  - The output box receives the interior of U^{n+1}; its ghost zones are
+ *    left unspecified.  Input and output must not overlap.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYDRO_OK = 0,
+  HYDRO_EINVAL = -1,     /* invalid argument (nothing enqueued) */
+  HYDRO_ENOMEM = -2,     /* device or host allocation failed */
+  HYDRO_ECUDA = -3,      /* a CUDA runtime call failed */
+  HYDRO_EBADSTATE = -4,  /* a zone held rho <= 0, p <= 0 or a non-finite value */
+  HYDRO_EAGAIN = -5,     /* result not ready yet (serve_poll) */
+  HYDRO_ETIMEDOUT = -6,  /* a bounded wait ran out */
+  HYDRO_ENOTIMPL = -7    /* not supported by this build */
+} hydro_status;
+
+/* boundary kind of one face of a box */
+enum {
+  HYDRO_BC_OUTFLOW = 0,   /* zero-gradient: ghost = nearest interior zone */
+  HYDRO_BC_REFLECT = 1,   /* mirror image, normal momentum negated */
+  HYDRO_BC_PERIODIC = 2,  /* wrap around the same box (both faces of the axis) */
+  HYDRO_BC_PREFILLED = 3  /* ghost zones hold valid data supplied by the caller */
+};
+
+/* hydro_params_t.flags */
+#define HYDRO_FLAG_NO_FLATTEN 1u /* disable Colella-Woodward flattening */
+
+typedef struct {
+  double gamma;       /* gamma-law EOS exponent, > 1 */
+  double cfl;         /* Courant number for the time-step estimate, in (0, 1] */
+  double grav[3];     /* constant gravitational acceleration (0 = none) */
+  double small_dens;  /* density floor (> 0), e.g. 1e-200 */
+  double small_pres;  /* pressure floor (> 0), e.g. 1e-200 */
+  int dim;            /* 2 or 3 */
+  unsigned flags;     /* HYDRO_FLAG_* */
+} hydro_params_t;
+
+typedef struct {
+  double* u;            /* device: field 0 at the first grown zone (see layout above) */
+  int n[3];             /* interior zones per axis, >= 1; n[2] = 1 when dim = 2 */
+  int ng;               /* ghost zones per side on active axes: must be 4 */
+  long long stride[3];  /* element strides: row, plane, component */
+  double dx[3];         /* zone widths, > 0 on active axes */
+  int bc[3][2];         /* boundary kind per axis (x, y, z) and side (low, high) */
+} hydro_box_t;
+
+typedef struct hydro_ctx hydro_ctx_t;
+
+/* Create a context on CUDA device `device`.  The context owns the scratch
+ * memory of the staged step (grown on demand to the largest box seen), the
+ * device flags for bad-state detection and the reduction buffers of the CFL
+ * estimate.  Returns HYDRO_ECUDA if the device cannot be used. */
+int hydro_ctx_create(hydro_ctx_t** ctx, int device);
+
+/* Release a context and everything it owns.  Synchronises its device. NULL is a no-op. */
+void hydro_ctx_destroy(hydro_ctx_t* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* hydro_strerror(int status);
+
+/* CFL time step of a box (paper Sec. 3.1: a compressible step is limited by
+ * the sound speed): dt = cfl * min over interior zones and active directions
+ * d of dx_d / (|u_d| + c), c = sqrt(gamma p / rho).  Writes the value to
+ * *dt_host (host) after synchronising `stream`.  HYDRO_EBADSTATE if any
+ * interior zone is non-physical. */
+int hydro_dt(hydro_ctx_t* ctx, const hydro_box_t* box, const hydro_params_t* params, double* dt_host,
+             void* stream);
+
+/* Advance one box by dt with one CTU-PPM step (paper Sec. 3.2's unsplit PPM;
+ * Sec. 4's box-at-a-time kernel call): in -> out, out of place.
+ *  - in, out: boxes of identical interior size on the same device (strides may
+ *    differ); `in` is only read.
+ *  - dt: the step, > 0.
+ *  - dt_next_host: NULL, or host memory that receives the CFL step of U^{n+1}
+ *    (the call then synchronises `stream` and also reports HYDRO_EBADSTATE
+ *    for a non-physical input or result).  With NULL the call is fully
+ *    asynchronous; a bad state is then recorded in the context and reported by
+ *    the next hydro_ctx_check().
+ *  - Every grown-box zone of `in` that the stencil reads must hold a physical
+ *    state. */
+int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                      const hydro_params_t* params, double dt, double* dt_next_host, void* stream);
+
+/* Report and clear the context's sticky bad-state flag: synchronises the
+ * context's device, returns HYDRO_EBADSTATE if any step since the last check
+ * met a non-physical zone, else HYDRO_OK. */
+int hydro_ctx_check(hydro_ctx_t* ctx);
+
+/* ---- instrumentation (paper: no profiler is named; this is the build's own tracing) ----
+ * Stages of a step, in order: 0 primitive state, 1 characteristic tracing,
+ * 2 first Riemann solves, 3 intermediate (3-D) solves, 4 final solves,
+ * 5 update + CFL reduction. */
+#define HYDRO_NSTAGES 6
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing of hydro_advance_box
+ * on the stream it is called with, and reset the accumulated times.  While
+ * enabled every hydro_advance_box call synchronises its stream after the step. */
+int hydro_ctx_set_profiling(hydro_ctx_t* ctx, int enable);
+
+/* Copy up to nmax accumulated stage durations (milliseconds, summed over the
+ * profiled calls) into ms (host) and the number of profiled calls into *calls
+ * (host, nullable).  Returns the number of stages (HYDRO_NSTAGES) or a
+ * negative status. */
+int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* calls);
+
+/* Total number of CUDA kernels this context has enqueued (host counter). */
+long long hydro_ctx_launches(const hydro_ctx_t* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYDRO_H */

@@ -69,6 +69,7 @@ def _lib(counting=False):
         if counting:
             lib.oracle_tally_reset.argtypes = []
             lib.oracle_tally_get.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+            lib.oracle_tally_stages.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         _libs[name] = lib
     return _libs[name]
 
@@ -167,6 +168,22 @@ def count_ops(U, P, dt_):
     t = (ctypes.c_longlong * 5)()
     lib.oracle_tally_get(t)
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), list(t)))
+
+
+STAGES = ("prim", "trace", "flux1", "flux2", "flux3", "update")
+
+
+def count_ops_by_stage(U, P, dt_):
+    """Per-stage operation tallies of one step: {stage: dict(add, mul, div, sqrt, cmp)}."""
+    lib = _lib(counting=True)
+    lib.oracle_tally_reset()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty_like(U)
+    lib.oracle_step(_ptr(U), _ptr(out), ctypes.byref(P), float(dt_), None)
+    t = (ctypes.c_longlong * 30)()
+    lib.oracle_tally_stages(t)
+    keys = ("add", "mul", "div", "sqrt", "cmp")
+    return {st: dict(zip(keys, list(t)[5 * k: 5 * k + 5])) for k, st in enumerate(STAGES)}
 
 
 def hllc(qL, qR, d, gamma):

@@ -39,7 +39,20 @@
 #include "flopcount.h"
 typedef counted real;
 op_tally g_tally;
+/* tallies per stage of the step: prim, trace, flux1, flux2, flux3, update */
+static op_tally g_stage_tally[6];
+static op_tally g_mark;
+static void stage_mark(int stage) {
+  if (stage > 0) {
+    op_tally& t = g_stage_tally[stage - 1];
+    t.add += g_tally.add - g_mark.add; t.mul += g_tally.mul - g_mark.mul; t.div += g_tally.div - g_mark.div;
+    t.sqrt += g_tally.sqrt - g_mark.sqrt; t.cmp += g_tally.cmp - g_mark.cmp;
+  }
+  g_mark = g_tally;
+}
+#define STAGE_MARK(k) stage_mark(k)
 #else
+#define STAGE_MARK(k) ((void)0)
 typedef double real;
 using std::isfinite;
 using std::sqrt;
@@ -82,14 +95,18 @@ struct Grid {
 /* ---- Step 1: ghost-zone fill (outflow / reflect / periodic / prefilled) ---- */
 void fill_ghosts(real* W, const Grid& g, const oracle_params& P) {
   for (int a = 0; a < g.dim; ++a) {
-    /* fill axis a over the interior range of later axes and the full grown
-     * range of earlier ones, so edges and corners are a product of the
-     * per-axis maps */
+    /* fill axis a over the full grown range of earlier axes (already
+     * filled) and, on later axes, over the interior plus any prefilled ghost
+     * layers (caller data): edges and corners are then the product of the
+     * per-axis maps, a prefilled face mapping each zone to itself */
     int lo[3], hi[3];
     for (int b = 0; b < 3; ++b) {
       int gb = (b == 2) ? g.ngz : NG;
       if (b < a) { lo[b] = -gb; hi[b] = g.n[b] + gb; }
-      else { lo[b] = 0; hi[b] = g.n[b]; }
+      else {
+        lo[b] = (b < g.dim && P.bc[b][0] == ORACLE_BC_PREFILLED) ? -gb : 0;
+        hi[b] = (b < g.dim && P.bc[b][1] == ORACLE_BC_PREFILLED) ? g.n[b] + gb : g.n[b];
+      }
     }
     for (int side = 0; side < 2; ++side) {
       int bc = P.bc[a][side];
@@ -272,21 +289,21 @@ void trace_zone(const std::vector<real>* Q, long id, long st, int d, const oracl
     bool reach[3];
     for (int w = 0; w < 3; ++w) reach[w] = side ? (lam[w] > 0.0) : (lam[w] < 0.0);
     int fast = side ? 2 : 0; /* fastest wave toward that face gives the reference state */
-    real I[3][5];
-    for (int w = 0; w < 3; ++w)
-      for (int v = 0; v < 5; ++v)
-        I[w][v] = side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
+    /* I(w, v): average of variable v's parabola over the domain swept by wave w */
+    auto I = [&](int w, int v) {
+      return side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
+    };
     real ref[5];
-    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I[fast][v] : line[v][3];
+    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : line[v][3];
     /* wave strengths beta = l . (ref - I(sigma_nu)) of the waves that reach the face */
     real bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
-    if (reach[0]) bm = -lu * (ref[1] - I[0][1]) + lp * (ref[4] - I[0][4]);
+    if (reach[0]) bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
     if (reach[1]) {
-      b0 = (ref[0] - I[1][0]) - inv_c2 * (ref[4] - I[1][4]);
-      bt1 = ref[2] - I[1][2];
-      bt2 = ref[3] - I[1][3];
+      b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
+      bt1 = ref[2] - I(1, 2);
+      bt2 = ref[3] - I(1, 3);
     }
-    if (reach[2]) bp = lu * (ref[1] - I[2][1]) + lp * (ref[4] - I[2][4]);
+    if (reach[2]) bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
     /* edge state = ref - sum beta_nu r_nu */
     real s_rho = ref[0] - ((bm + b0) + bp);
     real s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
@@ -446,6 +463,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
   std::vector<real> W(Uin, Uin + 5 * N);
   fill_ghosts(W.data(), g, *P);
 
+  STAGE_MARK(0);
   /* Step 2: primitive variables and sound speed on the whole grown box */
   std::vector<real> Q[NQ];
   for (int v = 0; v < NQ; ++v) Q[v].assign(N, real(0.0));
@@ -471,6 +489,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
   for (int a = 0; a < 3; ++a) dtdx[a] = (a < dim) ? dt / P->dx[a] : 0.0;
   const int kz0 = (dim == 3) ? -1 : 0, kz1 = (dim == 3) ? g.n[2] : 0; /* the [-1, n] range in z, 3-D only */
 
+  STAGE_MARK(1);
   /* Steps 4-6: traced states of every zone in [-1, n] on all active axes */
   Fields TM[3], TP[3];
   for (int d = 0; d < dim; ++d) {
@@ -488,6 +507,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
         }
   }
 
+  STAGE_MARK(2);
   /* Step 7a: first Riemann solves on d-faces f in [0, n_d], transverse range [-1, n].
    * Face f (between zones f-1 and f) is stored at zone index f. */
   Fields F1[3];
@@ -512,6 +532,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
         }
   }
 
+  STAGE_MARK(3);
   /* Step 8 (3-D only): intermediate fluxes F^{d|t}: d-states corrected by the
    * t-flux difference of their own zone with coefficient dt/(3 dx_t), on d-faces
    * [0, n_d], t-range [0, n_t), third-axis range [-1, n]. */
@@ -547,6 +568,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
       }
   }
 
+  STAGE_MARK(4);
   /* Step 8 final: d-states corrected with coefficient dt/(2 dx_t) by the
    * transverse flux differences (2-D: F^t; 3-D: F^{t1|t2} then F^{t2|t1}),
    * then the final solves on d-faces [0, n_d], transverse interior. */
@@ -585,6 +607,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
         }
   }
 
+  STAGE_MARK(5);
   /* Step 9: conservative update, x then y then z flux differences;
    * Step 10: time-centred constant-gravity source. */
   const bool grav = P->grav[0] != 0.0 || P->grav[1] != 0.0 || P->grav[2] != 0.0;
@@ -617,6 +640,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
         bad |= zb;
         for (int c = 0; c < 5; ++c) Out[c * N + id] = u1[c];
       }
+  STAGE_MARK(6);
   for (long i = 0; i < 5 * N; ++i) Uout[i] = double(Out[i]);
 
   if (dbg) {
@@ -707,7 +731,17 @@ void oracle_prim_to_cons(const double* q, double gamma, double* U) {
 }
 
 #ifdef ORACLE_COUNT_FLOPS
-void oracle_tally_reset(void) { g_tally = op_tally{0, 0, 0, 0, 0}; }
+void oracle_tally_reset(void) {
+  g_tally = op_tally{0, 0, 0, 0, 0};
+  for (auto& t : g_stage_tally) t = op_tally{0, 0, 0, 0, 0};
+}
+void oracle_tally_stages(long long* out30) {
+  for (int k = 0; k < 6; ++k) {
+    const op_tally& t = g_stage_tally[k];
+    out30[5 * k + 0] = t.add; out30[5 * k + 1] = t.mul; out30[5 * k + 2] = t.div;
+    out30[5 * k + 3] = t.sqrt; out30[5 * k + 4] = t.cmp;
+  }
+}
 void oracle_tally_get(long long* out5) {
   out5[0] = g_tally.add; out5[1] = g_tally.mul; out5[2] = g_tally.div;
   out5[3] = g_tally.sqrt; out5[4] = g_tally.cmp;

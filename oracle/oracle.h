@@ -46,6 +46,11 @@ void oracle_trace_lines(const double* lines6x7, int d, const oracle_params* P, d
 void oracle_cons_to_prim(const double* U, const oracle_params* P, double* q, int* bad);
 void oracle_prim_to_cons(const double* q, double gamma, double* U);
 
+/* counting build only (liboracle_count.so): operation tallies */
+void oracle_tally_reset(void);
+void oracle_tally_get(long long* out5);
+void oracle_tally_stages(long long* out30);
+
 /* exact Riemann solver for the gamma-law Euler equations */
 int oracle_exact_star(const double* WL, const double* WR, double gamma, double* pstar_ustar);
 int oracle_exact_sample(const double* WL, const double* WR, double gamma, const double* xi, int n, double* W_out);

@@ -1,0 +1,182 @@
+"""Thin ctypes binding of libhydro.so (include/hydro.h).
+
+Argument marshalling only: every stage of the step runs in the library's CUDA
+kernels.  Functions keep the C names.  Tensors are PyTorch CUDA float64
+tensors of shape (5, gz, gy, gx) over the grown box (x fastest); PyTorch is
+used for device memory and streams only.  There is no CPU fallback: if the
+library cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBDIR = os.path.join(HERE, "_build")
+
+HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA = 0, -1, -2, -3
+HYDRO_EBADSTATE, HYDRO_EAGAIN, HYDRO_ETIMEDOUT, HYDRO_ENOTIMPL = -4, -5, -6, -7
+BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
+FLAG_NO_FLATTEN = 1
+NG = 4
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+class hydro_params_t(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("grav", ctypes.c_double * 3),
+        ("small_dens", ctypes.c_double),
+        ("small_pres", ctypes.c_double),
+        ("dim", ctypes.c_int),
+        ("flags", ctypes.c_uint),
+    ]
+
+
+class hydro_box_t(ctypes.Structure):
+    _fields_ = [
+        ("u", ctypes.c_void_p),
+        ("n", ctypes.c_int * 3),
+        ("ng", ctypes.c_int),
+        ("stride", ctypes.c_longlong * 3),
+        ("dx", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+    ]
+
+
+_LIBS = {}
+
+
+def library_path(variant="default"):
+    name = "libhydro.so" if variant == "default" else "libhydro_exact.so"
+    return os.path.join(LIBDIR, name)
+
+
+def lib(variant="default"):
+    """Load libhydro (variant 'default') or its no-contraction build ('exact')."""
+    if variant in _LIBS:
+        return _LIBS[variant]
+    path = library_path(variant)
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_1711_06203_b300/build.py)")
+    L = ctypes.CDLL(path)
+    vp, P, B = ctypes.c_void_p, ctypes.POINTER(hydro_params_t), ctypes.POINTER(hydro_box_t)
+    D = ctypes.POINTER(ctypes.c_double)
+    L.hydro_ctx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    L.hydro_ctx_destroy.argtypes = [vp]
+    L.hydro_ctx_destroy.restype = None
+    L.hydro_ctx_check.argtypes = [vp]
+    L.hydro_strerror.argtypes = [ctypes.c_int]
+    L.hydro_strerror.restype = ctypes.c_char_p
+    L.hydro_dt.argtypes = [vp, B, P, D, vp]
+    L.hydro_advance_box.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
+    L.hydro_ctx_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.hydro_ctx_stage_times.argtypes = [vp, D, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+    L.hydro_ctx_launches.argtypes = [vp]
+    L.hydro_ctx_launches.restype = ctypes.c_longlong
+    _LIBS[variant] = L
+    return L
+
+
+def strerror(status):
+    try:
+        return lib().hydro_strerror(int(status)).decode()
+    except Exception:
+        return "unknown"
+
+
+def params(dim, gamma=1.4, cfl=0.5, grav=(0.0, 0.0, 0.0), small_dens=1e-200, small_pres=1e-200, flatten=True):
+    p = hydro_params_t()
+    p.gamma, p.cfl, p.dim = gamma, cfl, dim
+    for a in range(3):
+        p.grav[a] = grav[a]
+    p.small_dens, p.small_pres = small_dens, small_pres
+    p.flags = 0 if flatten else FLAG_NO_FLATTEN
+    return p
+
+
+def box(t, n, dx, bc=BC_OUTFLOW):
+    """hydro_box_t describing tensor t (5, gz, gy, gx), float64, x contiguous.
+    n: interior (nx, ny, nz); bc: one kind for every face or a 3x2 nested sequence."""
+    if t.dtype.itemsize != 8 or t.dim() != 4 or t.shape[0] != 5 or t.stride(3) != 1:
+        raise ValueError("box tensor must be float64 of shape (5, gz, gy, gx) with x contiguous")
+    b = hydro_box_t()
+    b.u = t.data_ptr()
+    for a in range(3):
+        b.n[a] = int(n[a]) if a < len(n) else 1
+        b.dx[a] = float(dx[a])
+        for s in range(2):
+            b.bc[a][s] = bc if isinstance(bc, int) else bc[a][s]
+    b.ng = NG
+    b.stride[0], b.stride[1], b.stride[2] = t.stride(2), t.stride(1), t.stride(0)
+    return b
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A hydro_ctx_t on one device (owns scratch and flags)."""
+
+    def __init__(self, device=0, variant="default"):
+        self.L = lib(variant)
+        h = ctypes.c_void_p()
+        rc = self.L.hydro_ctx_create(ctypes.byref(h), int(device))
+        if rc:
+            raise HydroError(rc, "hydro_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hydro_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def hydro_dt(self, b, p, stream=None):
+        out = ctypes.c_double(0.0)
+        rc = self.L.hydro_dt(self.h, ctypes.byref(b), ctypes.byref(p), ctypes.byref(out), _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_dt")
+        return out.value
+
+    def hydro_advance_box(self, bin_, bout, p, dt, want_dt_next=False, stream=None, raise_on_error=True):
+        out = ctypes.c_double(0.0)
+        rc = self.L.hydro_advance_box(self.h, ctypes.byref(bin_), ctypes.byref(bout), ctypes.byref(p), float(dt),
+                                      ctypes.byref(out) if want_dt_next else None, _stream_handle(stream))
+        if rc and raise_on_error:
+            raise HydroError(rc, "hydro_advance_box")
+        return (out.value if want_dt_next else None) if raise_on_error else (rc, out.value)
+
+    def hydro_ctx_check(self):
+        return self.L.hydro_ctx_check(self.h)
+
+    STAGES = ("prim", "trace", "flux1", "flux2", "flux3", "update")
+
+    def hydro_ctx_set_profiling(self, enable):
+        rc = self.L.hydro_ctx_set_profiling(self.h, 1 if enable else 0)
+        if rc:
+            raise HydroError(rc, "hydro_ctx_set_profiling")
+
+    def hydro_ctx_stage_times(self):
+        ms = (ctypes.c_double * 8)()
+        calls = ctypes.c_longlong(0)
+        n = self.L.hydro_ctx_stage_times(self.h, ms, 8, ctypes.byref(calls))
+        if n < 0:
+            raise HydroError(n, "hydro_ctx_stage_times")
+        return {self.STAGES[i]: ms[i] for i in range(n)}, calls.value
+
+    def hydro_ctx_launches(self):
+        return self.L.hydro_ctx_launches(self.h)

@@ -1,0 +1,334 @@
+// C ABI of the CTU-PPM step: context, argument validation, scratch
+// management and the box-level entry points declared in include/hydro.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hydro.h"
+#include "hydro_api_internal.cuh"
+
+using namespace hydro;
+
+namespace {
+
+// restores the calling thread's current device on scope exit
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+namespace hydro {
+
+bool valid_params(const hydro_params_t* p) {
+  if (!p) return false;
+  if (p->dim != 2 && p->dim != 3) return false;
+  if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return false;
+  if (!(p->cfl > 0.0) || !(p->cfl <= 1.0)) return false;
+  if (!(p->small_dens > 0.0) || !(p->small_pres > 0.0)) return false;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->grav[a])) return false;
+  return true;
+}
+
+bool valid_box(const hydro_box_t* b, int dim) {
+  if (!b || !b->u) return false;
+  if (reinterpret_cast<uintptr_t>(b->u) % sizeof(double)) return false;
+  if (b->ng != NG) return false;
+  for (int a = 0; a < 3; ++a)
+    if (b->n[a] < 1 || b->n[a] > (1 << 20)) return false;
+  if (dim == 2 && b->n[2] != 1) return false;
+  const long long gx = b->n[0] + 2 * NG, gy = b->n[1] + 2 * NG;
+  const long long gz = (dim == 3) ? b->n[2] + 2 * NG : 1;
+  if (b->stride[0] < gx || b->stride[1] < b->stride[0] * gy || b->stride[2] < b->stride[1] * gz) return false;
+  for (int a = 0; a < dim; ++a) {
+    if (!(b->dx[a] > 0.0) || !std::isfinite(b->dx[a])) return false;
+    for (int s = 0; s < 2; ++s)
+      if (b->bc[a][s] < HYDRO_BC_OUTFLOW || b->bc[a][s] > HYDRO_BC_PREFILLED) return false;
+    if ((b->bc[a][0] == HYDRO_BC_PERIODIC) != (b->bc[a][1] == HYDRO_BC_PERIODIC)) return false;
+    // a derived ghost layer copies interior zones, so the axis needs at least NG of them
+    bool derived = b->bc[a][0] != HYDRO_BC_PREFILLED || b->bc[a][1] != HYDRO_BC_PREFILLED;
+    if (derived && b->n[a] < NG) return false;
+  }
+  return true;
+}
+
+long long box_span(const hydro_box_t* b, int dim) {
+  const long long gz = (dim == 3) ? b->n[2] + 2 * NG : 1;
+  return 4 * b->stride[2] + (gz - 1) * b->stride[1] + (b->n[1] + 2 * NG - 1) * b->stride[0] + b->n[0] + 2 * NG;
+}
+
+bool boxes_overlap(const hydro_box_t* a, const hydro_box_t* b, int dim) {
+  const char* a0 = reinterpret_cast<const char*>(a->u);
+  const char* b0 = reinterpret_cast<const char*>(b->u);
+  const char* a1 = a0 + box_span(a, dim) * (long long)sizeof(double);
+  const char* b1 = b0 + box_span(b, dim) * (long long)sizeof(double);
+  return a0 < b1 && b0 < a1;
+}
+
+BoxGeom geom_of(const hydro_box_t* b, int dim) {
+  BoxGeom g;
+  g.u = b->u;
+  g.sy = b->stride[0];
+  g.sz = b->stride[1];
+  g.sc = b->stride[2];
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = b->n[a];
+    g.bc[a][0] = b->bc[a][0];
+    g.bc[a][1] = b->bc[a][1];
+  }
+  g.gz = (dim == 3) ? NG : 0;
+  return g;
+}
+
+StepConst step_const(const hydro_params_t* p, const double dx[3], double dt) {
+  StepConst K;
+  K.gamma = p->gamma;
+  K.gm1 = p->gamma - 1.0;
+  K.gm1inv = 1.0 / (p->gamma - 1.0);
+  K.small_dens = p->small_dens;
+  K.small_pres = p->small_pres;
+  for (int a = 0; a < 3; ++a) K.grav[a] = p->grav[a];
+  K.dt = dt;
+  K.hdt = 0.5 * dt;
+  for (int a = 0; a < 3; ++a) K.dtdx[a] = (a < p->dim) ? dt / dx[a] : 0.0;
+  K.dim = p->dim;
+  K.flatten = (p->flags & HYDRO_FLAG_NO_FLATTEN) ? 0 : 1;
+  K.has_grav = (p->grav[0] != 0.0 || p->grav[1] != 0.0 || p->grav[2] != 0.0) ? 1 : 0;
+  return K;
+}
+
+// scratch geometry of a box of interior n (contiguous, rows padded to even length)
+ScratchGeom scratch_geom(const int n[3], int dim) {
+  ScratchGeom sg;
+  long long gx = n[0] + 2 * NG, gy = n[1] + 2 * NG, gz = (dim == 3) ? n[2] + 2 * NG : 1;
+  sg.sy = (gx + 1) & ~1LL;
+  sg.sz = sg.sy * gy;
+  sg.sc = sg.sz * gz;
+  sg.gz = (dim == 3) ? NG : 0;
+  return sg;
+}
+
+Scratch carve_scratch(double* base, long long sc) {
+  Scratch s;
+  double* p = base;
+  auto take = [&](int nf) { double* r = p; p += (long long)nf * sc; return r; };
+  s.Q = take(NQ);
+  for (int d = 0; d < 3; ++d) s.TM[d] = take(5);
+  for (int d = 0; d < 3; ++d) s.TP[d] = take(5);
+  for (int d = 0; d < 3; ++d) s.F1[d] = take(5);
+  for (int d = 0; d < 3; ++d)
+    for (int t = 0; t < 3; ++t) s.F2[d][t] = (t == d) ? nullptr : take(5);
+  for (int d = 0; d < 3; ++d) s.F3[d] = take(5);
+  return s;
+}
+
+int ensure_scratch(hydro_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return HYDRO_OK;
+  if (ctx->scratch) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return HYDRO_ECUDA;
+    cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+  }
+  if (ctx->fail_alloc) return HYDRO_ENOMEM;
+  if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->scratch = nullptr;
+    return HYDRO_ENOMEM;
+  }
+  ctx->scratch_bytes = bytes;
+  return HYDRO_OK;
+}
+
+// copy the flag block to the host after the stream drains; clears the bad flag
+int read_flags(hydro_ctx* ctx, cudaStream_t st, DevFlags* host) {
+  if (cudaMemcpyAsync(host, ctx->flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return HYDRO_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
+  if (host->bad) {
+    if (cudaMemsetAsync(&ctx->flags->bad, 0, sizeof(int), st) != cudaSuccess) return HYDRO_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
+  }
+  return HYDRO_OK;
+}
+
+// after a profiled step: wait for it and add its stage durations
+int collect_stage_times(hydro_ctx* ctx, cudaStream_t st) {
+  if (cudaEventSynchronize(ctx->events[NSTAGES]) != cudaSuccess) return HYDRO_ECUDA;
+  for (int s = 0; s < NSTAGES; ++s) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->events[s], ctx->events[s + 1]) != cudaSuccess) return HYDRO_ECUDA;
+    ctx->stage_ms[s] += ms;
+  }
+  ctx->stage_calls += 1;
+  (void)st;
+  return HYDRO_OK;
+}
+
+}  // namespace hydro
+
+extern "C" {
+
+const char* hydro_strerror(int s) {
+  switch (s) {
+    case HYDRO_OK: return "ok";
+    case HYDRO_EINVAL: return "invalid argument";
+    case HYDRO_ENOMEM: return "out of memory";
+    case HYDRO_ECUDA: return "CUDA runtime error";
+    case HYDRO_EBADSTATE: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
+    case HYDRO_EAGAIN: return "not ready";
+    case HYDRO_ETIMEDOUT: return "timed out";
+    case HYDRO_ENOTIMPL: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+int hydro_ctx_create(hydro_ctx_t** out, int device) {
+  if (!out) return HYDRO_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return HYDRO_ECUDA;
+  }
+  DeviceGuard g(device);
+  if (!g.ok) return HYDRO_ECUDA;
+  hydro_ctx* ctx = new (std::nothrow) hydro_ctx();
+  if (!ctx) return HYDRO_ENOMEM;
+  ctx->device = device;
+  if (cudaMalloc(&ctx->flags, sizeof(DevFlags)) != cudaSuccess ||
+      cudaMemset(ctx->flags, 0, sizeof(DevFlags)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->flags) cudaFree(ctx->flags);
+    delete ctx;
+    return HYDRO_ENOMEM;
+  }
+  *out = ctx;
+  return HYDRO_OK;
+}
+
+void hydro_ctx_destroy(hydro_ctx_t* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->flags) cudaFree(ctx->flags);
+  for (auto& e : ctx->events)
+    if (e) cudaEventDestroy(e);
+  hydro_batch_release(ctx);
+  delete ctx;
+}
+
+int hydro_ctx_check(hydro_ctx_t* ctx) {
+  if (!ctx) return HYDRO_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HYDRO_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return HYDRO_ECUDA;
+  int bad = 0;
+  if (cudaMemcpy(&bad, &ctx->flags->bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HYDRO_ECUDA;
+  if (bad) {
+    if (cudaMemset(&ctx->flags->bad, 0, sizeof(int)) != cudaSuccess) return HYDRO_ECUDA;
+    return HYDRO_EBADSTATE;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_dt(hydro_ctx_t* ctx, const hydro_box_t* box, const hydro_params_t* params, double* dt_host,
+             void* stream) {
+  if (!ctx || !dt_host || !valid_params(params) || !valid_box(box, params->dim)) return HYDRO_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HYDRO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  StepConst K = step_const(params, box->dx, 1.0);
+  BoxGeom bg = geom_of(box, params->dim);
+  if (launch_dt(bg, K, box->dx, params->cfl, ctx->flags, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+  DevFlags h;
+  int rc = read_flags(ctx, st, &h);
+  if (rc) return rc;
+  *dt_host = h.dt_next;
+  return h.bad ? HYDRO_EBADSTATE : HYDRO_OK;
+}
+
+int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                      const hydro_params_t* params, double dt, double* dt_next_host, void* stream) {
+  if (!ctx || !valid_params(params)) return HYDRO_EINVAL;
+  const int dim = params->dim;
+  if (!valid_box(in, dim) || !out || !out->u || out->ng != NG) return HYDRO_EINVAL;
+  if (reinterpret_cast<uintptr_t>(out->u) % sizeof(double)) return HYDRO_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (out->n[a] != in->n[a]) return HYDRO_EINVAL;
+  {
+    hydro_box_t o = *out;
+    for (int a = 0; a < 3; ++a) { o.dx[a] = in->dx[a]; o.bc[a][0] = o.bc[a][1] = HYDRO_BC_PREFILLED; }
+    if (!valid_box(&o, dim)) return HYDRO_EINVAL;
+    if (boxes_overlap(in, &o, dim)) return HYDRO_EINVAL;
+  }
+  if (!(dt > 0.0) || !std::isfinite(dt)) return HYDRO_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HYDRO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  StepArgs a;
+  a.in = geom_of(in, dim);
+  a.out = geom_of(out, dim);
+  a.sg = scratch_geom(in->n, dim);
+  size_t bytes = (size_t)a.sg.sc * SCRATCH_FIELDS * sizeof(double);
+  int rc = ensure_scratch(ctx, bytes);
+  if (rc) return rc;
+  a.s = carve_scratch(ctx->scratch, a.sg.sc);
+  a.K = step_const(params, in->dx, dt);
+  for (int d = 0; d < 3; ++d) a.dx[d] = in->dx[d];
+  a.cfl = params->cfl;
+  a.flags = ctx->flags;
+  a.events = ctx->profiling ? ctx->events : nullptr;
+  if (launch_step(a, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+  if (ctx->profiling) {
+    rc = collect_stage_times(ctx, st);
+    if (rc) return rc;
+  }
+  if (dt_next_host) {
+    DevFlags h;
+    rc = read_flags(ctx, st, &h);
+    if (rc) return rc;
+    *dt_next_host = h.dt_next;
+    if (h.bad) return HYDRO_EBADSTATE;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_ctx_set_profiling(hydro_ctx_t* ctx, int enable) {
+  if (!ctx) return HYDRO_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HYDRO_ECUDA;
+  if (enable && !ctx->events[0]) {
+    for (auto& e : ctx->events)
+      if (cudaEventCreate(&e) != cudaSuccess) return HYDRO_ECUDA;
+  }
+  ctx->profiling = enable ? 1 : 0;
+  for (double& m : ctx->stage_ms) m = 0.0;
+  ctx->stage_calls = 0;
+  return HYDRO_OK;
+}
+
+int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* calls) {
+  if (!ctx || !ms || nmax < 0) return HYDRO_EINVAL;
+  for (int s = 0; s < nmax && s < NSTAGES; ++s) ms[s] = ctx->stage_ms[s];
+  if (calls) *calls = ctx->stage_calls;
+  return NSTAGES;
+}
+
+long long hydro_ctx_launches(const hydro_ctx_t* ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// Internal declarations shared by the C-ABI translation units.
+#pragma once
+#include <cstddef>
+
+#include "hydro.h"
+#include "hydro_step.cuh"
+
+struct hydro_batch_state;
+
+struct hydro_ctx {
+  int device = 0;
+  double* scratch = nullptr;      // staged-step intermediates (grown on demand)
+  size_t scratch_bytes = 0;
+  hydro::DevFlags* flags = nullptr;
+  int fail_alloc = 0;             // test hook: make the next scratch allocation fail
+  hydro_batch_state* batch = nullptr;
+  long long launches = 0;         // kernels enqueued by this context
+  int profiling = 0;              // record stage events around each step
+  cudaEvent_t events[hydro::NSTAGES + 1] = {};
+  double stage_ms[hydro::NSTAGES] = {};
+  long long stage_calls = 0;
+};
+
+void hydro_batch_release(hydro_ctx* ctx);
+
+namespace hydro {
+bool valid_params(const hydro_params_t* p);
+bool valid_box(const hydro_box_t* b, int dim);
+bool boxes_overlap(const hydro_box_t* a, const hydro_box_t* b, int dim);
+BoxGeom geom_of(const hydro_box_t* b, int dim);
+StepConst step_const(const hydro_params_t* p, const double dx[3], double dt);
+ScratchGeom scratch_geom(const int n[3], int dim);
+Scratch carve_scratch(double* base, long long sc);
+int ensure_scratch(hydro_ctx* ctx, size_t bytes);
+int read_flags(hydro_ctx* ctx, cudaStream_t st, DevFlags* host);
+int collect_stage_times(hydro_ctx* ctx, cudaStream_t st);
+}  // namespace hydro

@@ -1,0 +1,93 @@
+// Staged CTU-PPM step kernels (FP64, sm_103a).
+//
+// B300's FP64 pipe issues roughly 1.6 lane-operations per clock per SM (a
+// divide or square root costs about 8.6 of those slots) while the FP32/INT
+// pipes and HBM have ~75x and ~100x more headroom.  The step is therefore
+// laid out for zero redundant FP64 work rather than minimum memory traffic:
+// every intermediate (primitive state, traced face states, first,
+// intermediate and final fluxes) is computed exactly once over the range its
+// consumers need and kept in device scratch (L2-resident for small boxes).
+//
+// Ranges (zone coordinates, interior [0, n) per axis, ghosts to [-4, n+4)):
+//   prim            grown box (ghost zones mapped from the interior by BC kind)
+//   trace (per d)   zones [-1, n] on every active axis
+//   F1_d            d-faces [0, n_d] x transverse [-1, n]
+//   F2_{d|t} (3-D)  d-faces [0, n_d] x t in [0, n_t) x third axis [-1, n]
+//   F3_d            d-faces [0, n_d] x transverse interior
+//   update          interior
+// A face f along d is stored at the position of zone f (between f-1 and f).
+#pragma once
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+// geometry of a grown box with arbitrary element strides
+struct BoxGeom {
+  double* u;
+  long long sy, sz, sc;  // row, plane, component strides (elements)
+  int n[3];
+  int gz;                // ghost zones in z: 4 in 3-D, 0 in 2-D
+  int bc[3][2];
+  __host__ __device__ long long id(int i, int j, int k) const {
+    return (long long)(k + gz) * sz + (long long)(j + NG) * sy + (i + NG);
+  }
+};
+
+// geometry of the contiguous scratch arrays (same zone indexing)
+struct ScratchGeom {
+  long long sy, sz, sc;
+  int gz;
+  __host__ __device__ long long id(int i, int j, int k) const {
+    return (long long)(k + gz) * sz + (long long)(j + NG) * sy + (i + NG);
+  }
+};
+
+struct Range {
+  int lo[3];
+  int ext[3];
+  long long count() const { return (long long)ext[0] * ext[1] * ext[2]; }
+};
+
+// scratch field bases
+struct Scratch {
+  double* Q;          // NQ fields
+  double* TM[3];      // traced state at each zone's low face, 5 fields
+  double* TP[3];      // traced state at each zone's high face, 5 fields
+  double* F1[3];      // first fluxes
+  double* F2[3][3];   // intermediate fluxes F^{d|t}
+  double* F3[3];      // final fluxes
+};
+
+// number of scratch fields (each one grown box of doubles)
+constexpr int SCRATCH_FIELDS = NQ + 3 * 5 + 3 * 5 + 3 * 5 + 6 * 5 + 3 * 5;
+
+// device reduction / flag block owned by a context
+struct DevFlags {
+  unsigned long long maxspeed[3];  // bit patterns of max over zones of |u_d| + c (non-negative doubles)
+  int bad;                         // sticky non-physical-state flag
+  int pad;
+  double dt_next;                  // cfl * min_d dx_d / maxspeed_d
+};
+
+// stages of a step, timed separately when a context profiles
+enum Stage { ST_PRIM = 0, ST_TRACE = 1, ST_FLUX1 = 2, ST_FLUX2 = 3, ST_FLUX3 = 4, ST_UPDATE = 5, NSTAGES = 6 };
+
+struct StepArgs {
+  BoxGeom in, out;
+  ScratchGeom sg;
+  Scratch s;
+  StepConst K;
+  double dx[3];
+  double cfl;
+  DevFlags* flags;
+  cudaEvent_t* events;   // NSTAGES + 1 events recorded at stage boundaries, or null
+};
+
+// enqueue one step (all kernels) on `stream`; adds the number of kernels
+// launched to *launches
+cudaError_t launch_step(const StepArgs& a, cudaStream_t stream, long long* launches);
+// enqueue a CFL estimate of the interior of a box into flags->dt_next
+cudaError_t launch_dt(const BoxGeom& box, const StepConst& K, const double dx[3], double cfl, DevFlags* flags,
+                      cudaStream_t stream, long long* launches);
+
+}  // namespace hydro

@@ -1,0 +1,203 @@
+"""Parity of the CUDA CTU-PPM step (through the C ABI) with the CPU oracle.
+
+Tolerances (normwise relative L-infinity per conserved field, max|g-o|/max|o|):
+  * contraction-free build (libhydro_exact.so): bitwise equal to the oracle —
+    both evaluate the same FP64 operations in the same order;
+  * product build (multiply-add contraction on): <= 1e-10 after one step and
+    <= 1e-8 after 100 steps; conserved totals to 1e-13 relative.
+Boxes span several thread blocks and ragged sizes (not multiples of 32 or 128).
+"""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import gpu_steps, interior, oracle_params, rel_linf, to_dev
+from paper_1711_06203_b300 import binding as hb
+from paper_1711_06203_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+O, R, PER, PRE = hb.BC_OUTFLOW, hb.BC_REFLECT, hb.BC_PERIODIC, hb.BC_PREFILLED
+
+
+def _case(name):
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    if name == "sod2d":
+        n, dim = (64, 64), 2
+        return inputs.sod(64, 2, 0), dim, n, (1 / 64,) * 3, O, 1.4, (0, 0, 0), True
+    if name == "random2d_periodic":
+        n, dim = (37, 29), 2
+        return inputs.random_box(rng, (37, 29, 1), 2), dim, n, (1 / 37, 1 / 29, 1.0), PER, 5 / 3, (0, 0, 0), True
+    if name == "random3d_prefilled":
+        n, dim = (21, 13, 10), 3
+        return inputs.random_box(rng, n, 3), dim, n, (1 / 21, 1 / 13, 1 / 10), PRE, 5 / 3, (0, 0, 0), True
+    if name == "random3d_periodic_noflat":
+        n, dim = (16, 12, 9), 3
+        return inputs.random_box(rng, n, 3), dim, n, (1 / 16,) * 3, PER, 5 / 3, (0, 0, 0), False
+    if name == "sedov3d":
+        U, _ = inputs.sedov(24)
+        return U, 3, (24, 24, 24), (1 / 24,) * 3, O, 1.4, (0, 0, 0), True
+    if name == "stratified3d_gravity":
+        U = inputs.stratified(16, 3, 5 / 3, 1.0, 0.1, perturb=1e-3, rng=rng)
+        bc = ((PER, PER), (PER, PER), (R, R))
+        return U, 3, (16, 16, 16), (1 / 16,) * 3, bc, 5 / 3, (0.0, 0.0, -1.0), True
+    if name == "mixed_bc3d":
+        n = (18, 11, 13)
+        bc = ((O, R), (R, O), (PRE, O))
+        return inputs.random_box(rng, n, 3), 3, n, (0.05, 0.07, 0.06), bc, 1.4, (0.3, -0.2, 0.1), True
+    raise KeyError(name)
+
+
+CASES = ["sod2d", "random2d_periodic", "random3d_prefilled", "random3d_periodic_noflat", "sedov3d",
+         "stratified3d_gravity", "mixed_bc3d"]
+
+
+def _oracle_dt(U, dim, n, dx, bc, gamma, grav, flat):
+    P = oracle_params(dim, n, dx, bc, gamma, grav=grav, flatten=flat)
+    d, rc = oracle.dt(U, P)
+    assert rc == 0
+    return P, d
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_exact_build_is_bitwise_equal_to_oracle(name):
+    U, dim, n, dx, bc, gamma, grav, flat = _case(name)
+    P, d = _oracle_dt(U, dim, n, dx, bc, gamma, grav, flat)
+    ref, rc = oracle.step(U, P, d)
+    assert rc == 0
+    got, nxt = gpu_steps(U, dim, n, dx, bc, gamma, [d], grav=grav, flatten=flat, variant="exact")
+    gi, ri = interior(got, dim), interior(ref, dim)
+    bad = np.argwhere(gi != ri)
+    assert bad.size == 0, f"{len(bad)} zones differ; first {bad[:5].tolist()} max {np.abs(gi - ri).max()}"
+    dref, _ = oracle.dt(ref, P)
+    assert nxt[0] == dref
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_one_step_parity(name):
+    U, dim, n, dx, bc, gamma, grav, flat = _case(name)
+    P, d = _oracle_dt(U, dim, n, dx, bc, gamma, grav, flat)
+    ref, _ = oracle.step(U, P, d)
+    got, nxt = gpu_steps(U, dim, n, dx, bc, gamma, [d], grav=grav, flatten=flat)
+    err = rel_linf(interior(got, dim), interior(ref, dim))
+    assert np.all(err <= 1e-10), err
+    dref, _ = oracle.dt(ref, P)
+    assert abs(nxt[0] - dref) <= 1e-10 * dref
+
+
+@pytest.mark.parametrize("name,steps", [("sod2d", 100), ("random3d_periodic_noflat", 100), ("sedov3d", 100)])
+def test_many_step_parity(name, steps):
+    U, dim, n, dx, bc, gamma, grav, flat = _case(name)
+    P = oracle_params(dim, n, dx, bc, gamma, grav=grav, flatten=flat)
+    # both sides take the same time steps (the oracle's), so only the arithmetic differs
+    ref, t, dts = oracle.run(U, P, steps)
+    got, _ = gpu_steps(U, dim, n, dx, bc, gamma, dts, grav=grav, flatten=flat)
+    err = rel_linf(interior(got, dim), interior(ref, dim))
+    assert np.all(err <= 1e-8), err
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_conservation_on_gpu(dim):
+    rng = np.random.default_rng(7 + dim)
+    n = (33, 17, 11) if dim == 3 else (45, 23, 1)
+    U = inputs.random_box(rng, n, dim)
+    dx = (1 / 33, 1 / 17, 1 / 11)
+    P = oracle_params(dim, n, dx, PER, 5 / 3)
+    U0 = oracle.fill_ghosts(U, P)
+    d, _ = oracle.dt(U, P)
+    got, _ = gpu_steps(U, dim, n, dx, PER, 5 / 3, [d, d, d])
+    g, u0 = interior(got, dim), interior(U0, dim)
+    tot0, tot = u0.reshape(5, -1).sum(1), g.reshape(5, -1).sum(1)
+    mag = np.abs(u0).reshape(5, -1).sum(1)
+    rel = np.abs(tot - tot0) / np.where(mag > 0, mag, 1.0)
+    assert np.all(rel <= 1e-13), rel
+
+
+def test_hydro_dt_matches_oracle():
+    rng = np.random.default_rng(3)
+    n = (19, 23, 7)
+    U = inputs.random_box(rng, n, 3)
+    dx = (0.1, 0.07, 0.13)
+    P = oracle_params(3, n, dx, PRE, 5 / 3, cfl=0.8)
+    dref, _ = oracle.dt(U, P)
+    for variant in ("exact", "default"):
+        ctx = hb.Context(0, variant)
+        a = to_dev(U)
+        d = ctx.hydro_dt(hb.box(a, n, dx, PRE), hb.params(3, gamma=5 / 3, cfl=0.8))
+        ctx.close()
+        if variant == "exact":
+            assert d == dref
+        else:
+            assert abs(d - dref) <= 1e-14 * dref
+
+
+def test_bad_state_is_reported():
+    rng = np.random.default_rng(1)
+    n = (12, 12, 12)
+    U = inputs.random_box(rng, n, 3)
+    U[0, 8, 8, 8] = -1.0  # negative density in the interior
+    ctx = hb.Context(0)
+    a = to_dev(U)
+    b = torch.empty_like(a)
+    p = hb.params(3, gamma=5 / 3)
+    rc, _ = ctx.hydro_advance_box(hb.box(a, n, (0.1,) * 3, PRE), hb.box(b, n, (0.1,) * 3, PRE), p, 1e-3,
+                                  want_dt_next=True, raise_on_error=False)
+    assert rc == hb.HYDRO_EBADSTATE
+    # asynchronous form: recorded in the context, reported by hydro_ctx_check, then cleared
+    ctx.hydro_advance_box(hb.box(a, n, (0.1,) * 3, PRE), hb.box(b, n, (0.1,) * 3, PRE), p, 1e-3)
+    assert ctx.hydro_ctx_check() == hb.HYDRO_EBADSTATE
+    assert ctx.hydro_ctx_check() == hb.HYDRO_OK
+    with pytest.raises(hb.HydroError) as e:
+        ctx.hydro_dt(hb.box(a, n, (0.1,) * 3, PRE), p)
+    assert e.value.status == hb.HYDRO_EBADSTATE
+    ctx.close()
+
+
+def test_invalid_arguments_are_rejected():
+    ctx = hb.Context(0)
+    U = inputs.random_box(np.random.default_rng(0), (8, 8, 8), 3)
+    a = to_dev(U)
+    b = torch.empty_like(a)
+    p = hb.params(3, gamma=5 / 3)
+    good_in, good_out = hb.box(a, (8, 8, 8), (0.1,) * 3, PRE), hb.box(b, (8, 8, 8), (0.1,) * 3, PRE)
+    cases = []
+    x = hb.box(a, (8, 8, 8), (0.1,) * 3, PRE); x.ng = 3; cases.append((x, good_out, p, 1e-3))
+    x = hb.box(a, (8, 8, 8), (0.0, 0.1, 0.1), PRE); cases.append((x, good_out, p, 1e-3))
+    x = hb.box(a, (8, 8, 8), (0.1,) * 3, PRE); x.bc[0][0] = hb.BC_PERIODIC; cases.append((x, good_out, p, 1e-3))
+    x = hb.box(a, (8, 8, 8), (0.1,) * 3, PRE); x.stride[0] = 4; cases.append((x, good_out, p, 1e-3))
+    cases.append((good_in, good_in, p, 1e-3))  # in == out overlaps
+    cases.append((good_in, good_out, p, -1.0))  # negative dt
+    bad_p = hb.params(3, gamma=1.0); cases.append((good_in, good_out, bad_p, 1e-3))
+    bad_p = hb.params(4, gamma=1.4); cases.append((good_in, good_out, bad_p, 1e-3))
+    o2 = hb.box(b, (8, 8, 7), (0.1,) * 3, PRE); cases.append((good_in, o2, p, 1e-3))
+    for bi, bo, pp, dt in cases:
+        rc, _ = ctx.hydro_advance_box(bi, bo, pp, dt, want_dt_next=True, raise_on_error=False)
+        assert rc == hb.HYDRO_EINVAL
+    ctx.close()
+
+
+def test_strided_boxes_and_streams():
+    """Input and output with different padded strides, on a side stream."""
+    rng = np.random.default_rng(12)
+    n = (14, 10, 9)
+    U = inputs.random_box(rng, n, 3)
+    P = oracle_params(3, n, (0.1,) * 3, PRE, 5 / 3)
+    d, _ = oracle.dt(U, P)
+    ref, _ = oracle.step(U, P, d)
+    big = torch.zeros((5, 17 + 2, 18 + 3, 22 + 6), dtype=torch.float64, device="cuda")
+    a = big[:, 1:18, 2:20, 3:25]
+    a.copy_(to_dev(U))
+    out = torch.zeros((5, 17, 18, 24), dtype=torch.float64, device="cuda")[:, :, :, 1:23]
+    ctx = hb.Context(0)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx.hydro_advance_box(hb.box(a, n, (0.1,) * 3, PRE), hb.box(out, n, (0.1,) * 3, PRE),
+                              hb.params(3, gamma=5 / 3), d, stream=s)
+    s.synchronize()
+    got = out.cpu().numpy()
+    err = rel_linf(got[:, 4:-4, 4:-4, 4:-4], ref[:, 4:-4, 4:-4, 4:-4])
+    assert np.all(err <= 1e-10), err
+    ctx.close()

@@ -529,3 +529,36 @@ def test_hydrostatic_atmosphere_stays_near_rest():
         p = (5 / 3 - 1) * (q[4] - 0.5 * rho * vel ** 2)
         machs.append((vel / np.sqrt(5 / 3 * p / rho)).max())
     assert machs[0] < 1e-3 and machs[1] < machs[0] / 2.0, machs
+
+
+def test_ghost_fill_kinds_and_corner_composition():
+    """Outflow copies the nearest interior zone, reflect mirrors with the normal
+    momentum negated, periodic wraps; a prefilled face keeps caller data and a
+    derived face fills its ghost slab over that data (the maps compose)."""
+    n = (6, 5, 7)
+    rng = np.random.default_rng(21)
+    U = rng.normal(size=(5,) + inputs.grown_shape(n, 3))
+    bc = ((oracle.BC_OUTFLOW, oracle.BC_REFLECT), (oracle.BC_PERIODIC, oracle.BC_PERIODIC),
+          (oracle.BC_PREFILLED, oracle.BC_OUTFLOW))
+    P = oracle.params(3, n, bc=bc)
+    W = oracle.fill_ghosts(U, P)
+    g = 4
+    z = lambda k: k + g
+    y = lambda j: j + g
+    x = lambda i: i + g
+    for c in range(5):
+        # x low outflow, x high reflect (x-momentum negated)
+        assert W[c, z(2), y(1), x(-3)] == U[c, z(2), y(1), x(0)]
+        sgn = -1 if c == 1 else 1
+        assert W[c, z(2), y(1), x(6)] == sgn * U[c, z(2), y(1), x(5)]
+        assert W[c, z(2), y(1), x(9)] == sgn * U[c, z(2), y(1), x(2)]
+        # y periodic
+        assert W[c, z(3), y(-1), x(2)] == U[c, z(3), y(4), x(2)]
+        assert W[c, z(3), y(5), x(2)] == U[c, z(3), y(0), x(2)]
+        # z low prefilled: untouched; z high outflow
+        assert W[c, z(-2), y(1), x(1)] == U[c, z(-2), y(1), x(1)]
+        assert W[c, z(8), y(1), x(1)] == U[c, z(6), y(1), x(1)]
+        # corners: x-outflow over the prefilled z layer, reflect x periodic y, outflow z over all
+        assert W[c, z(-2), y(1), x(-1)] == U[c, z(-2), y(1), x(0)]
+        assert W[c, z(0), y(-2), x(7)] == sgn * U[c, z(0), y(3), x(4)]
+        assert W[c, z(9), y(-1), x(-2)] == U[c, z(6), y(4), x(0)]
