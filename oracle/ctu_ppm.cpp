@@ -223,14 +223,12 @@ real mc_slope(const real* a, int m) {
   real lim = rmin(fabs(da), rmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
   return copysign(lim, da);
 }
-/* interface value a_{m+1/2} (CW84 eq. 1.6 on a uniform grid) */
-real face_value(const real* a, int m) {
-  return 0.5 * (a[m] + a[m + 1]) - SIXTH * (mc_slope(a, m + 1) - mc_slope(a, m));
-}
-/* limited, flattened parabola of the zone at index 3: edge values am, ap and a6 */
-void ppm_parabola(const real* a, real chi, real* am, real* ap, real* a6) {
-  real ai = a[3];
-  real aP = face_value(a, 3), aM = face_value(a, 2);
+/* interface value a_{m+1/2} between zones m and m+1 from their averages and
+ * monotonised slopes (CW84 eq. 1.6 on a uniform grid) */
+real face_value(real a0, real a1, real s0, real s1) { return 0.5 * (a0 + a1) - SIXTH * (s1 - s0); }
+/* limited, flattened parabola of a zone with average ai and interface values
+ * aM (low) and aP (high): edge values am, ap and a6 */
+void ppm_limit(real ai, real aM, real aP, real chi, real* am, real* ap, real* a6) {
   /* CW84 eq. 1.10: local extremum -> constant; overshooting parabola -> steepen
    * the opposite edge.  The two tests (a+-a)(a-a-) <= 0 and D*M > D^2/6 are
    * written as sign tests, which are their exact-arithmetic meaning. */
@@ -249,6 +247,11 @@ void ppm_parabola(const real* a, real chi, real* am, real* ap, real* a6) {
   aM = chi * aM + (1.0 - chi) * ai;
   *am = aM; *ap = aP; *a6 = 6.0 * (ai - 0.5 * (aM + aP));
 }
+/* the same for the zone at index 3 of a 7-point line (unit pins) */
+void ppm_parabola(const real* a, real chi, real* am, real* ap, real* a6) {
+  real s2 = mc_slope(a, 2), s3 = mc_slope(a, 3), s4 = mc_slope(a, 4);
+  ppm_limit(a[3], face_value(a[2], a[3], s2, s3), face_value(a[3], a[4], s3, s4), chi, am, ap, a6);
+}
 /* averages of the parabola over the domains swept by a wave of Courant number
  * sigma toward the high (I+) and low (I-) face (CW84 eqs. 1.12) */
 real integ_plus(real am, real ap, real a6, real s) {
@@ -258,22 +261,17 @@ real integ_minus(real am, real ap, real a6, real s) {
   return am + 0.5 * s * ((ap - am) + (1.0 - TWOTHIRDS * s) * a6);
 }
 
-/* ---- Steps 4-6 for one zone and direction d: flatten, reconstruct, trace ----
- * Q holds the 6 primitive fields (rho,u,v,w,p,c) on the grown box.
- * Outputs the primitive states at the zone's low face (qm) and high face (qp)
- * at t^{n+1/2}, components in absolute order (rho, u, v, w, p). */
-void trace_zone(const std::vector<real>* Q, long id, long st, int d, const oracle_params& P,
-                real dtdx, real dt, real qm[5], real qp[5]) {
+/* ---- Step 6 for one zone and direction d: characteristic tracing ----
+ * am, ap, a6: the zone's limited parabolas of (rho, un, ut1, ut2, p);
+ * zone: its averages of the same five variables; Q, id: its sound speed and
+ * eigenvector coefficients.  Outputs the primitive states at the zone's low
+ * face (qm) and high face (qp) at t^{n+1/2}, components in absolute order
+ * (rho, u, v, w, p). */
+void trace_from_parabola(const real am[5], const real ap[5], const real a6[5], const real zone[5],
+                         const std::vector<real>* Q, long id, int d, const oracle_params& P, real dtdx, real dt,
+                         real qm[5], real qp[5]) {
   const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-  const int vmap[5] = {QRHO, QU + d, QU + t1, QU + t2, QP}; /* rho, un, ut1, ut2, p */
-  real line[5][7];
-  for (int v = 0; v < 5; ++v)
-    for (int m = 0; m < 7; ++m) line[v][m] = Q[vmap[v]][id + (m - 3) * st];
-  real chi = P.flatten ? flat_coef(line[4], line[1], P.small_pres) : real(1.0);
-  real am[5], ap[5], a6[5];
-  for (int v = 0; v < 5; ++v) ppm_parabola(line[v], chi, &am[v], &ap[v], &a6[v]);
-
-  real un = line[1][3], c = Q[QC][id];
+  real un = zone[1], c = Q[QC][id];
   /* eigenvectors of the primitive (rho, un, p) system at the zone state:
    *   r- = (1, -c/rho, c^2), r0 = (1, 0, 0), r+ = (1, c/rho, c^2)
    *   l- = (0, -rho/(2c), 1/(2c^2)), l0 = (1, 0, -1/c^2), l+ = (0, rho/(2c), 1/(2c^2)) */
@@ -294,7 +292,7 @@ void trace_zone(const std::vector<real>* Q, long id, long st, int d, const oracl
       return side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
     };
     real ref[5];
-    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : line[v][3];
+    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : zone[v];
     /* wave strengths beta = l . (ref - I(sigma_nu)) of the waves that reach the face */
     real bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
     if (reach[0]) bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
@@ -318,6 +316,64 @@ void trace_zone(const std::vector<real>* Q, long id, long st, int d, const oracl
     s_p = rmax(s_p, real(P.small_pres));
     real* out = side ? qp : qm;
     out[0] = s_rho; out[1 + d] = s_un; out[1 + t1] = s_t1; out[1 + t2] = s_t2; out[4] = s_p;
+  }
+}
+
+struct Fields {
+  /* 5-component arrays on the grown box */
+  std::vector<real> a;
+  long sc;
+  void init(long sc_) { sc = sc_; a.assign(5 * sc_, real(0.0)); }
+  void get(long id, real v[5]) const { for (int c = 0; c < 5; ++c) v[c] = a[c * sc + id]; }
+  void put(long id, const real v[5]) { for (int c = 0; c < 5; ++c) a[c * sc + id] = v[c]; }
+};
+
+/* ---- Steps 4-6 along one pencil in direction d ----
+ * The pencil holds zones -4 .. n_d+3 at (transverse) position `base`; every
+ * flattening coefficient, slope and interface value is formed once, then
+ * each zone in [-1, n_d] gets its parabolas and traced face states. */
+void trace_pencil(const std::vector<real>* Q, long base, long st, int nd, int d, const oracle_params& P,
+                  real dtdx, real dt, Fields& TM, Fields& TP) {
+  const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+  const int vmap[5] = {QRHO, QU + d, QU + t1, QU + t2, QP}; /* rho, un, ut1, ut2, p */
+  const int len = nd + 2 * NG, off = NG;                   /* index of zone j is j + off */
+  std::vector<real> a[5], slope[5], face[5];
+  for (int v = 0; v < 5; ++v) {
+    a[v].resize(len);
+    for (int m = 0; m < len; ++m) a[v][m] = Q[vmap[v]][base + (long)(m - off) * st];
+  }
+  /* CW84 flattening: chi~ on zones [-2, n+1], chi on zones [-1, n] */
+  std::vector<real> chit(len, real(1.0)), chi(len, real(1.0));
+  if (P.flatten) {
+    for (int j = -2; j <= nd + 1; ++j) chit[j + off] = flat_tilde(a[4].data(), a[1].data(), j + off, P.small_pres);
+    for (int j = -1; j <= nd; ++j) {
+      int m = j + off;
+      real dp1 = a[4][m + 1] - a[4][m - 1];
+      int s = (dp1 < 0.0) ? 1 : -1; /* the neighbour on the high-pressure side */
+      chi[m] = rmin(chit[m], chit[m + s]);
+    }
+  }
+  /* slopes on zones [-2, n+1]; interface j+1/2 for j in [-2, n] stored at j */
+  for (int v = 0; v < 5; ++v) {
+    slope[v].assign(len, real(0.0));
+    face[v].assign(len, real(0.0));
+    for (int j = -2; j <= nd + 1; ++j) slope[v][j + off] = mc_slope(a[v].data(), j + off);
+    for (int j = -2; j <= nd; ++j) {
+      int m = j + off;
+      face[v][m] = face_value(a[v][m], a[v][m + 1], slope[v][m], slope[v][m + 1]);
+    }
+  }
+  for (int j = -1; j <= nd; ++j) {
+    int m = j + off;
+    real am[5], ap[5], a6[5], zone[5], qm[5], qp[5];
+    for (int v = 0; v < 5; ++v) {
+      zone[v] = a[v][m];
+      ppm_limit(a[v][m], face[v][m - 1], face[v][m], chi[m], &am[v], &ap[v], &a6[v]);
+    }
+    long id = base + (long)j * st;
+    trace_from_parabola(am, ap, a6, zone, Q, id, d, P, dtdx, dt, qm, qp);
+    TM.put(id, qm);
+    TP.put(id, qp);
   }
 }
 
@@ -375,14 +431,7 @@ void correct_state(const real q[5], const oracle_params& P, const Consts& K, rea
   state_from_cons(U, P, out);
 }
 
-struct Fields {
-  /* 5-component arrays on the grown box */
-  std::vector<real> a;
-  long sc;
-  void init(long sc_) { sc = sc_; a.assign(5 * sc_, real(0.0)); }
-  void get(long id, real v[5]) const { for (int c = 0; c < 5; ++c) v[c] = a[c * sc + id]; }
-  void put(long id, const real v[5]) { for (int c = 0; c < 5; ++c) a[c * sc + id] = v[c]; }
-};
+
 
 bool valid_params(const oracle_params* P) {
   if (!P || (P->dim != 2 && P->dim != 3)) return false;
@@ -494,17 +543,20 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
   Fields TM[3], TP[3];
   for (int d = 0; d < dim; ++d) {
     TM[d].init(N); TP[d].init(N);
+    /* pencils along d through every transverse position in [-1, n] */
+    int ta = (d == 0) ? 1 : 0, tb = (d == 2) ? 1 : 2;
+    int a0 = -1, a1 = g.n[ta], b0 = (tb < dim) ? -1 : 0, b1 = (tb < dim) ? g.n[tb] : 0;
 #ifndef ORACLE_COUNT_FLOPS
-#pragma omp parallel for collapse(2)
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
 #endif
-    for (int k = kz0; k <= kz1; ++k)
-      for (int j = -1; j <= g.n[1]; ++j)
-        for (int i = -1; i <= g.n[0]; ++i) {
-          long id = g.id(i, j, k);
-          real qm[5], qp[5];
-          trace_zone(Q, id, g.str[d], d, *P, dtdx[d], dt, qm, qp);
-          TM[d].put(id, qm); TP[d].put(id, qp);
-        }
+    for (int pb = b0; pb <= b1; ++pb)
+      for (int pa = a0; pa <= a1; ++pa) {
+        int c[3] = {0, 0, 0};
+        c[ta] = pa;
+        c[tb] = pb;
+        c[d] = 0;
+        trace_pencil(Q, g.id(c[0], c[1], c[2]), g.str[d], g.n[d], d, *P, dtdx[d], dt, TM[d], TP[d]);
+      }
   }
 
   STAGE_MARK(2);
@@ -706,8 +758,17 @@ void oracle_trace_lines(const double* lines6x7, int d, const oracle_params* P, d
     Q[QIC2][m] = 1.0 / (c * c);
   }
   real m5[5], p5[5];
-  /* the 7-point lines are laid out contiguously: stride 1 along d */
-  trace_zone(Q, 3, 1, d, *P, dtdx, dt, m5, p5);
+  const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+  const int vmap[5] = {QRHO, QU + d, QU + t1, QU + t2, QP};
+  real line[5][7], am[5], ap[5], a6[5], zone[5];
+  for (int v = 0; v < 5; ++v)
+    for (int m = 0; m < 7; ++m) line[v][m] = Q[vmap[v]][m];
+  real chi = P->flatten ? flat_coef(line[4], line[1], P->small_pres) : real(1.0);
+  for (int v = 0; v < 5; ++v) {
+    ppm_parabola(line[v], chi, &am[v], &ap[v], &a6[v]);
+    zone[v] = line[v][3];
+  }
+  trace_from_parabola(am, ap, a6, zone, Q, 3, d, *P, dtdx, dt, m5, p5);
   for (int c = 0; c < 5; ++c) { qm[c] = double(m5[c]); qp[c] = double(p5[c]); }
 }
 

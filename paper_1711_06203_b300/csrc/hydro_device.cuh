@@ -28,25 +28,54 @@ struct StepConst {
   int dim, flatten, has_grav;
 };
 
-// min/max as explicit selects: ties return the first argument
-__device__ __forceinline__ double dmin(double a, double b) { return (b < a) ? b : a; }
-__device__ __forceinline__ double dmax(double a, double b) { return (a < b) ? b : a; }
-__device__ __forceinline__ bool same_sign_strict(double a, double b) {
-  return (a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0);
+// ---------------------------------------------------------------- comparisons
+// B300's FP64 pipe runs a compare (DSETP) or min/max at the same ~1.6
+// lanes/clock/SM as an FMA, so every comparison of doubles here is done on
+// the integer pipe from the bit pattern.  For finite (and infinite) values
+// these reproduce IEEE comparison exactly, including +0 == -0.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > 0: positive sign and nonzero magnitude
+__device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }
+// x < 0 <=> -x > 0
+__device__ __forceinline__ bool lt0(double x) {
+  return (dbits(x) ^ (long long)0x8000000000000000ULL) > 0;
 }
+__device__ __forceinline__ bool ge0(double x) { return !lt0(x); }
+// order key: monotone in x, equal for +0 and -0
+__device__ __forceinline__ long long okey(double x) {
+  long long b = dbits(x);
+  return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ bool dless(double a, double b) { return okey(a) < okey(b); }
+// min/max as explicit selects: ties return the first argument
+__device__ __forceinline__ double dmin(double a, double b) { return dless(b, a) ? b : a; }
+__device__ __forceinline__ double dmax(double a, double b) { return dless(a, b) ? b : a; }
+// operands known to be >= +0 (magnitudes, pressures, speeds): raw bits order
+__device__ __forceinline__ double dmin_nn(double a, double b) { return dbits(b) < dbits(a) ? b : a; }
+__device__ __forceinline__ double dmax_nn(double a, double b) { return dbits(a) < dbits(b) ? b : a; }
+// |x| > y for y >= +0
+__device__ __forceinline__ bool abs_gt(double x, double y) { return (dbits(x) & 0x7FFFFFFFFFFFFFFFLL) > dbits(y); }
+// a and b nonzero with the same sign
+__device__ __forceinline__ bool same_sign_strict(double a, double b) {
+  long long ba = dbits(a), bb = dbits(b);
+  bool nz = ((ba << 1) != 0) & ((bb << 1) != 0);
+  return nz & ((ba ^ bb) >= 0);
+}
+// finite: exponent field not all ones
+__device__ __forceinline__ bool dfinite(double x) { return ((dbits(x) >> 52) & 0x7FF) != 0x7FF; }
 
 // ---------------------------------------------------------------- EOS
 // conserved -> primitive with floors; sets *bad for a non-physical state
 __device__ __forceinline__ void cons_to_prim_flag(const double U[5], const StepConst& K, double q[5],
                                                   double* inv_out, bool* bad) {
   double rho = U[0];
-  if (!(rho > 0.0 && isfinite(rho))) *bad = true;
+  if (!(gt0(rho) && dfinite(rho))) *bad = true;
   rho = dmax(rho, K.small_dens);
   double inv = 1.0 / rho;
   double u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
   double ke = 0.5 * rho * ((u * u + v * v) + w * w);
   double p = K.gm1 * (U[4] - ke);
-  if (!(p > 0.0 && isfinite(p) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]))) *bad = true;
+  if (!(gt0(p) && dfinite(p) && dfinite(U[1]) && dfinite(U[2]) && dfinite(U[3]))) *bad = true;
   p = dmax(p, K.small_pres);
   q[0] = rho; q[1] = u; q[2] = v; q[3] = w; q[4] = p;
   *inv_out = inv;
@@ -79,45 +108,46 @@ __device__ __forceinline__ void state_from_cons(const double U[5], const StepCon
 }
 
 // ---------------------------------------------------------------- flattening (CW84 App. A)
-// line arrays hold offsets -3..3 about the zone (index 3)
-__device__ __forceinline__ double flat_tilde(const double* p, const double* un, int m, double small_pres) {
-  double dp1 = p[m + 1] - p[m - 1];
-  double dp2 = p[m + 2] - p[m - 2];
-  if (un[m - 1] - un[m + 1] > 0.0 && fabs(dp1) > FLAT_EPS * dmin(p[m + 1], p[m - 1])) {
-    double z = fabs(dp1) / dmax(fabs(dp2), small_pres);
+// chi~ of zone j from p_{j-2..j+2} and the normal velocities u_{j-1}, u_{j+1}
+__device__ __forceinline__ double flat_tilde(double pm2, double pm1, double pp1, double pp2, double um1, double up1,
+                                             double small_pres) {
+  double dp1 = pp1 - pm1;
+  double dp2 = pp2 - pm2;
+  if (gt0(um1 - up1) && abs_gt(dp1, FLAT_EPS * dmin_nn(pp1, pm1))) {
+    double z = fabs(dp1) / dmax_nn(fabs(dp2), small_pres);
     double f = dmax(0.0, dmin(1.0, FLAT_OMEGA2 * (z - FLAT_OMEGA1)));
     return 1.0 - f;
   }
   return 1.0;
 }
 
-__device__ __forceinline__ double flat_coef(const double* p, const double* un, double small_pres) {
-  double dp1 = p[4] - p[2];
-  int s = (dp1 < 0.0) ? 1 : -1;
-  return dmin(flat_tilde(p, un, 3, small_pres), flat_tilde(p, un, 3 + s, small_pres));
-}
-
 // ---------------------------------------------------------------- PPM (CW84 eqs. 1.6-1.10)
-__device__ __forceinline__ double mc_slope(const double* a, int m) {
-  double dl = a[m] - a[m - 1], dr = a[m + 1] - a[m];
+// monotonised centred slope of the middle zone of (am1, a0, ap1)
+__device__ __forceinline__ double mc_slope(double am1, double a0, double ap1) {
+  double dl = a0 - am1, dr = ap1 - a0;
   if (!same_sign_strict(dl, dr)) return 0.0;
-  double da = 0.5 * (a[m + 1] - a[m - 1]);
-  double lim = dmin(fabs(da), dmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
+  double da = 0.5 * (ap1 - am1);
+  // 2 min(|dl|, |dr|) == min(2|dl|, 2|dr|) exactly (doubling is exact)
+  double m2 = 2.0 * dmin_nn(fabs(dl), fabs(dr));
+  double lim = dmin_nn(fabs(da), m2);
   return copysign(lim, da);
 }
 
-__device__ __forceinline__ void ppm_parabola(const double* a, double chi, double& am, double& ap, double& a6) {
-  double ai = a[3];
-  double s2 = mc_slope(a, 2), s3 = mc_slope(a, 3), s4 = mc_slope(a, 4);
-  double aP = 0.5 * (a[3] + a[4]) - SIXTH * (s4 - s3);
-  double aM = 0.5 * (a[2] + a[3]) - SIXTH * (s3 - s2);
+// interface value between zones with averages a0, a1 and slopes s0, s1
+__device__ __forceinline__ double face_value(double a0, double a1, double s0, double s1) {
+  return 0.5 * (a0 + a1) - SIXTH * (s1 - s0);
+}
+
+// limited, flattened parabola of a zone: average ai, interface values aM, aP
+__device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, double chi, double& am, double& ap,
+                                          double& a6) {
   if (!same_sign_strict(aP - ai, ai - aM)) {
     aP = ai; aM = ai;
   } else {
     double D = aP - aM, M = ai - 0.5 * (aM + aP);
     double up = M - SIXTH * D, dn = M + SIXTH * D;
     if (same_sign_strict(D, up)) aM = 3.0 * ai - 2.0 * aP;
-    else if ((D > 0.0 && dn < 0.0) || (D < 0.0 && dn > 0.0)) aP = 3.0 * ai - 2.0 * aM;
+    else if ((gt0(D) && lt0(dn)) || (lt0(D) && gt0(dn))) aP = 3.0 * ai - 2.0 * aM;
   }
   aP = chi * aP + (1.0 - chi) * ai;
   aM = chi * aM + (1.0 - chi) * ai;
@@ -144,7 +174,7 @@ __device__ __forceinline__ void hllc_flux(const double sL[NS], const double sR[N
   double sr = dmax(ul + cl, ur + cr);
   double ml = rl * (sl - ul), mr = rr * (sr - ur);
   double sstar = ((pr - pl) + ml * ul - mr * ur) / (ml - mr);
-  int region = (sl >= 0.0) ? 0 : (sstar >= 0.0) ? 1 : (sr > 0.0) ? 2 : 3;
+  int region = ge0(sl) ? 0 : ge0(sstar) ? 1 : gt0(sr) ? 2 : 3;
   bool left = region <= 1;
   const double* s = left ? sL : sR;
   double rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];

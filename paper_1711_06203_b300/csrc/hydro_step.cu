@@ -65,51 +65,34 @@ __global__ void __launch_bounds__(BLOCK) k_prim(BoxGeom in, ScratchGeom sg, doub
   Q[QIC2 * sg.sc + id] = 1.0 / (c * c);
 }
 
-// ---- stages 2-3: flattening, PPM reconstruction and characteristic tracing along d
+// ---- stage 3 of a zone: characteristic tracing from its parabolas
+// am/ap/a6/zone: (rho, un, ut1, ut2, p); outputs the zone's low- and high-face
+// states to TM/TP at id in absolute component order.
 template <int D>
-__global__ void __launch_bounds__(BLOCK) k_trace(ScratchGeom sg, const double* __restrict__ Q,
-                                                 double* __restrict__ TM, double* __restrict__ TP, StepConst K,
-                                                 Range R) {
-  int i, j, k;
-  if (!range_zone(R, (long long)blockIdx.x * BLOCK + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void trace_zone(const double am[5], const double ap[5], const double a6[5],
+                                           const double zone[5], double c, double rho_c, double c_rho,
+                                           double inv_c2, const StepConst& K, double* __restrict__ TM,
+                                           double* __restrict__ TP, long long sc, long long id) {
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
-  const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
-  const long long id = sg.id(i, j, k);
-  const int vmap[5] = {QRHO, QU + D, QU + T1, QU + T2, QP};
-  double line[5][7];
-#pragma unroll
-  for (int v = 0; v < 5; ++v)
-#pragma unroll
-    for (int m = 0; m < 7; ++m) line[v][m] = Q[vmap[v] * sg.sc + id + (m - 3) * st];
-  double chi = K.flatten ? flat_coef(line[4], line[1], K.small_pres) : 1.0;
-  double am[5], ap[5], a6[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) ppm_parabola(line[v], chi, am[v], ap[v], a6[v]);
-
-  const double un = line[1][3], c = Q[QC * sg.sc + id];
-  const double rho_c = Q[QRC * sg.sc + id], c_rho = Q[QCR * sg.sc + id], inv_c2 = Q[QIC2 * sg.sc + id];
+  const double un = zone[1];
   const double c2 = c * c;
   const double lu = 0.5 * rho_c, lp = 0.5 * inv_c2;
   const double lam[3] = {un - c, un, un + c};
   double sig[3];
 #pragma unroll
   for (int w = 0; w < 3; ++w) sig[w] = fabs(lam[w]) * K.dtdx[D];
-
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     bool reach[3];
 #pragma unroll
-    for (int w = 0; w < 3; ++w) reach[w] = side ? (lam[w] > 0.0) : (lam[w] < 0.0);
+    for (int w = 0; w < 3; ++w) reach[w] = side ? gt0(lam[w]) : lt0(lam[w]);
     const int fast = side ? 2 : 0;
-    double ref[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-      ref[v] = reach[fast] ? (side ? integ_plus(am[v], ap[v], a6[v], sig[fast])
-                                   : integ_minus(am[v], ap[v], a6[v], sig[fast]))
-                           : line[v][3];
     auto I = [&](int w, int v) {
       return side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
     };
+    double ref[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : zone[v];
     // the reference wave contributes exactly zero (ref - I(sigma_fast) == 0), so
     // only the other acoustic wave and the entropy/shear wave are evaluated
     double bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
@@ -130,11 +113,115 @@ __global__ void __launch_bounds__(BLOCK) k_trace(ScratchGeom sg, const double* _
     s_rho = dmax(s_rho, K.small_dens);
     s_p = dmax(s_p, K.small_pres);
     double* out = side ? TP : TM;
-    out[0 * sg.sc + id] = s_rho;
-    out[(1 + D) * sg.sc + id] = s_un;
-    out[(1 + T1) * sg.sc + id] = s_t1;
-    out[(1 + T2) * sg.sc + id] = s_t2;
-    out[4 * sg.sc + id] = s_p;
+    out[0 * sc + id] = s_rho;
+    out[(1 + D) * sc + id] = s_un;
+    out[(1 + T1) * sc + id] = s_t1;
+    out[(1 + T2) * sc + id] = s_t2;
+    out[4 * sc + id] = s_p;
+  }
+}
+
+// pencil segments of the tracing sweep: zones [-1, n_d] along d cut into
+// segments of TRACE_SEG, for every transverse position in [-1, n]
+constexpr int TRACE_SEG = 16;
+struct SweepRange {
+  int lo1, ext1, lo2, ext2;  // transverse axes T1 (thread-fastest) and T2
+  int nd, nseg;              // zones along d, segments per pencil
+  __host__ __device__ long long count() const { return (long long)ext1 * ext2 * nseg; }
+};
+
+// ---- stages 2-3: flattening, PPM reconstruction and characteristic tracing
+// along d.  Each thread sweeps one pencil segment, so every flattening
+// coefficient, slope and interface value is formed once per zone (plus a
+// two-zone warm-up per segment) from sliding register windows.
+template <int D>
+__global__ void __launch_bounds__(BLOCK) k_trace(ScratchGeom sg, const double* __restrict__ Q,
+                                                 double* __restrict__ TM, double* __restrict__ TP, StepConst K,
+                                                 SweepRange R) {
+  long long t = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  if (t >= R.count()) return;
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  int c3[3];
+  c3[T1] = R.lo1 + (int)(t % R.ext1);
+  long long r = t / R.ext1;
+  c3[T2] = R.lo2 + (int)(r % R.ext2);
+  const int seg = (int)(r / R.ext2);
+  const int i0 = -1 + seg * TRACE_SEG;
+  const int i1 = min(i0 + TRACE_SEG, R.nd + 1);
+  c3[D] = i0;
+  const long long sc = sg.sc;
+  const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
+  const long long base = sg.id(c3[0], c3[1], c3[2]);
+  const double* __restrict__ qv[5] = {Q + QRHO * sc, Q + (QU + D) * sc, Q + (QU + T1) * sc, Q + (QU + T2) * sc,
+                                      Q + QP * sc};
+  const double sp = K.small_pres;
+
+  // windows relative to the current zone i: a0 = a_i, a1 = a_{i+1}, sl = slope_i,
+  // fm = interface i-1/2; pressures pm2 = p_{i-2}, pm1 = p_{i-1}, pp2 = p_{i+2};
+  // flattening ctm = chi~_{i-1}, ct0 = chi~_i
+  double a0[5], a1[5], sl[5], fm[5];
+  double pm2, pm1, pp2, ctm = 1.0, ct0 = 1.0;
+  {
+    double am2[5], am1[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      am2[v] = qv[v][base - 2 * st];
+      am1[v] = qv[v][base - st];
+      a0[v] = qv[v][base];
+      a1[v] = qv[v][base + st];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double s_m1 = mc_slope(am2[v], am1[v], a0[v]);
+      sl[v] = mc_slope(am1[v], a0[v], a1[v]);
+      fm[v] = face_value(am1[v], a0[v], s_m1, sl[v]);
+    }
+    pm2 = am2[4];
+    pm1 = am1[4];
+    pp2 = qv[4][base + 2 * st];
+    if (K.flatten) {
+      double pm3 = qv[4][base - 3 * st];
+      ctm = flat_tilde(pm3, pm2, a0[4], a1[4], am2[1], a0[1], sp);
+      ct0 = flat_tilde(pm2, pm1, a1[4], pp2, am1[1], a1[1], sp);
+    }
+  }
+  for (int i = i0; i < i1; ++i) {
+    const long long id = base + (long long)(i - i0) * st;
+    double a2[5];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) a2[v] = qv[v][id + 2 * st];
+    a2[4] = pp2;
+    double chi = 1.0, ctp = 1.0, pp3 = 0.0;
+    if (K.flatten) {
+      pp3 = qv[4][id + 3 * st];
+      ctp = flat_tilde(pm1, a0[4], a2[4], pp3, a0[1], a2[1], sp);
+      double dp1 = a1[4] - pm1;
+      chi = lt0(dp1) ? dmin(ct0, ctp) : dmin(ct0, ctm);
+    }
+    double am[5], ap[5], a6[5], zone[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double s1 = mc_slope(a0[v], a1[v], a2[v]);
+      double fp = face_value(a0[v], a1[v], sl[v], s1);
+      ppm_limit(a0[v], fm[v], fp, chi, am[v], ap[v], a6[v]);
+      zone[v] = a0[v];
+      sl[v] = s1;
+      fm[v] = fp;
+    }
+    trace_zone<D>(am, ap, a6, zone, Q[QC * sc + id], Q[QRC * sc + id], Q[QCR * sc + id], Q[QIC2 * sc + id], K,
+                  TM, TP, sc, id);
+    // slide the windows one zone
+    pm2 = pm1;
+    pm1 = a0[4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      a0[v] = a1[v];
+      a1[v] = a2[v];
+    }
+    if (K.flatten) pp2 = pp3;
+    else if (i + 1 < i1) pp2 = qv[4][id + 3 * st];
+    ctm = ct0;
+    ct0 = ctp;
   }
 }
 
@@ -234,14 +321,14 @@ __device__ __forceinline__ void block_max3(double v[3], DevFlags* flags) {
   for (int a = 0; a < 3; ++a) {
     double x = v[a];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = dmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    for (int o = 16; o > 0; o >>= 1) x = dmax_nn(x, __shfl_xor_sync(0xffffffffu, x, o));
     if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = x;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
     double x = red[threadIdx.x][0];
-    for (int w = 1; w < BLOCK / 32; ++w) x = dmax(x, red[threadIdx.x][w]);
-    if (x > 0.0) atomicMax(&flags->maxspeed[threadIdx.x], (unsigned long long)__double_as_longlong(x));
+    for (int w = 1; w < BLOCK / 32; ++w) x = dmax_nn(x, red[threadIdx.x][w]);
+    if (gt0(x)) atomicMax(&flags->maxspeed[threadIdx.x], (unsigned long long)__double_as_longlong(x));
   }
 }
 
@@ -261,7 +348,9 @@ __global__ void __launch_bounds__(BLOCK) k_update(BoxGeom in, BoxGeom out, Scrat
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       double v = u0[c];
-      for (int d = 0; d < K.dim; ++d) v = v - K.dtdx[d] * (F[d][c * sg.sc + id + st[d]] - F[d][c * sg.sc + id]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (d < K.dim) v = v - K.dtdx[d] * (F[d][c * sg.sc + id + st[d]] - F[d][c * sg.sc + id]);
       u1[c] = v;
     }
     if (K.has_grav) {
@@ -280,7 +369,9 @@ __global__ void __launch_bounds__(BLOCK) k_update(BoxGeom in, BoxGeom out, Scrat
     cons_to_prim_flag(u1, K, q, &inv, &bad);
     if (bad) atomicOr(&flags->bad, 1);
     double c = sqrt(K.gamma * q[4] * inv);
-    for (int d = 0; d < K.dim; ++d) spd[d] = fabs(q[1 + d]) + c;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;
   }
   block_max3(spd, flags);
 }
@@ -298,7 +389,9 @@ __global__ void __launch_bounds__(BLOCK) k_dt_partial(BoxGeom box, StepConst K, 
     cons_to_prim_flag(U, K, q, &inv, &bad);
     if (bad) atomicOr(&flags->bad, 1);
     double c = sqrt(K.gamma * q[4] * inv);
-    for (int d = 0; d < K.dim; ++d) spd[d] = fabs(q[1 + d]) + c;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;
   }
   block_max3(spd, flags);
 }
@@ -344,17 +437,25 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
   k_prim<<<blocks_for(rp.count()), BLOCK, 0, st>>>(a.in, sg, s.Q, a.K, rp, a.flags);
   nl += 1;
   mark(ST_TRACE);
-  // stages 2-3: traced states on zones [-1, n]
+  // stages 2-3: traced states on zones [-1, n] (pencil sweeps)
   Range rt;
   for (int ax = 0; ax < 3; ++ax) {
     bool act = ax < dim;
     rt.lo[ax] = act ? -1 : 0;
     rt.ext[ax] = act ? n[ax] + 2 : 1;
   }
-  unsigned bt = blocks_for(rt.count());
-  k_trace<0><<<bt, BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], a.K, rt);
-  k_trace<1><<<bt, BLOCK, 0, st>>>(sg, s.Q, s.TM[1], s.TP[1], a.K, rt);
-  if (dim == 3) k_trace<2><<<bt, BLOCK, 0, st>>>(sg, s.Q, s.TM[2], s.TP[2], a.K, rt);
+  for (int d = 0; d < dim; ++d) {
+    int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+    SweepRange sw;
+    sw.lo1 = rt.lo[t1]; sw.ext1 = rt.ext[t1];
+    sw.lo2 = rt.lo[t2]; sw.ext2 = rt.ext[t2];
+    sw.nd = n[d];
+    sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
+    unsigned b = blocks_for(sw.count());
+    if (d == 0) k_trace<0><<<b, BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], a.K, sw);
+    if (d == 1) k_trace<1><<<b, BLOCK, 0, st>>>(sg, s.Q, s.TM[1], s.TP[1], a.K, sw);
+    if (d == 2) k_trace<2><<<b, BLOCK, 0, st>>>(sg, s.Q, s.TM[2], s.TP[2], a.K, sw);
+  }
   nl += dim;
   mark(ST_FLUX1);
   // stage 4a: first fluxes on d-faces [0, n_d] x transverse [-1, n]
