@@ -56,7 +56,8 @@ typedef enum {
   HYDRO_EBADSTATE = -4,  /* a zone held rho <= 0, p <= 0 or a non-finite value */
   HYDRO_EAGAIN = -5,     /* result not ready yet (serve_poll) */
   HYDRO_ETIMEDOUT = -6,  /* a bounded wait ran out */
-  HYDRO_ENOTIMPL = -7    /* not supported by this build */
+  HYDRO_ENOTIMPL = -7,   /* not supported by this build */
+  HYDRO_ETOOBIG = -8     /* box larger than the fixed storage of hydro_advance_box_noalloc */
 } hydro_status;
 
 /* boundary kind of one face of a box */
@@ -130,6 +131,30 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
  * context's device, returns HYDRO_EBADSTATE if any step since the last check
  * met a non-physical zone, else HYDRO_OK. */
 int hydro_ctx_check(hydro_ctx_t* ctx);
+
+/* ---- allocation-free step (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory while they run: a host that
+ * has reserved the whole GPU for itself, a real-time loop that cannot afford
+ * the device-wide synchronisation an allocation or free may cause, or a
+ * plug-in whose host owns every allocation.  The step is the same as
+ * hydro_advance_box, but its scratch lives in fixed device storage of the
+ * library: no context, no cudaMalloc/cudaFree, no allocating library call.
+ *  - Maximum box: the scratch grid of the box (its grown extent, rows padded
+ *    to even length: ((n0+8+1)&~1) * (n1+8) * (n2+8 in 3-D, else 1)) must
+ *    hold at most HYDRO_NOALLOC_MAX_ZONES zones, e.g. a 32^3 3-D box or a
+ *    244^2 2-D box; larger boxes return HYDRO_ETOOBIG and enqueue nothing.
+ *  - The storage (48.3 MiB) is held on every GPU that loads this library until
+ *    the process exits, and is shared by every call on that device: calls
+ *    whose work overlaps on the GPU (different streams, or threads) race and
+ *    must be serialised by the caller.  Each call clears the state it needs.
+ *  - Runs on the calling thread's current device.  The first call on a device
+ *    looks up the storage's device address (cudaGetSymbolAddress); make that
+ *    first call outside any stream capture.
+ *  - in, out, params, dt, dt_next_host, stream: as for hydro_advance_box
+ *    (a bad state is reported only when dt_next_host is given). */
+#define HYDRO_NOALLOC_MAX_ZONES 64000
+int hydro_advance_box_noalloc(const hydro_box_t* in, const hydro_box_t* out, const hydro_params_t* params,
+                              double dt, double* dt_next_host, void* stream);
 
 /* ---- instrumentation (paper: no profiler is named; this is the build's own tracing) ----
  * Stages of a step, in order: 0 primitive state, 1 characteristic tracing,

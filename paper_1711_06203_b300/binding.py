@@ -14,6 +14,8 @@ LIBDIR = os.path.join(HERE, "_build")
 
 HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA = 0, -1, -2, -3
 HYDRO_EBADSTATE, HYDRO_EAGAIN, HYDRO_ETIMEDOUT, HYDRO_ENOTIMPL = -4, -5, -6, -7
+HYDRO_ETOOBIG = -8
+NOALLOC_MAX_ZONES = 64000
 BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
 FLAG_NO_FLATTEN = 1
 NG = 4
@@ -74,6 +76,7 @@ def lib(variant="default"):
     L.hydro_strerror.restype = ctypes.c_char_p
     L.hydro_dt.argtypes = [vp, B, P, D, vp]
     L.hydro_advance_box.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
+    L.hydro_advance_box_noalloc.argtypes = [B, B, P, ctypes.c_double, D, vp]
     L.hydro_ctx_set_profiling.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_stage_times.argtypes = [vp, D, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     L.hydro_ctx_launches.argtypes = [vp]
@@ -121,6 +124,17 @@ def _stream_handle(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def hydro_advance_box_noalloc(bin_, bout, p, dt, want_dt_next=False, stream=None, variant="default"):
+    """The allocation-free step: no context, fixed library-owned scratch (see
+    include/hydro.h).  Returns (status, dt_next or None); never raises on a
+    status so callers can test HYDRO_ETOOBIG and friends."""
+    L = lib(variant)
+    out = ctypes.c_double(0.0)
+    rc = L.hydro_advance_box_noalloc(ctypes.byref(bin_), ctypes.byref(bout), ctypes.byref(p), float(dt),
+                                     ctypes.byref(out) if want_dt_next else None, _stream_handle(stream))
+    return rc, (out.value if want_dt_next else None)
 
 
 class Context:
