@@ -69,7 +69,8 @@ enum {
 };
 
 /* hydro_params_t.flags */
-#define HYDRO_FLAG_NO_FLATTEN 1u /* disable Colella-Woodward flattening */
+#define HYDRO_FLAG_NO_FLATTEN 1u  /* disable Colella-Woodward flattening */
+#define HYDRO_FLAG_NO_AUTOTUNE 2u /* hydro_advance_batch: fixed 16-zone sweep segments, no timing runs */
 
 typedef struct {
   double gamma;       /* gamma-law EOS exponent, > 1 */
@@ -126,6 +127,37 @@ int hydro_dt(hydro_ctx_t* ctx, const hydro_box_t* box, const hydro_params_t* par
  *    state. */
 int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
                       const hydro_params_t* params, double dt, double* dt_next_host, void* stream);
+
+/* Advance every box of a level by one CTU-PPM step in one batched, graph-
+ * captured launch sequence (paper Sec. 3: a level is a set of boxes of uneven
+ * sizes that the box iterator hands to the kernel one by one; Fig. 1).
+ *  - in[b], out[b] (host arrays of nbox descriptors): as for hydro_advance_box,
+ *    box by box; all boxes share `params` (dim, gamma, gravity, flags).
+ *  - dt_dev: device array of nbox steps, read when the step runs (an AMR
+ *    level passes its level dt replicated); values are not checked.
+ *  - dt_next_dev: NULL or a device array receiving each box's CFL step of
+ *    U^{n+1}.
+ *  - bad_box_host: NULL, or host memory receiving the index of the first box
+ *    that met a non-physical zone (-1 if none); the call then synchronises
+ *    `stream` and returns HYDRO_EBADSTATE for a bad box.  Without it a bad
+ *    state is recorded in the context (hydro_ctx_check).
+ *  - The first call for a given set of descriptors, params and dt arrays
+ *    builds a plan: per-box work tables, scratch for all boxes in one
+ *    context-owned pool, the trace-sweep segment length per box-size class
+ *    (timed on the boxes unless HYDRO_FLAG_NO_AUTOTUNE; remembered in the
+ *    context, and in the file named by the environment variable
+ *    HYDRO_TUNE_CACHE if set) and a CUDA graph of the whole step.  Later
+ *    calls with the same descriptors replay the graph; the context keeps the
+ *    8 most recent plans.  Plans of one context share the scratch pool: do not
+ *    run two batched steps of one context concurrently. */
+int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                        const hydro_params_t* params, const double* dt_dev, double* dt_next_dev, int* bad_box_host,
+                        void* stream);
+
+/* The autotuned sweep segments of a context: up to nmax pairs (box extent
+ * along the sweep, zones per segment) into the host arrays extent/segment.
+ * Returns the number of tuned extents. */
+int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
 
 /* Report and clear the context's sticky bad-state flag: synchronises the
  * context's device, returns HYDRO_EBADSTATE if any step since the last check

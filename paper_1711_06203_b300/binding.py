@@ -18,6 +18,7 @@ HYDRO_ETOOBIG = -8
 NOALLOC_MAX_ZONES = 64000
 BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
 FLAG_NO_FLATTEN = 1
+FLAG_NO_AUTOTUNE = 2
 NG = 4
 
 
@@ -77,6 +78,8 @@ def lib(variant="default"):
     L.hydro_dt.argtypes = [vp, B, P, D, vp]
     L.hydro_advance_box.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_box_noalloc.argtypes = [B, B, P, ctypes.c_double, D, vp]
+    L.hydro_advance_batch.argtypes = [vp, B, B, ctypes.c_int, P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
+    L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.hydro_ctx_set_profiling.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_stage_times.argtypes = [vp, D, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     L.hydro_ctx_launches.argtypes = [vp]
@@ -176,6 +179,30 @@ class Context:
 
     def hydro_ctx_check(self):
         return self.L.hydro_ctx_check(self.h)
+
+    def hydro_advance_batch(self, bins, bouts, p, dt_dev, dt_next_dev=None, want_bad=False, stream=None,
+                            raise_on_error=True):
+        """Batched step of a level.  bins/bouts: lists of hydro_box_t; dt_dev,
+        dt_next_dev: CUDA float64 tensors of len(bins) (dt_next_dev optional).
+        Returns the index of the first bad box (-1) when want_bad, else None."""
+        n = len(bins)
+        arr_in = (hydro_box_t * n)(*bins)
+        arr_out = (hydro_box_t * n)(*bouts)
+        bad = ctypes.c_int(-1)
+        rc = self.L.hydro_advance_batch(self.h, arr_in, arr_out, n, ctypes.byref(p), ctypes.c_void_p(dt_dev.data_ptr()),
+                                        ctypes.c_void_p(dt_next_dev.data_ptr()) if dt_next_dev is not None else None,
+                                        ctypes.byref(bad) if want_bad else None, _stream_handle(stream))
+        if rc and raise_on_error:
+            raise HydroError(rc, "hydro_advance_batch")
+        if not raise_on_error:
+            return rc, bad.value
+        return bad.value if want_bad else None
+
+    def hydro_batch_tuning(self):
+        ext = (ctypes.c_int * 64)()
+        seg = (ctypes.c_int * 64)()
+        k = self.L.hydro_batch_tuning(self.h, ext, seg, 64)
+        return {ext[i]: seg[i] for i in range(min(k, 64))}
 
     STAGES = ("prim", "trace", "flux1", "flux2", "flux3", "update")
 

@@ -1,4 +1,626 @@
-// Batched advance of many boxes (placeholder until the batch engine lands).
-#include "hydro_api_internal.cuh"
+// Batched advance of the boxes of one AMR level (paper Sec. 3 and Fig. 1:
+// a level is a set of non-uniform boxes that a box iterator hands to the
+// compute kernel one by one; Sec. 4 StarLord paragraph).  Here every stage of
+// the CTU-PPM step is ONE launch over all boxes of the level: each block
+// belongs to one box (found through a per-launch block table) and processes
+// that box's work items with the same device bodies as the single-box path.
+// The launch sequence of a given set of boxes (a plan) is captured once in a
+// CUDA graph and replayed; per-box time steps are read from device memory at
+// run time, so one graph serves every step.  The pencil-segment length of
+// the tracing sweep is autotuned per box-size class.
+#include <cuda_runtime.h>
 
-void hydro_batch_release(hydro_ctx* ctx) { (void)ctx; }
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "hydro.h"
+#include "hydro_api_internal.cuh"
+#include "hydro_items.cuh"
+
+namespace hydro {
+
+// everything a batched kernel needs about one box (device resident)
+struct BatchBox {
+  BoxGeom in, out;
+  ScratchGeom sg;
+  Scratch s;
+  StepConst K;  // dt, hdt, dtdx refreshed on the device from dt_dev every call
+  double dx[3];
+  double cfl;
+  Range rp, ru;
+  SweepRange tr[3];
+  Range r1[3], r2[3][3], r3[3];
+  DevFlags flags;
+};
+
+namespace {
+
+// ---- batched kernels: block -> (box, first block of the box)
+__device__ __forceinline__ long long item_of(const int* box_first, int b) {
+  return (long long)(blockIdx.x - box_first[b]) * BLOCK + threadIdx.x;
+}
+
+__global__ void kb_prepare(BatchBox* boxes, int nbox, const double* __restrict__ dt_dev) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  BatchBox& B = boxes[b];
+  const double dt = dt_dev[b];
+  B.K.dt = dt;
+  B.K.hdt = 0.5 * dt;
+  for (int a = 0; a < 3; ++a) B.K.dtdx[a] = (a < B.K.dim) ? dt / B.dx[a] : 0.0;
+  B.flags.maxspeed[0] = B.flags.maxspeed[1] = B.flags.maxspeed[2] = 0ull;
+  B.flags.bad = 0;
+}
+
+__global__ void __launch_bounds__(BLOCK) kb_prim(BatchBox* boxes, const int* __restrict__ blk_box,
+                                                 const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  BatchBox& B = boxes[b];
+  prim_item(B.in, B.sg, B.s.Q, B.K, B.rp, &B.flags, item_of(box_first, b));
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLOCK) kb_trace(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
+                                                  const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  const BatchBox& B = boxes[b];
+  trace_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], item_of(box_first, b));
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLOCK) kb_flux1(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
+                                                  const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  const BatchBox& B = boxes[b];
+  flux1_item<D>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[D], B.K, B.r1[D], item_of(box_first, b));
+}
+
+template <int D, int T>
+__global__ void __launch_bounds__(BLOCK) kb_flux2(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
+                                                  const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  const BatchBox& B = boxes[b];
+  flux2_item<D, T>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[T], B.s.F2[D][T], B.K, B.r2[D][T], item_of(box_first, b));
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLOCK) kb_flux3(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
+                                                  const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  const BatchBox& B = boxes[b];
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  const bool three = B.K.dim == 3;
+  const double* fa = three ? B.s.F2[T1][T2] : B.s.F1[T1];
+  const double* fb = three ? B.s.F2[T2][T1] : nullptr;
+  flux3_item<D>(B.sg, B.s.TP[D], B.s.TM[D], fa, fb, B.s.F3[D], B.K, B.r3[D], item_of(box_first, b));
+}
+
+__global__ void __launch_bounds__(BLOCK) kb_update(BatchBox* boxes, const int* __restrict__ blk_box,
+                                                   const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  BatchBox& B = boxes[b];
+  update_item(B.in, B.out, B.sg, B.s.F3[0], B.s.F3[1], B.K.dim == 3 ? B.s.F3[2] : B.s.F3[0], B.K, B.ru, &B.flags,
+              item_of(box_first, b));
+}
+
+// per box: CFL step of the new state, bad-state flags
+__global__ void kb_finalize(BatchBox* boxes, int nbox, double* __restrict__ dt_next_dev, int* __restrict__ bad_out,
+                            DevFlags* ctx_flags) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  BatchBox& B = boxes[b];
+  dt_final_item(&B.flags, B.dx[0], B.dx[1], B.dx[2], B.K.dim, B.cfl);
+  if (dt_next_dev) dt_next_dev[b] = B.flags.dt_next;
+  bad_out[b] = B.flags.bad;
+  if (B.flags.bad) atomicOr(&ctx_flags->bad, 1);
+}
+
+// ---- host side: plans
+enum LaunchKind { L_PRIM, L_TRACE, L_FLUX1, L_FLUX2, L_FLUX3, L_UPDATE };
+
+struct LaunchSpec {
+  LaunchKind kind;
+  int d, t;
+  int nblocks;
+  size_t map_off;    // offset of blk_box in the plan's map array (ints)
+  size_t first_off;  // offset of box_first (nbox ints)
+};
+
+struct Plan {
+  uint64_t key = 0;
+  int nbox = 0, dim = 0;
+  BatchBox* d_boxes = nullptr;
+  int* d_maps = nullptr;
+  int* d_bad = nullptr;
+  std::vector<LaunchSpec> launches;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+};
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+unsigned nblk(long long items) { return (unsigned)((items + BLOCK - 1) / BLOCK); }
+
+void destroy_plan(Plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->d_boxes) cudaFree(p->d_boxes);
+  if (p->d_maps) cudaFree(p->d_maps);
+  if (p->d_bad) cudaFree(p->d_bad);
+  delete p;
+}
+
+}  // namespace
+}  // namespace hydro
+
+using namespace hydro;
+
+struct hydro_batch_state {
+  std::vector<Plan*> plans;
+  double* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaStream_t capture = nullptr;
+  uint64_t clock = 0;
+  // autotuned number of segments per pencil, keyed by box extent along the sweep
+  std::map<int, int> seg_parts;
+  bool tune_loaded = false;
+};
+
+namespace {
+
+constexpr int MAX_PLANS = 8;
+const int SEG_PARTS[] = {1, 2, 3, 4};
+
+int segment_length(hydro_batch_state* S, int nd) {
+  auto it = S->seg_parts.find(nd);
+  int parts = (it == S->seg_parts.end()) ? -1 : it->second;
+  if (parts <= 0) return TRACE_SEG;
+  return (nd + 2 + parts - 1) / parts;
+}
+
+// per-box ranges of every stage (same ranges as the single-box launch sequence)
+void fill_ranges(BatchBox& B, int dim, hydro_batch_state* S) {
+  const int* n = B.in.n;
+  for (int ax = 0; ax < 3; ++ax) {
+    int g = (ax < 2 || dim == 3) ? NG : 0;
+    B.rp.lo[ax] = -g;
+    B.rp.ext[ax] = n[ax] + 2 * g;
+  }
+  Range rt;
+  for (int ax = 0; ax < 3; ++ax) {
+    bool act = ax < dim;
+    rt.lo[ax] = act ? -1 : 0;
+    rt.ext[ax] = act ? n[ax] + 2 : 1;
+  }
+  for (int d = 0; d < 3; ++d) {
+    int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+    SweepRange& sw = B.tr[d];
+    sw.lo1 = rt.lo[t1]; sw.ext1 = rt.ext[t1];
+    sw.lo2 = rt.lo[t2]; sw.ext2 = rt.ext[t2];
+    sw.nd = n[d];
+    sw.seg = (d < dim) ? segment_length(S, n[d]) : TRACE_SEG;
+    sw.nseg = (n[d] + 2 + sw.seg - 1) / sw.seg;
+    Range r = rt;
+    r.lo[d] = 0;
+    r.ext[d] = n[d] + 1;
+    B.r1[d] = r;
+    Range f;
+    for (int ax = 0; ax < 3; ++ax) { f.lo[ax] = 0; f.ext[ax] = (ax < dim) ? n[ax] : 1; }
+    f.ext[d] = n[d] + 1;
+    B.r3[d] = f;
+    for (int t = 0; t < 3; ++t) {
+      if (t == d) continue;
+      int o = 3 - d - t;
+      Range q;
+      q.lo[d] = 0; q.ext[d] = n[d] + 1;
+      q.lo[t] = 0; q.ext[t] = n[t];
+      q.lo[o] = -1; q.ext[o] = n[o] + 2;
+      B.r2[d][t] = q;
+    }
+  }
+  for (int ax = 0; ax < 3; ++ax) { B.ru.lo[ax] = 0; B.ru.ext[ax] = (ax < dim) ? n[ax] : 1; }
+}
+
+long long items_of(const BatchBox& B, LaunchKind k, int d, int t) {
+  switch (k) {
+    case L_PRIM: return B.rp.count();
+    case L_TRACE: return B.tr[d].count();
+    case L_FLUX1: return B.r1[d].count();
+    case L_FLUX2: return B.r2[d][t].count();
+    case L_FLUX3: return B.r3[d].count();
+    default: return B.ru.count();
+  }
+}
+
+void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
+  const int* bb = p->d_maps + L.map_off;
+  const int* bf = p->d_maps + L.first_off;
+  BatchBox* B = p->d_boxes;
+  const unsigned g = (unsigned)L.nblocks;
+  switch (L.kind) {
+    case L_PRIM: kb_prim<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
+    case L_TRACE:
+      if (L.d == 0) kb_trace<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 1) kb_trace<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 2) kb_trace<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      break;
+    case L_FLUX1:
+      if (L.d == 0) kb_flux1<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 1) kb_flux1<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 2) kb_flux1<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      break;
+    case L_FLUX2:
+#define F2(DD, TT) \
+  if (L.d == DD && L.t == TT) kb_flux2<DD, TT><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      F2(0, 1) F2(0, 2) F2(1, 0) F2(1, 2) F2(2, 0) F2(2, 1)
+#undef F2
+      break;
+    case L_FLUX3:
+      if (L.d == 0) kb_flux3<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 1) kb_flux3<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 2) kb_flux3<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      break;
+    case L_UPDATE: kb_update<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
+  }
+}
+
+// the stage launches of a step, in order
+std::vector<LaunchSpec> launch_list(int dim) {
+  std::vector<LaunchSpec> v;
+  v.push_back({L_PRIM, 0, 0, 0, 0, 0});
+  for (int d = 0; d < dim; ++d) v.push_back({L_TRACE, d, 0, 0, 0, 0});
+  for (int d = 0; d < dim; ++d) v.push_back({L_FLUX1, d, 0, 0, 0, 0});
+  if (dim == 3)
+    for (int d = 0; d < 3; ++d)
+      for (int t = 0; t < 3; ++t)
+        if (t != d) v.push_back({L_FLUX2, d, t, 0, 0, 0});
+  for (int d = 0; d < dim; ++d) v.push_back({L_FLUX3, d, 0, 0, 0, 0});
+  v.push_back({L_UPDATE, 0, 0, 0, 0, 0});
+  return v;
+}
+
+// block tables of every launch for the given box descriptors (host)
+void build_maps(const std::vector<BatchBox>& boxes, std::vector<LaunchSpec>& L, std::vector<int>& maps) {
+  const int nbox = (int)boxes.size();
+  maps.clear();
+  for (auto& l : L) {
+    l.first_off = maps.size();
+    maps.resize(maps.size() + nbox);
+    long long total = 0;
+    for (int b = 0; b < nbox; ++b) {
+      maps[l.first_off + b] = (int)total;
+      total += nblk(items_of(boxes[b], l.kind, l.d, l.t));
+    }
+    l.nblocks = (int)total;
+    l.map_off = maps.size();
+    maps.resize(maps.size() + total);
+    for (int b = 0; b < nbox; ++b) {
+      long long nb = nblk(items_of(boxes[b], l.kind, l.d, l.t));
+      std::fill(maps.begin() + l.map_off + maps[l.first_off + b], maps.begin() + l.map_off + maps[l.first_off + b] + nb,
+                b);
+    }
+  }
+}
+
+int ensure_batch_scratch(hydro_ctx* ctx, size_t bytes) {
+  hydro_batch_state* S = ctx->batch;
+  if (bytes <= S->scratch_bytes) return HYDRO_OK;
+  // the pool moves: every plan points into it, so drop them all
+  if (cudaDeviceSynchronize() != cudaSuccess) return HYDRO_ECUDA;
+  for (Plan* p : S->plans) destroy_plan(p);
+  S->plans.clear();
+  if (S->scratch) cudaFree(S->scratch);
+  S->scratch = nullptr;
+  S->scratch_bytes = 0;
+  if (ctx->fail_alloc) return HYDRO_ENOMEM;
+  if (cudaMalloc(&S->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HYDRO_ENOMEM;
+  }
+  S->scratch_bytes = bytes;
+  return HYDRO_OK;
+}
+
+// optional persisted tuning: "nd parts" lines in the file named by HYDRO_TUNE_CACHE
+void load_tuning(hydro_batch_state* S) {
+  S->tune_loaded = true;
+  const char* path = std::getenv("HYDRO_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int nd, parts;
+  while (std::fscanf(f, "%d %d", &nd, &parts) == 2)
+    if (nd > 0 && parts >= 1 && parts <= 8) S->seg_parts[nd] = parts;
+  std::fclose(f);
+}
+
+void save_tuning(const hydro_batch_state* S) {
+  const char* path = std::getenv("HYDRO_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (auto& kv : S->seg_parts) std::fprintf(f, "%d %d\n", kv.first, kv.second);
+  std::fclose(f);
+}
+
+// Time the x-sweep of the tracing stage over the boxes of each untuned size
+// class for every candidate segment count, keep the fastest.  Runs the
+// primitive stage first so the sweep reads real data; writes scratch only.
+int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
+  hydro_batch_state* S = ctx->batch;
+  std::map<int, std::vector<int>> cls;
+  for (int b = 0; b < (int)boxes.size(); ++b)
+    for (int d = 0; d < dim; ++d)
+      if (!S->seg_parts.count(boxes[b].in.n[d])) cls[boxes[b].in.n[d]].push_back(b);
+  if (cls.empty()) return HYDRO_OK;
+  cudaStream_t st = S->capture;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return HYDRO_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return HYDRO_ECUDA; }
+  // primitive state of every box (the plan's first launch)
+  enqueue_launch(tmp, tmp->launches[0], st);
+  int rc = HYDRO_OK;
+  for (auto& kv : cls) {
+    const int nd = kv.first;
+    float best_ms = 1e30f;
+    int best = 1;
+    for (int parts : SEG_PARTS) {
+      if (parts > 1 && (nd + 2 + parts - 1) / parts < 4) continue;
+      // a one-launch sub-batch: the x-sweep (or the first axis of that extent) of the class boxes
+      std::vector<BatchBox> sub;
+      for (int b : kv.second) {
+        BatchBox B = boxes[b];
+        for (int d = 0; d < dim; ++d) {
+          if (B.in.n[d] != nd) continue;
+          B.tr[d].seg = (nd + 2 + parts - 1) / parts;
+          B.tr[d].nseg = (nd + 2 + B.tr[d].seg - 1) / B.tr[d].seg;
+        }
+        sub.push_back(B);
+      }
+      std::vector<LaunchSpec> L;
+      for (int d = 0; d < dim; ++d) L.push_back({L_TRACE, d, 0, 0, 0, 0});
+      std::vector<int> maps;
+      build_maps(sub, L, maps);
+      Plan p;
+      if (cudaMalloc(&p.d_boxes, sub.size() * sizeof(BatchBox)) != cudaSuccess ||
+          cudaMalloc(&p.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (p.d_boxes) cudaFree(p.d_boxes);
+        rc = HYDRO_ENOMEM;
+        break;
+      }
+      cudaMemcpyAsync(p.d_boxes, sub.data(), sub.size() * sizeof(BatchBox), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(p.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+      p.launches = L;
+      // only the sweeps along axes of this extent matter; time all dims of the sub-batch
+      for (int rep = 0; rep < 4; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, st);
+        for (auto& l : p.launches) enqueue_launch(&p, l, st);
+      }
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaFree(p.d_boxes);
+      cudaFree(p.d_maps);
+      p.d_boxes = nullptr;
+      p.d_maps = nullptr;
+      if (ms < best_ms) { best_ms = ms; best = parts; }
+    }
+    if (rc) break;
+    S->seg_parts[nd] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess && rc == HYDRO_OK) rc = HYDRO_ECUDA;
+  if (rc == HYDRO_OK) save_tuning(S);
+  return rc;
+}
+
+}  // namespace
+
+void hydro_batch_release(hydro_ctx* ctx) {
+  if (!ctx || !ctx->batch) return;
+  hydro_batch_state* S = ctx->batch;
+  for (Plan* p : S->plans) destroy_plan(p);
+  if (S->scratch) cudaFree(S->scratch);
+  if (S->capture) cudaStreamDestroy(S->capture);
+  delete S;
+  ctx->batch = nullptr;
+}
+
+extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                                   const hydro_params_t* params, const double* dt_dev, double* dt_next_dev,
+                                   int* bad_box_host, void* stream) {
+  if (!ctx || !in || !out || nbox < 1 || !dt_dev || !valid_params(params)) return HYDRO_EINVAL;
+  const int dim = params->dim;
+  for (int b = 0; b < nbox; ++b) {
+    if (!valid_box(&in[b], dim) || !out[b].u || out[b].ng != NG) return HYDRO_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out[b].u) % sizeof(double)) return HYDRO_EINVAL;
+    hydro_box_t o = out[b];
+    for (int a = 0; a < 3; ++a) {
+      if (o.n[a] != in[b].n[a]) return HYDRO_EINVAL;
+      o.dx[a] = in[b].dx[a];
+      o.bc[a][0] = o.bc[a][1] = HYDRO_BC_PREFILLED;
+    }
+    if (!valid_box(&o, dim) || boxes_overlap(&in[b], &o, dim)) return HYDRO_EINVAL;
+  }
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) return HYDRO_ECUDA;
+  if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return HYDRO_ECUDA;
+  struct Restore {
+    int dev, prev;
+    ~Restore() { if (prev >= 0 && prev != dev) cudaSetDevice(prev); }
+  } restore{ctx->device, prev};
+
+  if (!ctx->batch) {
+    ctx->batch = new (std::nothrow) hydro_batch_state();
+    if (!ctx->batch) return HYDRO_ENOMEM;
+    if (cudaStreamCreateWithFlags(&ctx->batch->capture, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx->batch;
+      ctx->batch = nullptr;
+      return HYDRO_ECUDA;
+    }
+  }
+  hydro_batch_state* S = ctx->batch;
+  if (!S->tune_loaded) load_tuning(S);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // plan key: every box's geometry and pointers, the params, the dt arrays
+  uint64_t key = 1469598103934665603ull;
+  key = fnv(key, &nbox, sizeof nbox);
+  key = fnv(key, in, sizeof(hydro_box_t) * nbox);
+  key = fnv(key, out, sizeof(hydro_box_t) * nbox);
+  key = fnv(key, params, sizeof(hydro_params_t));
+  key = fnv(key, &dt_dev, sizeof dt_dev);
+  key = fnv(key, &dt_next_dev, sizeof dt_next_dev);
+  const bool tune = !(params->flags & HYDRO_FLAG_NO_AUTOTUNE);
+  key = fnv(key, &tune, sizeof tune);
+  Plan* plan = nullptr;
+  for (Plan* p : S->plans)
+    if (p->key == key) plan = p;
+
+  if (!plan) {
+    // scratch pool: one scratch block per box
+    std::vector<ScratchGeom> sgs(nbox);
+    size_t total = 0;
+    for (int b = 0; b < nbox; ++b) {
+      sgs[b] = scratch_geom(in[b].n, dim);
+      total += (size_t)sgs[b].sc * SCRATCH_FIELDS;
+    }
+    int rc = ensure_batch_scratch(ctx, total * sizeof(double));
+    if (rc) return rc;
+    std::vector<BatchBox> boxes(nbox);
+    size_t off = 0;
+    for (int b = 0; b < nbox; ++b) {
+      BatchBox& B = boxes[b];
+      std::memset(&B, 0, sizeof B);
+      B.in = geom_of(&in[b], dim);
+      B.out = geom_of(&out[b], dim);
+      B.sg = sgs[b];
+      B.s = carve_scratch(S->scratch + off, sgs[b].sc);
+      off += (size_t)sgs[b].sc * SCRATCH_FIELDS;
+      B.K = step_const(params, in[b].dx, 1.0);  // dt fields are set on the device every call
+      for (int a = 0; a < 3; ++a) B.dx[a] = in[b].dx[a];
+      B.cfl = params->cfl;
+    }
+    for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
+    if (tune) {
+      // a throw-away plan holding only the primitive stage, for the tuner's input
+      Plan tmp;
+      std::vector<LaunchSpec> L = {{L_PRIM, 0, 0, 0, 0, 0}};
+      std::vector<int> maps;
+      build_maps(boxes, L, maps);
+      tmp.launches = L;
+      if (cudaMalloc(&tmp.d_boxes, nbox * sizeof(BatchBox)) != cudaSuccess ||
+          cudaMalloc(&tmp.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (tmp.d_boxes) cudaFree(tmp.d_boxes);
+        return HYDRO_ENOMEM;
+      }
+      cudaMemcpyAsync(tmp.d_boxes, boxes.data(), nbox * sizeof(BatchBox), cudaMemcpyHostToDevice, S->capture);
+      cudaMemcpyAsync(tmp.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, S->capture);
+      rc = autotune(ctx, boxes, &tmp, dim);
+      cudaStreamSynchronize(S->capture);
+      cudaFree(tmp.d_boxes);
+      cudaFree(tmp.d_maps);
+      if (rc) return rc;
+      for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
+    } else {
+      for (int b = 0; b < nbox; ++b)
+        for (int d = 0; d < 3; ++d) {
+          boxes[b].tr[d].seg = TRACE_SEG;
+          boxes[b].tr[d].nseg = (boxes[b].in.n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
+        }
+    }
+    plan = new (std::nothrow) Plan();
+    if (!plan) return HYDRO_ENOMEM;
+    plan->key = key;
+    plan->nbox = nbox;
+    plan->dim = dim;
+    plan->launches = launch_list(dim);
+    std::vector<int> maps;
+    build_maps(boxes, plan->launches, maps);
+    if (cudaMalloc(&plan->d_boxes, nbox * sizeof(BatchBox)) != cudaSuccess ||
+        cudaMalloc(&plan->d_maps, maps.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&plan->d_bad, nbox * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_plan(plan);
+      return HYDRO_ENOMEM;
+    }
+    if (cudaMemcpyAsync(plan->d_boxes, boxes.data(), nbox * sizeof(BatchBox), cudaMemcpyHostToDevice, S->capture) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(plan->d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, S->capture) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(S->capture) != cudaSuccess) {
+      destroy_plan(plan);
+      return HYDRO_ECUDA;
+    }
+    // capture the whole step as a graph
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(S->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      destroy_plan(plan);
+      return HYDRO_ECUDA;
+    }
+    const unsigned gb = (unsigned)((nbox + 127) / 128);
+    kb_prepare<<<gb, 128, 0, S->capture>>>(plan->d_boxes, nbox, dt_dev);
+    for (auto& l : plan->launches) enqueue_launch(plan, l, S->capture);
+    kb_finalize<<<gb, 128, 0, S->capture>>>(plan->d_boxes, nbox, dt_next_dev, plan->d_bad, ctx->flags);
+    cudaError_t ce = cudaStreamEndCapture(S->capture, &graph);
+    if (ce != cudaSuccess || !graph || cudaGraphInstantiate(&plan->exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      destroy_plan(plan);
+      return HYDRO_ECUDA;
+    }
+    cudaGraphDestroy(graph);
+    if ((int)S->plans.size() >= MAX_PLANS) {
+      auto lru = std::min_element(S->plans.begin(), S->plans.end(),
+                                  [](const Plan* a, const Plan* b) { return a->last_use < b->last_use; });
+      if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
+      destroy_plan(*lru);
+      S->plans.erase(lru);
+    }
+    S->plans.push_back(plan);
+  }
+  plan->last_use = ++S->clock;
+  if (cudaGraphLaunch(plan->exec, st) != cudaSuccess) return HYDRO_ECUDA;
+  ctx->launches += (long long)plan->launches.size() + 2;
+  if (bad_box_host) {
+    std::vector<int> bad(nbox);
+    if (cudaMemcpyAsync(bad.data(), plan->d_bad, nbox * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return HYDRO_ECUDA;
+    *bad_box_host = -1;
+    for (int b = 0; b < nbox; ++b)
+      if (bad[b]) { *bad_box_host = b; break; }
+    if (*bad_box_host >= 0) return HYDRO_EBADSTATE;
+  }
+  return HYDRO_OK;
+}
+
+extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax) {
+  if (!ctx || nmax < 0 || (nmax > 0 && (!extent || !segment))) return HYDRO_EINVAL;
+  if (!ctx->batch) return 0;
+  int k = 0;
+  for (auto& kv : ctx->batch->seg_parts) {
+    if (k < nmax) {
+      extent[k] = kv.first;
+      segment[k] = (kv.first + 2 + kv.second - 1) / kv.second;
+    }
+    ++k;
+  }
+  return k;
+}

@@ -1,0 +1,407 @@
+// Per-item device bodies of the staged CTU-PPM step.  Each stage is a
+// function of one work item t (a zone, a face, or a pencil segment of one
+// box); the single-box kernels and the batched kernels are thin wrappers
+// that only differ in how they find the box and the item index.
+#pragma once
+#include "hydro_step.cuh"
+
+namespace hydro {
+namespace {
+
+constexpr int BLOCK = 128;
+
+__device__ __forceinline__ bool range_zone(const Range& R, long long t, int& i, int& j, int& k) {
+  long long e0 = R.ext[0], e1 = R.ext[1];
+  if (t >= e0 * e1 * R.ext[2]) return false;
+  i = R.lo[0] + (int)(t % e0);
+  long long r = t / e0;
+  j = R.lo[1] + (int)(r % e1);
+  k = R.lo[2] + (int)(r / e1);
+  return true;
+}
+
+// map a grown-box coordinate on one axis to the interior zone whose data it holds
+__device__ __forceinline__ int map_axis(int i, int n, int bclo, int bchi, bool& flip) {
+  if (i < 0) {
+    if (bclo == 0) return 0;                        // outflow
+    if (bclo == 1) { flip = !flip; return -1 - i; } // reflect
+    if (bclo == 2) return i + n;                    // periodic
+    return i;                                       // prefilled
+  }
+  if (i >= n) {
+    if (bchi == 0) return n - 1;
+    if (bchi == 1) { flip = !flip; return 2 * n - 1 - i; }
+    if (bchi == 2) return i - n;
+    return i;
+  }
+  return i;
+}
+
+// ---- stage 1: conserved -> primitive on the grown box (ghosts mapped by BC kind)
+__device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __restrict__ Q, StepConst K,
+                                                Range R, DevFlags* flags, long long t) {
+  int i, j, k;
+  if (!range_zone(R, t, i, j, k)) return;
+  bool flip[3] = {false, false, false};
+  int src[3] = {i, j, k};
+  src[0] = map_axis(i, in.n[0], in.bc[0][0], in.bc[0][1], flip[0]);
+  src[1] = map_axis(j, in.n[1], in.bc[1][0], in.bc[1][1], flip[1]);
+  if (K.dim == 3) src[2] = map_axis(k, in.n[2], in.bc[2][0], in.bc[2][1], flip[2]);
+  long long si = in.id(src[0], src[1], src[2]);
+  double U[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) U[c] = in.u[c * in.sc + si];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (flip[a]) U[1 + a] = -U[1 + a];
+  double q[5], inv;
+  bool bad = false;
+  cons_to_prim_flag(U, K, q, &inv, &bad);
+  if (bad) atomicOr(&flags->bad, 1);
+  double c = sqrt(K.gamma * q[4] * inv);
+  long long id = sg.id(i, j, k);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Q[v * sg.sc + id] = q[v];
+  Q[QC * sg.sc + id] = c;
+  Q[QRC * sg.sc + id] = q[0] / c;
+  Q[QCR * sg.sc + id] = c / q[0];
+  Q[QIC2 * sg.sc + id] = 1.0 / (c * c);
+}
+
+// ---- stage 3 of a zone: characteristic tracing from its parabolas
+// am/ap/a6/zone: (rho, un, ut1, ut2, p); outputs the zone's low- and high-face
+// states to TM/TP at id in absolute component order.
+template <int D>
+__device__ __forceinline__ void trace_zone(const double am[5], const double ap[5], const double a6[5],
+                                           const double zone[5], double c, double rho_c, double c_rho,
+                                           double inv_c2, const StepConst& K, double* __restrict__ TM,
+                                           double* __restrict__ TP, long long sc, long long id) {
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  const double un = zone[1];
+  const double c2 = c * c;
+  const double lu = 0.5 * rho_c, lp = 0.5 * inv_c2;
+  const double lam[3] = {un - c, un, un + c};
+  double sig[3];
+#pragma unroll
+  for (int w = 0; w < 3; ++w) sig[w] = fabs(lam[w]) * K.dtdx[D];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    bool reach[3];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) reach[w] = side ? gt0(lam[w]) : lt0(lam[w]);
+    const int fast = side ? 2 : 0;
+    auto I = [&](int w, int v) {
+      return side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
+    };
+    double ref[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : zone[v];
+    // the reference wave contributes exactly zero (ref - I(sigma_fast) == 0), so
+    // only the other acoustic wave and the entropy/shear wave are evaluated
+    double bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
+    if (side == 1 && reach[0]) bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
+    if (reach[1]) {
+      b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
+      bt1 = ref[2] - I(1, 2);
+      bt2 = ref[3] - I(1, 3);
+    }
+    if (side == 0 && reach[2]) bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
+    double s_rho = ref[0] - ((bm + b0) + bp);
+    double s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
+    double s_p = ref[4] - (bm * c2 + bp * c2);
+    double s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
+    s_un = s_un + K.hdt * K.grav[D];
+    s_t1 = s_t1 + K.hdt * K.grav[T1];
+    s_t2 = s_t2 + K.hdt * K.grav[T2];
+    s_rho = dmax(s_rho, K.small_dens);
+    s_p = dmax(s_p, K.small_pres);
+    double* out = side ? TP : TM;
+    out[0 * sc + id] = s_rho;
+    out[(1 + D) * sc + id] = s_un;
+    out[(1 + T1) * sc + id] = s_t1;
+    out[(1 + T2) * sc + id] = s_t2;
+    out[4 * sc + id] = s_p;
+  }
+}
+
+// ---- stages 2-3: flattening, PPM reconstruction and characteristic tracing
+// along d.  Each thread sweeps one pencil segment, so every flattening
+// coefficient, slope and interface value is formed once per zone (plus a
+// two-zone warm-up per segment) from sliding register windows.
+template <int D>
+__device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restrict__ Q,
+                                                 double* __restrict__ TM, double* __restrict__ TP, StepConst K,
+                                                 SweepRange R, long long t) {
+  if (t >= R.count()) return;
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  int c3[3];
+  c3[T1] = R.lo1 + (int)(t % R.ext1);
+  long long r = t / R.ext1;
+  c3[T2] = R.lo2 + (int)(r % R.ext2);
+  const int seg = (int)(r / R.ext2);
+  const int i0 = -1 + seg * R.seg;
+  const int i1 = min(i0 + R.seg, R.nd + 1);
+  c3[D] = i0;
+  const long long sc = sg.sc;
+  const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
+  const long long base = sg.id(c3[0], c3[1], c3[2]);
+  const double* __restrict__ qv[5] = {Q + QRHO * sc, Q + (QU + D) * sc, Q + (QU + T1) * sc, Q + (QU + T2) * sc,
+                                      Q + QP * sc};
+  const double sp = K.small_pres;
+
+  // windows relative to the current zone i: a0 = a_i, a1 = a_{i+1}, sl = slope_i,
+  // fm = interface i-1/2; pressures pm2 = p_{i-2}, pm1 = p_{i-1}, pp2 = p_{i+2};
+  // flattening ctm = chi~_{i-1}, ct0 = chi~_i
+  double a0[5], a1[5], sl[5], fm[5];
+  double pm2, pm1, pp2, ctm = 1.0, ct0 = 1.0;
+  {
+    double am2[5], am1[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      am2[v] = qv[v][base - 2 * st];
+      am1[v] = qv[v][base - st];
+      a0[v] = qv[v][base];
+      a1[v] = qv[v][base + st];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double s_m1 = mc_slope(am2[v], am1[v], a0[v]);
+      sl[v] = mc_slope(am1[v], a0[v], a1[v]);
+      fm[v] = face_value(am1[v], a0[v], s_m1, sl[v]);
+    }
+    pm2 = am2[4];
+    pm1 = am1[4];
+    pp2 = qv[4][base + 2 * st];
+    if (K.flatten) {
+      double pm3 = qv[4][base - 3 * st];
+      ctm = flat_tilde(pm3, pm2, a0[4], a1[4], am2[1], a0[1], sp);
+      ct0 = flat_tilde(pm2, pm1, a1[4], pp2, am1[1], a1[1], sp);
+    }
+  }
+  for (int i = i0; i < i1; ++i) {
+    const long long id = base + (long long)(i - i0) * st;
+    double a2[5];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) a2[v] = qv[v][id + 2 * st];
+    a2[4] = pp2;
+    double chi = 1.0, ctp = 1.0, pp3 = 0.0;
+    if (K.flatten) {
+      pp3 = qv[4][id + 3 * st];
+      ctp = flat_tilde(pm1, a0[4], a2[4], pp3, a0[1], a2[1], sp);
+      double dp1 = a1[4] - pm1;
+      chi = lt0(dp1) ? dmin(ct0, ctp) : dmin(ct0, ctm);
+    }
+    double am[5], ap[5], a6[5], zone[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double s1 = mc_slope(a0[v], a1[v], a2[v]);
+      double fp = face_value(a0[v], a1[v], sl[v], s1);
+      ppm_limit(a0[v], fm[v], fp, chi, am[v], ap[v], a6[v]);
+      zone[v] = a0[v];
+      sl[v] = s1;
+      fm[v] = fp;
+    }
+    trace_zone<D>(am, ap, a6, zone, Q[QC * sc + id], Q[QRC * sc + id], Q[QCR * sc + id], Q[QIC2 * sc + id], K,
+                  TM, TP, sc, id);
+    // slide the windows one zone
+    pm2 = pm1;
+    pm1 = a0[4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      a0[v] = a1[v];
+      a1[v] = a2[v];
+    }
+    if (K.flatten) pp2 = pp3;
+    else if (i + 1 < i1) pp2 = qv[4][id + 3 * st];
+    ctm = ct0;
+    ct0 = ctp;
+  }
+}
+
+__device__ __forceinline__ void load5(const double* __restrict__ A, long long sc, long long id, double v[5]) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) v[c] = A[c * sc + id];
+}
+__device__ __forceinline__ void store5(double* __restrict__ A, long long sc, long long id, const double v[5]) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) A[c * sc + id] = v[c];
+}
+
+// ---- stage 4a: first Riemann solves from the traced states
+template <int D>
+__device__ __forceinline__ void flux1_item(ScratchGeom sg, const double* __restrict__ TP,
+                                                 const double* __restrict__ TM, double* __restrict__ F1, StepConst K,
+                                                 Range R, long long t) {
+  int i, j, k;
+  if (!range_zone(R, t, i, j, k)) return;
+  const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
+  const long long id = sg.id(i, j, k);
+  double qL[5], qR[5], sL[NS], sR[NS], F[5];
+  load5(TP, sg.sc, id - st, qL);
+  load5(TM, sg.sc, id, qR);
+  state_from_prim(qL, K, sL);
+  state_from_prim(qR, K, sR);
+  hllc_flux(sL, sR, D, K, F);
+  store5(F1, sg.sc, id, F);
+}
+
+// transverse correction of a traced primitive state by one or two flux differences
+__device__ __forceinline__ void correct(const double q[5], const StepConst& K, double ca, const double* Fa,
+                                        long long sc, long long ida_hi, long long ida_lo, double cb,
+                                        const double* Fb, long long idb_hi, long long idb_lo, double s[NS]) {
+  double U[5];
+  U[0] = q[0];
+  U[1] = q[0] * q[1];
+  U[2] = q[0] * q[2];
+  U[3] = q[0] * q[3];
+  U[4] = energy_of(q, K);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    U[c] = U[c] - ca * (Fa[c * sc + ida_hi] - Fa[c * sc + ida_lo]);
+    if (Fb) U[c] = U[c] - cb * (Fb[c * sc + idb_hi] - Fb[c * sc + idb_lo]);
+  }
+  state_from_cons(U, K, s);
+}
+
+// ---- stage 4b (3-D): intermediate fluxes F^{d|t}
+template <int D, int T>
+__device__ __forceinline__ void flux2_item(ScratchGeom sg, const double* __restrict__ TP,
+                                                 const double* __restrict__ TM, const double* __restrict__ F1t,
+                                                 double* __restrict__ F2, StepConst K, Range R, long long t) {
+  int i, j, k;
+  if (!range_zone(R, t, i, j, k)) return;
+  const long long sd = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
+  const long long stt = (T == 0) ? 1 : (T == 1) ? sg.sy : sg.sz;
+  const long long id = sg.id(i, j, k), zl = id - sd;
+  const double coef = K.dtdx[T] * THIRD;
+  double qL[5], qR[5], sL[NS], sR[NS], F[5];
+  load5(TP, sg.sc, zl, qL);
+  load5(TM, sg.sc, id, qR);
+  correct(qL, K, coef, F1t, sg.sc, zl + stt, zl, 0.0, nullptr, 0, 0, sL);
+  correct(qR, K, coef, F1t, sg.sc, id + stt, id, 0.0, nullptr, 0, 0, sR);
+  hllc_flux(sL, sR, D, K, F);
+  store5(F2, sg.sc, id, F);
+}
+
+// ---- stage 4c: final fluxes from fully corrected states
+// 2-D: Fa = F1 of the other axis, Fb = null; 3-D: Fa = F^{t1|t2}, Fb = F^{t2|t1}
+template <int D>
+__device__ __forceinline__ void flux3_item(ScratchGeom sg, const double* __restrict__ TP,
+                                                 const double* __restrict__ TM, const double* __restrict__ Fa,
+                                                 const double* __restrict__ Fb, double* __restrict__ F3,
+                                                 StepConst K, Range R, long long t) {
+  int i, j, k;
+  if (!range_zone(R, t, i, j, k)) return;
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  const long long sd = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
+  const long long s1 = (T1 == 0) ? 1 : (T1 == 1) ? sg.sy : sg.sz;
+  const long long s2 = (T2 == 0) ? 1 : (T2 == 1) ? sg.sy : sg.sz;
+  const long long id = sg.id(i, j, k), zl = id - sd;
+  const double ca = 0.5 * K.dtdx[T1], cb = 0.5 * K.dtdx[T2];
+  double qL[5], qR[5], sL[NS], sR[NS], F[5];
+  load5(TP, sg.sc, zl, qL);
+  load5(TM, sg.sc, id, qR);
+  correct(qL, K, ca, Fa, sg.sc, zl + s1, zl, cb, Fb, zl + s2, zl, sL);
+  correct(qR, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
+  hllc_flux(sL, sR, D, K, F);
+  store5(F3, sg.sc, id, F);
+}
+
+// block-wide max of three non-negative doubles, then one atomicMax per value
+__device__ __forceinline__ void block_max3(double v[3], DevFlags* flags) {
+  __shared__ double red[3][BLOCK / 32];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double x = v[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = dmax_nn(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double x = red[threadIdx.x][0];
+    for (int w = 1; w < BLOCK / 32; ++w) x = dmax_nn(x, red[threadIdx.x][w]);
+    if (gt0(x)) atomicMax(&flags->maxspeed[threadIdx.x], (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+// ---- stage 5: conservative update, gravity source, bad-state check, CFL partials
+__device__ __forceinline__ void update_item(BoxGeom in, BoxGeom out, ScratchGeom sg, const double* __restrict__ Fx,
+                                                  const double* __restrict__ Fy, const double* __restrict__ Fz,
+                                                  StepConst K, Range R, DevFlags* flags, long long t) {
+  int i, j, k;
+  double spd[3] = {0.0, 0.0, 0.0};
+  if (range_zone(R, t, i, j, k)) {
+    const long long ii = in.id(i, j, k), oi = out.id(i, j, k), id = sg.id(i, j, k);
+    const double* F[3] = {Fx, Fy, Fz};
+    const long long st[3] = {1, sg.sy, sg.sz};
+    double u0[5], u1[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u0[c] = in.u[c * in.sc + ii];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double v = u0[c];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (d < K.dim) v = v - K.dtdx[d] * (F[d][c * sg.sc + id + st[d]] - F[d][c * sg.sc + id]);
+      u1[c] = v;
+    }
+    if (K.has_grav) {
+      double rho_mid = 0.5 * (u0[0] + u1[0]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) u1[1 + a] = u1[1 + a] + K.dt * rho_mid * K.grav[a];
+      double e0 = 0.5 * (u0[1] + u1[1]) * K.grav[0];
+      double e1 = 0.5 * (u0[2] + u1[2]) * K.grav[1];
+      double e2 = 0.5 * (u0[3] + u1[3]) * K.grav[2];
+      u1[4] = u1[4] + K.dt * ((e0 + e1) + e2);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out.u[c * out.sc + oi] = u1[c];
+    double q[5], inv;
+    bool bad = false;
+    cons_to_prim_flag(u1, K, q, &inv, &bad);
+    if (bad) atomicOr(&flags->bad, 1);
+    double c = sqrt(K.gamma * q[4] * inv);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;
+  }
+  block_max3(spd, flags);
+}
+
+// ---- CFL estimate of an existing box (interior)
+__device__ __forceinline__ void dt_partial_item(BoxGeom box, StepConst K, Range R, DevFlags* flags, long long t) {
+  int i, j, k;
+  double spd[3] = {0.0, 0.0, 0.0};
+  if (range_zone(R, t, i, j, k)) {
+    long long id = box.id(i, j, k);
+    double U[5], q[5], inv;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) U[c] = box.u[c * box.sc + id];
+    bool bad = false;
+    cons_to_prim_flag(U, K, q, &inv, &bad);
+    if (bad) atomicOr(&flags->bad, 1);
+    double c = sqrt(K.gamma * q[4] * inv);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;
+  }
+  block_max3(spd, flags);
+}
+
+// dt = cfl * min_d dx_d / max_zones(|u_d| + c): equal to cfl * min over zones
+// and d of dx_d/(|u_d| + c) because a correctly rounded quotient is monotone
+// in its denominator
+__device__ __forceinline__ void dt_final_item(DevFlags* flags, double dx0, double dx1, double dx2, int dim,
+                                              double cfl) {
+  double dx[3] = {dx0, dx1, dx2};
+  double m = HUGE_VAL;
+  for (int d = 0; d < dim; ++d) {
+    double s = __longlong_as_double((long long)flags->maxspeed[d]);
+    m = dmin(m, dx[d] / s);
+  }
+  flags->dt_next = cfl * m;
+}
+
+}  // namespace
+}  // namespace hydro

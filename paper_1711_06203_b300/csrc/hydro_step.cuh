@@ -48,6 +48,15 @@ struct Range {
   long long count() const { return (long long)ext[0] * ext[1] * ext[2]; }
 };
 
+// pencil segments of the tracing sweep: zones [-1, n_d] along d cut into
+// segments of TRACE_SEG, for every transverse position in [-1, n]
+constexpr int TRACE_SEG = 16;
+struct SweepRange {
+  int lo1, ext1, lo2, ext2;  // transverse axes T1 (thread-fastest) and T2
+  int nd, nseg, seg;         // zones along d, segments per pencil, zones per segment
+  __host__ __device__ long long count() const { return (long long)ext1 * ext2 * nseg; }
+};
+
 // scratch field bases
 struct Scratch {
   double* Q;          // NQ fields
