@@ -157,6 +157,70 @@ def run_reference(args):
     return 0
 
 
+def bench_batch(args, dev, stream):
+    """Batched level: 512 boxes, sides drawn from {16,24,32,48,64} per axis
+    (seed 1711), random prefilled states, gamma = 5/3, dx = 1/64, one step at
+    the level dt (min over boxes).  The batched step (one launch per stage over
+    all boxes, graph-replayed, autotuned sweeps) against 512 per-box launches."""
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    sizes, Us = inputs.level_boxes(512, seed=1711)
+    zones = sum(a * b * c for a, b, c in sizes)
+    dx = (1.0 / 64,) * 3
+    a = [torch.from_numpy(U).to(dev) for U in Us]
+    del Us
+    out = [torch.empty_like(x) for x in a]
+    bin_ = [hb.box(x, s, dx, hb.BC_PREFILLED) for x, s in zip(a, sizes)]
+    bout = [hb.box(x, s, dx, hb.BC_PREFILLED) for x, s in zip(out, sizes)]
+    p = hb.params(3, gamma=5.0 / 3.0, cfl=0.5)
+    ctx = hb.Context(dev.index)
+    level_dt = min(ctx.hydro_dt(bx, p, stream) for bx in bin_)
+    dt_dev = torch.full((len(sizes),), level_dt, dtype=torch.float64, device=dev)
+    dt_next = torch.empty_like(dt_dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ctx.hydro_advance_batch(bin_, bout, p, dt_dev, dt_next, stream=stream)  # plan, tuning, graph
+    torch.cuda.synchronize(dev)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    reps = max(3, min(args.steps, 10))
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    l0 = ctx.hydro_ctx_launches()
+    ms_batch = timed(lambda: ctx.hydro_advance_batch(bin_, bout, p, dt_dev, dt_next, stream=stream), reps)
+    launches_batch = (ctx.hydro_ctx_launches() - l0) // (reps + 2)
+
+    def per_box():
+        for bi, bo in zip(bin_, bout):
+            ctx.hydro_advance_box(bi, bo, p, level_dt, stream=stream)
+
+    l0 = ctx.hydro_ctx_launches()
+    ms_plain = timed(per_box, max(2, reps // 3))
+    launches_plain = (ctx.hydro_ctx_launches() - l0) // (max(2, reps // 3) + 2)
+    tuning = ctx.hydro_batch_tuning()
+    ctx.close()
+    return {"workload": "level of 512 boxes, sides from {16,24,32,48,64} (seed 1711), prefilled, gamma 5/3",
+            "interior_zones": zones, "zone_updates_per_s": zones / (ms_batch * 1e-3), "ms_per_step": ms_batch,
+            "per_box_zone_updates_per_s": zones / (ms_plain * 1e-3), "per_box_ms_per_step": ms_plain,
+            "speedup_vs_per_box": ms_plain / ms_batch, "launches_per_step": launches_batch,
+            "per_box_launches_per_step": launches_plain, "plan_build_ms": plan_ms,
+            "sweep_segment_by_extent": {str(k): v for k, v in sorted(tuning.items())},
+            "l2": "working set 3.7 GB of state + scratch, larger than L2"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -249,6 +313,10 @@ def run_ours(args):
     step_gbs = algorithmic_bytes_per_step(n) / (total_ms / args.steps * 1e-3) / 1e9
     step_gflops = sum(FLOPS_PER_UNIT[k] * units[k] for k in units) / (total_ms / args.steps * 1e-3) / 1e9
 
+    batch = None
+    if world == 1 and not args.no_batch:
+        batch = bench_batch(args, dev, stream)
+
     if rank != 0:
         return 0
     cpu = None
@@ -275,6 +343,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": zones / (e2e_ms * 1e-3) * world, "unit": "zone-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
+        "batched_level": batch,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,
@@ -294,6 +363,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=128, help="box side (the workload is 128)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-level leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

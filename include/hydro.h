@@ -164,6 +164,65 @@ int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
  * met a non-physical zone, else HYDRO_OK. */
 int hydro_ctx_check(hydro_ctx_t* ctx);
 
+/* ---- serving: continuous batching of independent problems ----
+ * A server owns a context, a stream and a scheduler thread.  Requests are
+ * admitted in arrival order while their device footprint (two copies of the
+ * grown state plus the step's scratch) fits the HBM budget and a slot is
+ * free; every scheduler iteration then advances ALL admitted requests by one
+ * CTU-PPM step in a single batched step (hydro_advance_batch's engine), each
+ * with its own gamma and CFL time step, so requests that arrive while others
+ * run join the next iteration.  Finished requests are retired and their memory
+ * released.  All serve_* calls are thread-safe. */
+enum { HYDRO_PROB_SOD = 0, HYDRO_PROB_SEDOV = 1, HYDRO_PROB_TWO_STATE = 2 };
+
+typedef struct {
+  int kind;             /* HYDRO_PROB_*: 3-D problem on the unit cube, outflow boundaries */
+  int n;                /* zones per side (cubic box), 4..1024 */
+  int steps;            /* CTU-PPM steps to take, >= 1 */
+  double gamma;         /* gamma-law exponent, > 1 */
+  double cfl;           /* Courant number, (0, 1] */
+  double rho_l, p_l;    /* Sod / two-state: state at x < 0.5 (at rest) */
+  double rho_r, p_r;    /*                  state at x >= 0.5 (at rest) */
+  double energy;        /* Sedov: blast energy, deposited as pressure within 4 zones of the centre */
+  double p_ambient;     /* Sedov: ambient pressure (density 1) */
+  double* result_host;  /* NULL, or host memory for 5*(n+8)^3 doubles: the final grown state (interior
+                           valid), written before the request completes; owned by the caller */
+} hydro_request_t;
+
+typedef struct {
+  int status;              /* HYDRO_OK, or the error that retired the request */
+  int steps_done;
+  double t_final;          /* simulated time reached */
+  double latency_ms;       /* submit -> result ready */
+  double queue_ms;         /* submit -> admitted */
+  long long zone_updates;  /* steps_done * n^3 */
+} hydro_result_t;
+
+typedef struct {
+  int queued, active;
+  long long admitted, completed, iterations, zone_updates;
+  double busy_ms;           /* time the scheduler spent in batched steps */
+  size_t hbm_budget, hbm_states, hbm_scratch_pool;
+} hydro_serve_stats_t;
+
+typedef struct serve serve_t;
+
+/* Create a server on `device` with an HBM budget in bytes (0: 80% of the free
+ * memory at creation) and at most max_slots concurrently active requests. */
+int serve_create(serve_t** s, int device, size_t hbm_budget_bytes, int max_slots);
+/* Queue a request (copied); *id receives its handle.  HYDRO_ETOOBIG if it can
+ * never fit the budget, HYDRO_EINVAL for bad parameters. */
+int serve_submit(serve_t* s, const hydro_request_t* req, uint64_t* id);
+/* Wait up to timeout_ms (0: do not wait, < 0: forever) for request `id`.
+ * HYDRO_OK: *res filled and the handle released; HYDRO_EAGAIN (timeout 0) or
+ * HYDRO_ETIMEDOUT: not finished yet; HYDRO_EINVAL: unknown handle. */
+int serve_poll(serve_t* s, uint64_t id, hydro_result_t* res, int timeout_ms);
+/* Snapshot of the server's counters. */
+int serve_stats(serve_t* s, hydro_serve_stats_t* st);
+/* Stop the scheduler (the step in flight completes), release everything;
+ * requests not yet polled are dropped.  NULL is a no-op. */
+void serve_destroy(serve_t* s);
+
 /* ---- allocation-free step (the paper has no counterpart) ----
  * For callers that cannot allocate device memory while they run: a host that
  * has reserved the whole GPU for itself, a real-time loop that cannot afford

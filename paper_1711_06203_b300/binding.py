@@ -51,6 +51,35 @@ class hydro_box_t(ctypes.Structure):
     ]
 
 
+PROB_SOD, PROB_SEDOV, PROB_TWO_STATE = 0, 1, 2
+
+
+class hydro_request_t(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int), ("n", ctypes.c_int), ("steps", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("rho_l", ctypes.c_double), ("p_l", ctypes.c_double), ("rho_r", ctypes.c_double), ("p_r", ctypes.c_double),
+        ("energy", ctypes.c_double), ("p_ambient", ctypes.c_double),
+        ("result_host", ctypes.c_void_p),
+    ]
+
+
+class hydro_result_t(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("t_final", ctypes.c_double),
+        ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("zone_updates", ctypes.c_longlong),
+    ]
+
+
+class hydro_serve_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("queued", ctypes.c_int), ("active", ctypes.c_int),
+        ("admitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("iterations", ctypes.c_longlong),
+        ("zone_updates", ctypes.c_longlong), ("busy_ms", ctypes.c_double),
+        ("hbm_budget", ctypes.c_size_t), ("hbm_states", ctypes.c_size_t), ("hbm_scratch_pool", ctypes.c_size_t),
+    ]
+
+
 _LIBS = {}
 
 
@@ -80,6 +109,12 @@ def lib(variant="default"):
     L.hydro_advance_box_noalloc.argtypes = [B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_batch.argtypes = [vp, B, B, ctypes.c_int, P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
+    L.serve_submit.argtypes = [vp, ctypes.POINTER(hydro_request_t), ctypes.POINTER(ctypes.c_uint64)]
+    L.serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hydro_result_t), ctypes.c_int]
+    L.serve_stats.argtypes = [vp, ctypes.POINTER(hydro_serve_stats_t)]
+    L.serve_destroy.argtypes = [vp]
+    L.serve_destroy.restype = None
     L.hydro_ctx_set_profiling.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_stage_times.argtypes = [vp, D, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     L.hydro_ctx_launches.argtypes = [vp]
@@ -221,3 +256,62 @@ class Context:
 
     def hydro_ctx_launches(self):
         return self.L.hydro_ctx_launches(self.h)
+
+
+class Server:
+    """A serve_t: continuous batching of independent hydro problems on one device."""
+
+    def __init__(self, device=0, hbm_budget=0, max_slots=64, variant="default"):
+        self.L = lib(variant)
+        h = ctypes.c_void_p()
+        rc = self.L.serve_create(ctypes.byref(h), int(device), int(hbm_budget), int(max_slots))
+        if rc:
+            raise HydroError(rc, "serve_create")
+        self.h = h
+        self._bufs = {}
+
+    def serve_submit(self, kind, n, steps, gamma=1.4, cfl=0.5, rho_l=1.0, p_l=1.0, rho_r=0.125, p_r=0.1,
+                     energy=1.0, p_ambient=1e-5, want_state=False):
+        """Queue a request; returns its id.  want_state: keep a host copy of the final grown state."""
+        import numpy as np
+        r = hydro_request_t(kind, n, steps, gamma, cfl, rho_l, p_l, rho_r, p_r, energy, p_ambient, None)
+        buf = None
+        if want_state:
+            buf = np.empty((5, n + 2 * NG, n + 2 * NG, n + 2 * NG), dtype=np.float64)
+            r.result_host = buf.ctypes.data
+        rid = ctypes.c_uint64(0)
+        rc = self.L.serve_submit(self.h, ctypes.byref(r), ctypes.byref(rid))
+        if rc:
+            raise HydroError(rc, "serve_submit")
+        self._bufs[rid.value] = buf
+        return rid.value
+
+    def serve_poll(self, rid, timeout_ms=-1):
+        """Result dict of a finished request, or None if it is not finished within timeout_ms."""
+        res = hydro_result_t()
+        rc = self.L.serve_poll(self.h, ctypes.c_uint64(rid), ctypes.byref(res), int(timeout_ms))
+        if rc in (HYDRO_EAGAIN, HYDRO_ETIMEDOUT):
+            return None
+        if rc:
+            raise HydroError(rc, "serve_poll")
+        out = {k: getattr(res, k) for k, _ in hydro_result_t._fields_}
+        out["state"] = self._bufs.pop(rid, None)
+        return out
+
+    def serve_stats(self):
+        st = hydro_serve_stats_t()
+        rc = self.L.serve_stats(self.h, ctypes.byref(st))
+        if rc:
+            raise HydroError(rc, "serve_stats")
+        return {k: getattr(st, k) for k, _ in hydro_serve_stats_t._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hydro_api.cu", "hydro_step.cu", "hydro_batch.cu", "hydro_noalloc.cu"]
+SOURCES = ["hydro_api.cu", "hydro_step.cu", "hydro_batch.cu", "hydro_serve.cu", "hydro_noalloc.cu"]
 
 
 def _nvcc():
@@ -51,7 +51,7 @@ def build(force=False, verbose=False):
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         cmd += [os.path.join(CSRC, s) for s in SOURCES]
-        cmd += ["-lcudart"]
+        cmd += ["-lcudart", "-Xcompiler", "-pthread"]
         subprocess.run(cmd, check=True)
     return OUT
 

@@ -22,6 +22,10 @@ struct hydro_ctx {
 };
 
 void hydro_batch_release(hydro_ctx* ctx);
+size_t hydro_batch_pool_bytes(const hydro_ctx* ctx);
+int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                    const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,
+                    int* bad_first_host, int* bad_all_host, cudaStream_t st);
 
 namespace hydro {
 bool valid_params(const hydro_params_t* p);

@@ -431,6 +431,8 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
 
 }  // namespace
 
+size_t hydro_batch_pool_bytes(const hydro_ctx* ctx) { return ctx && ctx->batch ? ctx->batch->scratch_bytes : 0; }
+
 void hydro_batch_release(hydro_ctx* ctx) {
   if (!ctx || !ctx->batch) return;
   hydro_batch_state* S = ctx->batch;
@@ -441,11 +443,18 @@ void hydro_batch_release(hydro_ctx* ctx) {
   ctx->batch = nullptr;
 }
 
-extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
-                                   const hydro_params_t* params, const double* dt_dev, double* dt_next_dev,
-                                   int* bad_box_host, void* stream) {
-  if (!ctx || !in || !out || nbox < 1 || !dt_dev || !valid_params(params)) return HYDRO_EINVAL;
-  const int dim = params->dim;
+// Batched step with per-box parameters (params[b * pstride]); all boxes
+// share params[0].dim.  bad_all_host (nullable, nbox ints) receives every
+// box's bad-state flag, bad_first_host the first bad box index.
+int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                    const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,
+                    int* bad_first_host, int* bad_all_host, cudaStream_t st) {
+  if (!ctx || !in || !out || nbox < 1 || !dt_dev || !params) return HYDRO_EINVAL;
+  const int dim = params[0].dim;
+  for (int b = 0; b < nbox; ++b) {
+    const hydro_params_t* pb = &params[(size_t)b * pstride];
+    if (!valid_params(pb) || pb->dim != dim || pb->flags != params[0].flags) return HYDRO_EINVAL;
+  }
   for (int b = 0; b < nbox; ++b) {
     if (!valid_box(&in[b], dim) || !out[b].u || out[b].ng != NG) return HYDRO_EINVAL;
     if (reinterpret_cast<uintptr_t>(out[b].u) % sizeof(double)) return HYDRO_EINVAL;
@@ -476,17 +485,17 @@ extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, cons
   }
   hydro_batch_state* S = ctx->batch;
   if (!S->tune_loaded) load_tuning(S);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const hydro_params_t* params0 = params;
 
   // plan key: every box's geometry and pointers, the params, the dt arrays
   uint64_t key = 1469598103934665603ull;
   key = fnv(key, &nbox, sizeof nbox);
   key = fnv(key, in, sizeof(hydro_box_t) * nbox);
   key = fnv(key, out, sizeof(hydro_box_t) * nbox);
-  key = fnv(key, params, sizeof(hydro_params_t));
+  for (int b = 0; b < (pstride ? nbox : 1); ++b) key = fnv(key, &params[(size_t)b * pstride], sizeof(hydro_params_t));
   key = fnv(key, &dt_dev, sizeof dt_dev);
   key = fnv(key, &dt_next_dev, sizeof dt_next_dev);
-  const bool tune = !(params->flags & HYDRO_FLAG_NO_AUTOTUNE);
+  const bool tune = !(params0->flags & HYDRO_FLAG_NO_AUTOTUNE);
   key = fnv(key, &tune, sizeof tune);
   Plan* plan = nullptr;
   for (Plan* p : S->plans)
@@ -512,9 +521,10 @@ extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, cons
       B.sg = sgs[b];
       B.s = carve_scratch(S->scratch + off, sgs[b].sc);
       off += (size_t)sgs[b].sc * SCRATCH_FIELDS;
-      B.K = step_const(params, in[b].dx, 1.0);  // dt fields are set on the device every call
+      const hydro_params_t* pb = &params[(size_t)b * pstride];
+      B.K = step_const(pb, in[b].dx, 1.0);  // dt fields are set on the device every call
       for (int a = 0; a < 3; ++a) B.dx[a] = in[b].dx[a];
-      B.cfl = params->cfl;
+      B.cfl = pb->cfl;
     }
     for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
     if (tune) {
@@ -598,17 +608,30 @@ extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, cons
   plan->last_use = ++S->clock;
   if (cudaGraphLaunch(plan->exec, st) != cudaSuccess) return HYDRO_ECUDA;
   ctx->launches += (long long)plan->launches.size() + 2;
-  if (bad_box_host) {
-    std::vector<int> bad(nbox);
-    if (cudaMemcpyAsync(bad.data(), plan->d_bad, nbox * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  if (bad_first_host || bad_all_host) {
+    std::vector<int> tmp;
+    int* bad = bad_all_host;
+    if (!bad) {
+      tmp.resize(nbox);
+      bad = tmp.data();
+    }
+    if (cudaMemcpyAsync(bad, plan->d_bad, nbox * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return HYDRO_ECUDA;
-    *bad_box_host = -1;
+    int first = -1;
     for (int b = 0; b < nbox; ++b)
-      if (bad[b]) { *bad_box_host = b; break; }
-    if (*bad_box_host >= 0) return HYDRO_EBADSTATE;
+      if (bad[b]) { first = b; break; }
+    if (bad_first_host) *bad_first_host = first;
+    if (first >= 0) return HYDRO_EBADSTATE;
   }
   return HYDRO_OK;
+}
+
+extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                                   const hydro_params_t* params, const double* dt_dev, double* dt_next_dev,
+                                   int* bad_box_host, void* stream) {
+  return hydro_batch_run(ctx, in, out, nbox, params, 0, dt_dev, dt_next_dev, bad_box_host, nullptr,
+                         static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax) {

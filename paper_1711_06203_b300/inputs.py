@@ -83,7 +83,7 @@ def sedov(n=128, dim=3, gamma=1.4, E=1.0, rho0=1.0, p_amb=1e-5, radius_zones=4.0
     dx = 1.0 / n
     mask = sedov_deposit_mask(n, dim, radius_zones)
     ndep = int(mask[:, NG:-NG, NG:-NG].sum()) if dim == 2 else int(mask[NG:-NG, NG:-NG, NG:-NG].sum())
-    vol = dx ** dim
+    vol = dx * dx * dx if dim == 3 else dx * dx
     p_dep = (gamma - 1.0) * E / (ndep * vol)
     rho = np.full(mask.shape, rho0)
     p = np.where(mask, p_dep, p_amb)
