@@ -112,6 +112,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, steps, total_ms):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -221,6 +236,50 @@ def bench_batch(args, dev, stream):
             "l2": "working set 3.7 GB of state + scratch, larger than L2"}
 
 
+def bench_serve(args, dev, zone_rate):
+    """Serving stream: a seeded prefix of independent 3-D problems (Sod,
+    Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
+    process at 0.7 x the measured plain capacity (requests/s), served by the
+    continuous-batching server with state resident on the device."""
+    import numpy as np
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    reqs = inputs.serve_requests(args.serve_requests, seed=1711)
+    mean_work = np.mean([r["steps"] * r["n"] ** 3 for r in reqs])
+    expected_work = np.mean([s ** 3 for s in inputs.SERVE_SIDES]) * 55.0
+    capacity = zone_rate / expected_work  # requests per second the plain step sustains
+    rate = 0.7 * capacity
+    arrivals = inputs.poisson_arrivals(len(reqs), rate, seed=1711)
+    torch.cuda.empty_cache()
+    srv = hb.Server(dev.index, max_slots=64)
+    t0 = time.perf_counter()
+    ids = []
+    for r, ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        ids.append(srv.serve_submit(**r))
+    res = [srv.serve_poll(i, timeout_ms=-1) for i in ids]
+    wall = time.perf_counter() - t0
+    st = srv.serve_stats()
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    work = sum(r["zone_updates"] for r in res)
+    ok = sum(1 for r in res if r["status"] == 0)
+    return {"workload": "prefix of a seeded stream of 3-D Sod/Sedov/two-state requests, sides {32..256}, "
+                        "10-100 steps, Poisson arrivals at 0.7 x plain capacity",
+            "requests": len(reqs), "completed_ok": ok, "arrival_rate_per_s": rate,
+            "plain_capacity_requests_per_s": capacity, "mean_work_zone_updates": float(mean_work),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_queue_ms": float(np.mean([r["queue_ms"] for r in res])),
+            "zone_updates_per_s": work / wall, "busy_zone_updates_per_s": st["zone_updates"] / (st["busy_ms"] * 1e-3),
+            "iterations": st["iterations"], "wall_s": wall,
+            "hbm_budget_gb": st["hbm_budget"] / 1e9, "scratch_pool_gb": st["hbm_scratch_pool"] / 1e9}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -276,13 +335,9 @@ def run_ours(args):
     launches = ctx.hydro_ctx_launches() - launches0
     stage_ms, calls = ctx.hydro_ctx_stage_times()
     ctx.hydro_ctx_set_profiling(False)
-    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), dist, dev)
     zones = n ** 3
-    value = world * zones * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(zones, world, args.steps, total_ms)
 
     # end to end: pinned host state in, result out, every step, copies inside the events
     h_in = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
@@ -316,6 +371,9 @@ def run_ours(args):
     batch = None
     if world == 1 and not args.no_batch:
         batch = bench_batch(args, dev, stream)
+    serve = None
+    if world == 1 and args.serve_requests > 0:
+        serve = bench_serve(args, dev, value)
 
     if rank != 0:
         return 0
@@ -344,6 +402,7 @@ def run_ours(args):
         "e2e": {"value": zones / (e2e_ms * 1e-3) * world, "unit": "zone-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "batched_level": batch,
+        "serve": serve,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,
@@ -364,6 +423,7 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="box side (the workload is 128)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-level leg")
+    ap.add_argument("--serve-requests", type=int, default=24, help="served request prefix (0 skips the leg)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

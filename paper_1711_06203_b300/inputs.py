@@ -139,3 +139,33 @@ def level_boxes(nbox=512, seed=1711, gamma=5.0 / 3.0, sides=LEVEL_SIDES):
 def two_state(n, dim=3, gamma=1.4, rhoL=1.0, pL=1.0, rhoR=0.125, pR=0.1, x0=0.5):
     """Planar two-state Riemann problem along x at rest (the served 'two-state' kind)."""
     return sod(n, dim, 0, gamma, (rhoL, 0.0, pL), (rhoR, 0.0, pR), x0)
+
+
+SERVE_SIDES = (32, 64, 96, 128, 192, 256)
+
+
+def serve_requests(count, seed=1711, sides=SERVE_SIDES):
+    """Seeded stream of independent problems for the server: kind uniform over
+    {Sod (gamma 1.4), Sedov (gamma 1.4, E = 1, ambient p = 1e-5), two-state
+    (rho_L, rho_R, p_L, p_R ~ LogNormal(0, 1), gamma from {1.4, 5/3})}, cubic
+    side uniform over `sides`, steps uniform in [10, 100].  Returns a list of
+    keyword dicts (kind 0 = Sod, 1 = Sedov, 2 = two-state)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(count):
+        kind = int(rng.integers(0, 3))
+        n = int(rng.choice(sides))
+        steps = int(rng.integers(10, 101))
+        r = dict(kind=kind, n=n, steps=steps, gamma=1.4)
+        if kind == 2:
+            rl, rr, pl, pr = rng.lognormal(0.0, 1.0, 4)
+            r.update(gamma=float(rng.choice((1.4, 5.0 / 3.0))), rho_l=float(rl), p_l=float(pl), rho_r=float(rr),
+                     p_r=float(pr))
+        reqs.append(r)
+    return reqs
+
+
+def poisson_arrivals(count, rate, seed=1711):
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed + 7)
+    return np.cumsum(rng.exponential(1.0 / rate, count))
