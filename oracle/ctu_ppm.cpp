@@ -242,9 +242,11 @@ void ppm_limit(real ai, real aM, real aP, real chi, real* am, real* ap, real* a6
     if ((D > 0.0 && up > 0.0) || (D < 0.0 && up < 0.0)) aM = 3.0 * ai - 2.0 * aP;
     else if ((D > 0.0 && dn < 0.0) || (D < 0.0 && dn > 0.0)) aP = 3.0 * ai - 2.0 * aM;
   }
-  /* flattening blends the edges toward the zone average */
-  aP = chi * aP + (1.0 - chi) * ai;
-  aM = chi * aM + (1.0 - chi) * ai;
+  /* flattening blends the edges toward the zone average where chi < 1 */
+  if (chi < 1.0) {
+    aP = chi * aP + (1.0 - chi) * ai;
+    aM = chi * aM + (1.0 - chi) * ai;
+  }
   *am = aM; *ap = aP; *a6 = 6.0 * (ai - 0.5 * (aM + aP));
 }
 /* the same for the zone at index 3 of a 7-point line (unit pins) */
@@ -307,11 +309,13 @@ void trace_from_parabola(const real am[5], const real ap[5], const real a6[5], c
     real s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
     real s_p = ref[4] - (bm * c2 + bp * c2);
     real s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
-    /* half-step gravity on every velocity component, then floors */
-    real hdt = 0.5 * dt;
-    s_un = s_un + hdt * P.grav[d];
-    s_t1 = s_t1 + hdt * P.grav[t1];
-    s_t2 = s_t2 + hdt * P.grav[t2];
+    /* half-step gravity on every velocity component (none without gravity), then floors */
+    if (P.grav[0] != 0.0 || P.grav[1] != 0.0 || P.grav[2] != 0.0) {
+      real hdt = 0.5 * dt;
+      s_un = s_un + hdt * P.grav[d];
+      s_t1 = s_t1 + hdt * P.grav[t1];
+      s_t2 = s_t2 + hdt * P.grav[t2];
+    }
     s_rho = rmax(s_rho, real(P.small_dens));
     s_p = rmax(s_p, real(P.small_pres));
     real* out = side ? qp : qm;

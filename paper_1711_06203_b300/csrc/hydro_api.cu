@@ -125,8 +125,8 @@ Scratch carve_scratch(double* base, long long sc) {
   double* p = base;
   auto take = [&](int nf) { double* r = p; p += (long long)nf * sc; return r; };
   s.Q = take(NQ);
-  for (int d = 0; d < 3; ++d) s.TM[d] = take(5);
-  for (int d = 0; d < 3; ++d) s.TP[d] = take(5);
+  for (int d = 0; d < 3; ++d) s.TM[d] = take(TS_FIELDS);
+  for (int d = 0; d < 3; ++d) s.TP[d] = take(TS_FIELDS);
   for (int d = 0; d < 3; ++d) s.F1[d] = take(5);
   for (int d = 0; d < 3; ++d)
     for (int t = 0; t < 3; ++t) s.F2[d][t] = (t == d) ? nullptr : take(5);

@@ -79,7 +79,7 @@ template <int D>
 __global__ void __launch_bounds__(BLOCK) kb_flux1(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first) {
   const int b = blk_box[blockIdx.x];
-  const BatchBox& B = boxes[b];
+  const BatchBox& B = boxes[b];  // the traced-state arrays are written through B.s pointers
   flux1_item<D>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[D], B.K, B.r1[D], item_of(box_first, b));
 }
 

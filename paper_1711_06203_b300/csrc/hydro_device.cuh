@@ -33,36 +33,51 @@ struct StepConst {
 // lanes/clock/SM as an FMA, so every comparison of doubles here is done on
 // the integer pipe from the bit pattern.  For finite (and infinite) values
 // these reproduce IEEE comparison exactly, including +0 == -0.
+// The compares themselves are inline PTX on 64-bit integers, so that the
+// compiler cannot fold a bit-pattern compare back into an FP64 compare.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
-// x > 0: positive sign and nonzero magnitude
-__device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }
-// x < 0 <=> -x > 0
-__device__ __forceinline__ bool lt0(double x) {
-  return (dbits(x) ^ (long long)0x8000000000000000ULL) > 0;
+// signed 64-bit a < b, evaluated on the integer pipe
+__device__ __forceinline__ bool ilt(long long a, long long b) {
+  int r;
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.s64 p, %1, %2;\n\tselp.s32 %0, 1, 0, p;\n\t}" : "=r"(r) : "l"(a), "l"(b));
+  return r != 0;
 }
+// x > 0: positive sign and nonzero magnitude
+__device__ __forceinline__ bool gt0(double x) { return ilt(0, dbits(x)); }
+// x < 0 <=> -x > 0
+__device__ __forceinline__ bool lt0(double x) { return ilt(0, dbits(x) ^ (long long)0x8000000000000000ULL); }
 __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }
 // order key: monotone in x, equal for +0 and -0
 __device__ __forceinline__ long long okey(double x) {
   long long b = dbits(x);
   return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFLL);
 }
-__device__ __forceinline__ bool dless(double a, double b) { return okey(a) < okey(b); }
+__device__ __forceinline__ bool dless(double a, double b) { return ilt(okey(a), okey(b)); }
 // min/max as explicit selects: ties return the first argument
 __device__ __forceinline__ double dmin(double a, double b) { return dless(b, a) ? b : a; }
 __device__ __forceinline__ double dmax(double a, double b) { return dless(a, b) ? b : a; }
 // operands known to be >= +0 (magnitudes, pressures, speeds): raw bits order
-__device__ __forceinline__ double dmin_nn(double a, double b) { return dbits(b) < dbits(a) ? b : a; }
-__device__ __forceinline__ double dmax_nn(double a, double b) { return dbits(a) < dbits(b) ? b : a; }
+__device__ __forceinline__ double dmin_nn(double a, double b) { return ilt(dbits(b), dbits(a)) ? b : a; }
+__device__ __forceinline__ double dmax_nn(double a, double b) { return ilt(dbits(a), dbits(b)) ? b : a; }
 // |x| > y for y >= +0
-__device__ __forceinline__ bool abs_gt(double x, double y) { return (dbits(x) & 0x7FFFFFFFFFFFFFFFLL) > dbits(y); }
+__device__ __forceinline__ bool abs_gt(double x, double y) {
+  return ilt(dbits(y), dbits(x) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// signed 64-bit a != b on the integer pipe (a bit-pattern "x != 0" written in
+// C would be recognised as the FP64 compare x != 0.0)
+__device__ __forceinline__ bool ine(long long a, long long b) {
+  int r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.s64 p, %1, %2;\n\tselp.s32 %0, 1, 0, p;\n\t}" : "=r"(r) : "l"(a), "l"(b));
+  return r != 0;
+}
 // a and b nonzero with the same sign
 __device__ __forceinline__ bool same_sign_strict(double a, double b) {
   long long ba = dbits(a), bb = dbits(b);
-  bool nz = ((ba << 1) != 0) & ((bb << 1) != 0);
-  return nz & ((ba ^ bb) >= 0);
+  bool nz = ine(ba << 1, 0) & ine(bb << 1, 0);
+  return nz & !ilt(ba ^ bb, 0);
 }
 // finite: exponent field not all ones
-__device__ __forceinline__ bool dfinite(double x) { return ((dbits(x) >> 52) & 0x7FF) != 0x7FF; }
+__device__ __forceinline__ bool dfinite(double x) { return ine((dbits(x) >> 52) & 0x7FF, 0x7FF); }
 
 // ---------------------------------------------------------------- EOS
 // conserved -> primitive with floors; sets *bad for a non-physical state
@@ -149,8 +164,10 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
     if (same_sign_strict(D, up)) aM = 3.0 * ai - 2.0 * aP;
     else if ((gt0(D) && lt0(dn)) || (lt0(D) && gt0(dn))) aP = 3.0 * ai - 2.0 * aM;
   }
-  aP = chi * aP + (1.0 - chi) * ai;
-  aM = chi * aM + (1.0 - chi) * ai;
+  if (ilt(dbits(chi), dbits(1.0))) {  // chi < 1 (chi is in [0, 1]): blend toward the average
+    aP = chi * aP + (1.0 - chi) * ai;
+    aM = chi * aM + (1.0 - chi) * ai;
+  }
   am = aM; ap = aP; a6 = 6.0 * (ai - 0.5 * (aM + aP));
 }
 

@@ -110,11 +110,14 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
     double s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
     double s_p = ref[4] - (bm * c2 + bp * c2);
     double s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
-    s_un = s_un + K.hdt * K.grav[D];
-    s_t1 = s_t1 + K.hdt * K.grav[T1];
-    s_t2 = s_t2 + K.hdt * K.grav[T2];
+    if (K.has_grav) {
+      s_un = s_un + K.hdt * K.grav[D];
+      s_t1 = s_t1 + K.hdt * K.grav[T1];
+      s_t2 = s_t2 + K.hdt * K.grav[T2];
+    }
     s_rho = dmax(s_rho, K.small_dens);
     s_p = dmax(s_p, K.small_pres);
+    // primitive form; the first Riemann solve adds the conserved form
     double* out = side ? TP : TM;
     out[0 * sc + id] = s_rho;
     out[(1 + D) * sc + id] = s_un;
@@ -222,6 +225,19 @@ __device__ __forceinline__ void load5(const double* __restrict__ A, long long sc
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = A[c * sc + id];
 }
+// face state of a traced state for its (only) first Riemann solve; the
+// conserved form (rho*u, rho*v, rho*w, rho*E) is stored beside the primitive
+// fields, since the transverse corrections update it three more times
+__device__ __forceinline__ void traced_state(double* __restrict__ T, long long sc, long long id,
+                                             const StepConst& K, double s[NS]) {
+  double q[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) q[c] = T[c * sc + id];
+  state_from_prim(q, K, s);
+#pragma unroll
+  for (int c = 1; c < 4; ++c) T[(TS_MOM + c - 1) * sc + id] = q[0] * q[c];
+  T[TS_E * sc + id] = s[S_E];
+}
 __device__ __forceinline__ void store5(double* __restrict__ A, long long sc, long long id, const double v[5]) {
 #pragma unroll
   for (int c = 0; c < 5; ++c) A[c * sc + id] = v[c];
@@ -229,32 +245,31 @@ __device__ __forceinline__ void store5(double* __restrict__ A, long long sc, lon
 
 // ---- stage 4a: first Riemann solves from the traced states
 template <int D>
-__device__ __forceinline__ void flux1_item(ScratchGeom sg, const double* __restrict__ TP,
-                                                 const double* __restrict__ TM, double* __restrict__ F1, StepConst K,
-                                                 Range R, long long t) {
+__device__ __forceinline__ void flux1_item(ScratchGeom sg, double* __restrict__ TP, double* __restrict__ TM,
+                                           double* __restrict__ F1, StepConst K, Range R, long long t) {
   int i, j, k;
   if (!range_zone(R, t, i, j, k)) return;
   const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
   const long long id = sg.id(i, j, k);
-  double qL[5], qR[5], sL[NS], sR[NS], F[5];
-  load5(TP, sg.sc, id - st, qL);
-  load5(TM, sg.sc, id, qR);
-  state_from_prim(qL, K, sL);
-  state_from_prim(qR, K, sR);
+  double sL[NS], sR[NS], F[5];
+  traced_state(TP, sg.sc, id - st, K, sL);
+  traced_state(TM, sg.sc, id, K, sR);
   hllc_flux(sL, sR, D, K, F);
   store5(F1, sg.sc, id, F);
 }
 
-// transverse correction of a traced primitive state by one or two flux differences
-__device__ __forceinline__ void correct(const double q[5], const StepConst& K, double ca, const double* Fa,
-                                        long long sc, long long ida_hi, long long ida_lo, double cb,
-                                        const double* Fb, long long idb_hi, long long idb_lo, double s[NS]) {
+// transverse correction of a traced state (conserved form at T[.., id]) by
+// one or two flux differences, back to a face state
+__device__ __forceinline__ void correct(const double* __restrict__ T, long long id, const StepConst& K, double ca,
+                                        const double* Fa, long long sc, long long ida_hi, long long ida_lo,
+                                        double cb, const double* Fb, long long idb_hi, long long idb_lo,
+                                        double s[NS]) {
   double U[5];
-  U[0] = q[0];
-  U[1] = q[0] * q[1];
-  U[2] = q[0] * q[2];
-  U[3] = q[0] * q[3];
-  U[4] = energy_of(q, K);
+  U[0] = T[id];
+  U[1] = T[TS_MOM * sc + id];
+  U[2] = T[(TS_MOM + 1) * sc + id];
+  U[3] = T[(TS_MOM + 2) * sc + id];
+  U[4] = T[TS_E * sc + id];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     U[c] = U[c] - ca * (Fa[c * sc + ida_hi] - Fa[c * sc + ida_lo]);
@@ -274,11 +289,9 @@ __device__ __forceinline__ void flux2_item(ScratchGeom sg, const double* __restr
   const long long stt = (T == 0) ? 1 : (T == 1) ? sg.sy : sg.sz;
   const long long id = sg.id(i, j, k), zl = id - sd;
   const double coef = K.dtdx[T] * THIRD;
-  double qL[5], qR[5], sL[NS], sR[NS], F[5];
-  load5(TP, sg.sc, zl, qL);
-  load5(TM, sg.sc, id, qR);
-  correct(qL, K, coef, F1t, sg.sc, zl + stt, zl, 0.0, nullptr, 0, 0, sL);
-  correct(qR, K, coef, F1t, sg.sc, id + stt, id, 0.0, nullptr, 0, 0, sR);
+  double sL[NS], sR[NS], F[5];
+  correct(TP, zl, K, coef, F1t, sg.sc, zl + stt, zl, 0.0, nullptr, 0, 0, sL);
+  correct(TM, id, K, coef, F1t, sg.sc, id + stt, id, 0.0, nullptr, 0, 0, sR);
   hllc_flux(sL, sR, D, K, F);
   store5(F2, sg.sc, id, F);
 }
@@ -298,13 +311,27 @@ __device__ __forceinline__ void flux3_item(ScratchGeom sg, const double* __restr
   const long long s2 = (T2 == 0) ? 1 : (T2 == 1) ? sg.sy : sg.sz;
   const long long id = sg.id(i, j, k), zl = id - sd;
   const double ca = 0.5 * K.dtdx[T1], cb = 0.5 * K.dtdx[T2];
-  double qL[5], qR[5], sL[NS], sR[NS], F[5];
-  load5(TP, sg.sc, zl, qL);
-  load5(TM, sg.sc, id, qR);
-  correct(qL, K, ca, Fa, sg.sc, zl + s1, zl, cb, Fb, zl + s2, zl, sL);
-  correct(qR, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
+  double sL[NS], sR[NS], F[5];
+  correct(TP, zl, K, ca, Fa, sg.sc, zl + s1, zl, cb, Fb, zl + s2, zl, sL);
+  correct(TM, id, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
   hllc_flux(sL, sR, D, K, F);
   store5(F3, sg.sc, id, F);
+}
+
+// Warp-granular dynamic scheduling: each warp takes the next 32 work items
+// from a cursor until the item space [0, total) is exhausted.  Used by the
+// tracing sweep, whose items (pencil segments) are few and long, so a static
+// grid would leave a partly filled last wave.
+template <typename F>
+__device__ __forceinline__ void for_dynamic_items(unsigned long long* cursor, long long total, F&& body) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= total) return;
+    body((long long)base + lane);
+  }
 }
 
 // block-wide max of three non-negative doubles, then one atomicMax per value

@@ -1,4 +1,6 @@
 // Single-box kernels of the staged CTU-PPM step and their launch sequence.
+#include <algorithm>
+
 #include "hydro_items.cuh"
 
 namespace hydro {
@@ -13,14 +15,29 @@ __global__ void __launch_bounds__(BLOCK) k_prim(BoxGeom in, ScratchGeom sg, doub
 template <int D>
 __global__ void __launch_bounds__(BLOCK) k_trace(ScratchGeom sg, const double* __restrict__ Q,
                                                  double* __restrict__ TM, double* __restrict__ TP, StepConst K,
-                                                 SweepRange R) {
-  trace_item<D>(sg, Q, TM, TP, K, R, (long long)blockIdx.x * BLOCK + threadIdx.x);
+                                                 SweepRange R, unsigned long long* cursor) {
+  for_dynamic_items(cursor, R.count(), [&](long long t) { trace_item<D>(sg, Q, TM, TP, K, R, t); });
+}
+
+// blocks of k_trace<D> that fit on the device at once (queried once per process and device)
+template <int D>
+int trace_resident_blocks() {
+  static int cached[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 1;
+  if (!cached[dev]) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<D>, BLOCK, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = std::max(1, per_sm * sms);
+  }
+  return cached[dev];
 }
 
 template <int D>
-__global__ void __launch_bounds__(BLOCK) k_flux1(ScratchGeom sg, const double* __restrict__ TP,
-                                                 const double* __restrict__ TM, double* __restrict__ F1, StepConst K,
-                                                 Range R) {
+__global__ void __launch_bounds__(BLOCK) k_flux1(ScratchGeom sg, double* __restrict__ TP, double* __restrict__ TM,
+                                                 double* __restrict__ F1, StepConst K, Range R) {
   flux1_item<D>(sg, TP, TM, F1, K, R, (long long)blockIdx.x * BLOCK + threadIdx.x);
 }
 
@@ -57,6 +74,13 @@ __global__ void k_reset_speed(DevFlags* flags) {
   if (threadIdx.x < 3) flags->maxspeed[threadIdx.x] = 0ull;
 }
 
+__global__ void k_reset_step(DevFlags* flags) {
+  if (threadIdx.x < 3) {
+    flags->maxspeed[threadIdx.x] = 0ull;
+    flags->work[threadIdx.x] = 0ull;
+  }
+}
+
 inline unsigned blocks_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
 }  // namespace
@@ -68,6 +92,8 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
     if (a.events) cudaEventRecord(a.events[stage], st);
   };
   mark(ST_PRIM);
+  k_reset_step<<<1, 32, 0, st>>>(a.flags);
+  nl += 1;
   const int* n = a.in.n;
   const ScratchGeom& sg = a.sg;
   const Scratch& s = a.s;
@@ -96,10 +122,11 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
     sw.nd = n[d];
     sw.seg = TRACE_SEG;
     sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
-    unsigned b = blocks_for(sw.count());
-    if (d == 0) k_trace<0><<<b, BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], a.K, sw);
-    if (d == 1) k_trace<1><<<b, BLOCK, 0, st>>>(sg, s.Q, s.TM[1], s.TP[1], a.K, sw);
-    if (d == 2) k_trace<2><<<b, BLOCK, 0, st>>>(sg, s.Q, s.TM[2], s.TP[2], a.K, sw);
+    const unsigned need = blocks_for(sw.count());
+    unsigned long long* cur = &a.flags->work[d];
+    if (d == 0) k_trace<0><<<std::min<unsigned>(need, trace_resident_blocks<0>()), BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], a.K, sw, cur);
+    if (d == 1) k_trace<1><<<std::min<unsigned>(need, trace_resident_blocks<1>()), BLOCK, 0, st>>>(sg, s.Q, s.TM[1], s.TP[1], a.K, sw, cur);
+    if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
   }
   nl += dim;
   mark(ST_FLUX1);
@@ -151,14 +178,13 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
     nl += 1;
   }
   mark(ST_UPDATE);
-  // stage 5: update + CFL partials
-  k_reset_speed<<<1, 32, 0, st>>>(a.flags);
+  // stage 5: update + CFL partials (speed maxima were reset at the start of the step)
   Range ru;
   for (int ax = 0; ax < 3; ++ax) { ru.lo[ax] = 0; ru.ext[ax] = (ax < dim) ? n[ax] : 1; }
   k_update<<<blocks_for(ru.count()), BLOCK, 0, st>>>(a.in, a.out, sg, s.F3[0], s.F3[1], dim == 3 ? s.F3[2] : s.F3[0],
                                                      a.K, ru, a.flags);
   k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], dim, a.cfl);
-  nl += 3;
+  nl += 2;
   mark(NSTAGES);
   if (launches) *launches += nl;
   return cudaGetLastError();

@@ -57,18 +57,21 @@ struct SweepRange {
   __host__ __device__ long long count() const { return (long long)ext1 * ext2 * nseg; }
 };
 
+// fields of a traced face state: rho, u, v, w, p, then rho*u, rho*v, rho*w, rho*E
+enum { TS_MOM = 5, TS_E = 8, TS_FIELDS = 9 };
+
 // scratch field bases
 struct Scratch {
   double* Q;          // NQ fields
-  double* TM[3];      // traced state at each zone's low face, 5 fields
-  double* TP[3];      // traced state at each zone's high face, 5 fields
+  double* TM[3];      // traced state at each zone's low face, TS_FIELDS fields
+  double* TP[3];      // traced state at each zone's high face, TS_FIELDS fields
   double* F1[3];      // first fluxes
   double* F2[3][3];   // intermediate fluxes F^{d|t}
   double* F3[3];      // final fluxes
 };
 
 // number of scratch fields (each one grown box of doubles)
-constexpr int SCRATCH_FIELDS = NQ + 3 * 5 + 3 * 5 + 3 * 5 + 6 * 5 + 3 * 5;
+constexpr int SCRATCH_FIELDS = NQ + 3 * TS_FIELDS + 3 * TS_FIELDS + 3 * 5 + 6 * 5 + 3 * 5;
 
 // device reduction / flag block owned by a context
 struct DevFlags {
@@ -76,6 +79,7 @@ struct DevFlags {
   int bad;                         // sticky non-physical-state flag
   int pad;
   double dt_next;                  // cfl * min_d dx_d / maxspeed_d
+  unsigned long long work[3];      // work cursors of the three tracing sweeps
 };
 
 // stages of a step, timed separately when a context profiles
