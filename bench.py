@@ -236,6 +236,68 @@ def bench_batch(args, dev, stream):
             "l2": "working set 3.7 GB of state + scratch, larger than L2"}
 
 
+def stratified_device(n, dev, H=0.1, g=1.0, gamma=5.0 / 3.0, perturb=1e-3, seed=1711):
+    """Isothermal atmosphere rho = exp(-z/H), p = rho g H (1 + perturb N(0,1)),
+    at rest, built directly on the device (the recipe of inputs.stratified; a
+    520^3 grown box is 5.6 GB per state, too large to stage through host numpy)."""
+    import torch
+    gsz = n + 8
+    z = ((torch.arange(gsz, dtype=torch.float64, device=dev) - 4 + 0.5) / n).view(gsz, 1, 1)
+    rho = torch.exp(-z / H).expand(gsz, gsz, gsz)
+    p = rho * g * H
+    if perturb:
+        gen = torch.Generator(device=dev).manual_seed(seed)
+        p = p * (1.0 + perturb * torch.randn((gsz, gsz, gsz), generator=gen, dtype=torch.float64, device=dev))
+    U = torch.zeros((5, gsz, gsz, gsz), dtype=torch.float64, device=dev)
+    U[0] = rho
+    U[4] = p / (gamma - 1.0)
+    return U
+
+
+def bench_large(args, dev, stream):
+    """Large box: 512^3 stratified atmosphere under g = -1 in z, seeded 1e-3
+    pressure perturbations, periodic x/y, reflecting z, gamma 5/3, CFL 0.5;
+    zone-updates/s and the step's algorithmic HBM traffic against the peak."""
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+
+    n = 512
+    torch.cuda.empty_cache()
+    a = stratified_device(n, dev)
+    b = torch.empty_like(a)
+    bc = ((hb.BC_PERIODIC,) * 2, (hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT,) * 2)
+    p = hb.params(3, gamma=5.0 / 3.0, cfl=0.5, grav=(0.0, 0.0, -1.0))
+    ctx = hb.Context(dev.index)
+
+    def box(t):
+        return hb.box(t, (n, n, n), (1.0 / n,) * 3, bc)
+
+    dt = ctx.hydro_dt(box(a), p, stream)
+    for _ in range(3):
+        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+        a, b = b, a
+    steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+        a, b = b, a
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    ctx.close()
+    del a, b
+    torch.cuda.empty_cache()
+    hbm = algorithmic_bytes_per_step(n) / (ms * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs", 6400.0)
+    return {"workload": "512^3 stratified atmosphere, g = -1 in z, 1e-3 pressure perturbations, periodic x/y, "
+                        "reflecting z", "steps_timed": steps, "ms_per_step": ms,
+            "zone_updates_per_s": n ** 3 / (ms * 1e-3), "hbm_algorithmic_gbs": hbm, "hbm_peak_gbs": peak,
+            "hbm_frac": hbm / peak, "l2": "inputs far larger than L2 (5.6 GB per state)"}
+
+
 def bench_serve(args, dev, zone_rate):
     """Serving stream: a seeded prefix of independent 3-D problems (Sod,
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
@@ -374,6 +436,9 @@ def run_ours(args):
     serve = None
     if world == 1 and args.serve_requests > 0:
         serve = bench_serve(args, dev, value)
+    large = None
+    if world == 1 and not args.no_large:
+        large = bench_large(args, dev, stream)
 
     if rank != 0:
         return 0
@@ -403,6 +468,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": nbytes},
         "batched_level": batch,
         "serve": serve,
+        "large_box": large,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,
@@ -424,6 +490,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-level leg")
     ap.add_argument("--serve-requests", type=int, default=24, help="served request prefix (0 skips the leg)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 512^3 large-box leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
