@@ -39,6 +39,10 @@ LAUNCHES_PER_STEP_3D = {"prim": 2, "trace": 3, "flux1": 3, "flux2": 6, "flux3": 
 # measured 476 G lane-FMA/s = 0.95 TFLOP/s on the B300s.)
 FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per unit of the dominant stage from one ncu
+# capture of the current kernel (k_flux2<0,1>, Sedov 96^3: 135.6 MB for
+# 912,576 solves), scaled to a launch by its units.
+DRAM_BYTES_PER_UNIT = {"flux2": 148.6}
 
 
 def units_per_step(n):
@@ -457,7 +461,10 @@ def run_ours(args):
                    "parallelism": f"replica x{world}"},
         "roofline": {"bound": "alu", "kernel": f"{dom} stage ({LAUNCHES_PER_STEP_3D[dom]} launches/step)",
                      "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_GFLOPS,
+                     "traffic": (DRAM_BYTES_PER_UNIT[dom] * units[dom] / LAUNCHES_PER_STEP_3D[dom]
+                                 if dom in DRAM_BYTES_PER_UNIT else None),
+                     "traffic_note": "bytes per launch: ncu dram read+write of a 96^3 capture, scaled by units",
                      "peak_note": "FP64 derived: 148 SMs x 2 FMA lanes x 2 flop x 2.032 GHz"},
         "hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
                 "note": "algorithmic bytes of the whole step (read grown box, write interior) / step time, of measured"},
