@@ -154,6 +154,29 @@ int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box
                         const hydro_params_t* params, const double* dt_dev, double* dt_next_dev, int* bad_box_host,
                         void* stream);
 
+/* Fill every ghost zone of a level of boxes that tile a rectangular domain
+ * (paper Sec. 3: the AMR library manages a level's grid data and ghost
+ * exchange; Fig. 1: a level of uneven boxes).
+ *  - boxes[b] (host array): the level's boxes (device data); their bc fields
+ *    are ignored.  lo (host, 3*nbox ints): global index of each box's interior
+ *    zone (0,0,0); the boxes must cover [0, domain) exactly, without overlap.
+ *  - domain (host, dim ints): zones per axis; domain_bc (host, 2*dim ints):
+ *    HYDRO_BC_OUTFLOW / REFLECT / PERIODIC for the low and high face of each
+ *    axis (periodic on both faces or neither).
+ *  - Each ghost zone's global index is mapped through the domain boundary kind
+ *    per axis (the same per-axis maps as a single box's derived ghosts) and
+ *    copied from the box owning the zone it lands on.  Only ghost zones are
+ *    written.  Synchronises `stream` (the fill tables are staged per call).
+ *  After the fill, advance the level with hydro_advance_batch on the same
+ *  boxes marked HYDRO_BC_PREFILLED. */
+int hydro_fill_boundary(hydro_ctx_t* ctx, const hydro_box_t* boxes, const int* lo, int nbox, int dim,
+                        const int* domain, const int* domain_bc, void* stream);
+
+/* Level time step: dt_dev[b] = min over all boxes of dt_next_dev[b'] (the AMR
+ * level advances every box with the same dt).  Device arrays of nbox doubles;
+ * enqueued on `stream`. */
+int hydro_level_min_dt(const double* dt_next_dev, double* dt_dev, int nbox, void* stream);
+
 /* The autotuned sweep segments of a context: up to nmax pairs (box extent
  * along the sweep, zones per segment) into the host arrays extent/segment.
  * Returns the number of tuned extents. */

@@ -109,6 +109,9 @@ def lib(variant="default"):
     L.hydro_advance_box_noalloc.argtypes = [B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_batch.argtypes = [vp, B, B, ctypes.c_int, P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    IP = ctypes.POINTER(ctypes.c_int)
+    L.hydro_fill_boundary.argtypes = [vp, B, IP, ctypes.c_int, ctypes.c_int, IP, IP, vp]
+    L.hydro_level_min_dt.argtypes = [vp, vp, ctypes.c_int, vp]
     L.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
     L.serve_submit.argtypes = [vp, ctypes.POINTER(hydro_request_t), ctypes.POINTER(ctypes.c_uint64)]
     L.serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hydro_result_t), ctypes.c_int]
@@ -232,6 +235,24 @@ class Context:
         if not raise_on_error:
             return rc, bad.value
         return bad.value if want_bad else None
+
+    def hydro_fill_boundary(self, boxes, lo, dim, domain, domain_bc, stream=None):
+        """Fill the ghost zones of a level tiling [0, domain): boxes (hydro_box_t list),
+        lo (per-box global corner triples), domain_bc ((lo, hi) kinds per axis)."""
+        n = len(boxes)
+        arr = (hydro_box_t * n)(*boxes)
+        lo_arr = (ctypes.c_int * (3 * n))(*[int(v) for c in lo for v in (tuple(c) + (0,) * (3 - len(c)))])
+        dom = (ctypes.c_int * 3)(*(list(domain) + [1] * (3 - len(domain))))
+        bcs = (ctypes.c_int * 6)(*[int(k) for pair in domain_bc for k in pair] + [0] * (6 - 2 * len(domain_bc)))
+        rc = self.L.hydro_fill_boundary(self.h, arr, lo_arr, n, dim, dom, bcs, _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_fill_boundary")
+
+    def hydro_level_min_dt(self, dt_next_dev, dt_dev, stream=None):
+        rc = self.L.hydro_level_min_dt(ctypes.c_void_p(dt_next_dev.data_ptr()), ctypes.c_void_p(dt_dev.data_ptr()),
+                                       dt_dev.numel(), _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_level_min_dt")
 
     def hydro_batch_tuning(self):
         ext = (ctypes.c_int * 64)()

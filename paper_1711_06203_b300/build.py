@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hydro_api.cu", "hydro_step.cu", "hydro_batch.cu", "hydro_serve.cu", "hydro_noalloc.cu"]
+SOURCES = ["hydro_api.cu", "hydro_step.cu", "hydro_batch.cu", "hydro_level.cu", "hydro_serve.cu",
+           "hydro_noalloc.cu"]
 
 
 def _nvcc():

@@ -169,3 +169,28 @@ def poisson_arrivals(count, rate, seed=1711):
     """Arrival times (seconds from 0) of a Poisson process of the given rate."""
     rng = np.random.default_rng(seed + 7)
     return np.cumsum(rng.exponential(1.0 / rate, count))
+
+
+def level_tiling(domain, sides=LEVEL_SIDES, seed=1711):
+    """Cut a rectangular domain into a level of uneven boxes: along each axis
+    the domain is split into consecutive pieces with lengths drawn from `sides`
+    (the last piece takes the remainder, which must be a multiple of 8).
+    Returns (lo corners, sizes) of the product tiling, x fastest."""
+    rng = np.random.default_rng(seed)
+    cuts = []
+    for n in domain:
+        pieces, pos = [], 0
+        while pos < n:
+            s = int(rng.choice(sides))
+            if pos + s > n:
+                s = n - pos
+            pieces.append((pos, s))
+            pos += s
+        cuts.append(pieces)
+    lo, sizes = [], []
+    for (z0, nz) in (cuts[2] if len(domain) == 3 else [(0, 1)]):
+        for (y0, ny) in cuts[1]:
+            for (x0, nx) in cuts[0]:
+                lo.append((x0, y0, z0))
+                sizes.append((nx, ny, nz))
+    return lo, sizes
