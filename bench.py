@@ -302,6 +302,81 @@ def bench_large(args, dev, stream):
             "hbm_frac": hbm / peak, "l2": "inputs far larger than L2 (5.6 GB per state)"}
 
 
+def bench_level(args, dev, stream):
+    """Multi-step level advance: a 192^3 domain (periodic x, reflecting y,
+    outflow z) tiled by uneven boxes (sides from {16,24,32,48,64}, seed 1711),
+    random initial state; every step is a device ghost fill, a batched
+    graph-replayed step and the level dt reduction, with no host
+    synchronisation.  Compared with the single box covering the domain."""
+    import numpy as np
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    domain = (192, 192, 192)
+    lo, sizes = inputs.level_tiling(domain, seed=1711)
+    U = inputs.random_box(np.random.default_rng(1711), domain, 3)
+    bc = ((hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT,) * 2, (hb.BC_OUTFLOW,) * 2)
+    dx = (1.0 / 192,) * 3
+    p = hb.params(3, gamma=5.0 / 3.0, cfl=0.5)
+    ctx = hb.Context(dev.index)
+    a = []
+    for c, s in zip(lo, sizes):
+        B = np.zeros((5, s[2] + 8, s[1] + 8, s[0] + 8))
+        B[:, 4:-4, 4:-4, 4:-4] = U[:, 4 + c[2]:4 + c[2] + s[2], 4 + c[1]:4 + c[1] + s[1], 4 + c[0]:4 + c[0] + s[0]]
+        a.append(torch.from_numpy(B).to(dev))
+    b = [torch.empty_like(x) for x in a]
+    da = [hb.box(t, s, dx, hb.BC_PREFILLED) for t, s in zip(a, sizes)]
+    db = [hb.box(t, s, dx, hb.BC_PREFILLED) for t, s in zip(b, sizes)]
+    big = torch.from_numpy(U).to(dev)
+    big2 = torch.empty_like(big)
+    dt0 = ctx.hydro_dt(hb.box(big, domain, dx, bc), p, stream)
+    dt_dev = torch.full((len(sizes),), dt0, dtype=torch.float64, device=dev)
+    dt_next = torch.empty_like(dt_dev)
+
+    def level_step():
+        nonlocal da, db
+        ctx.hydro_fill_boundary(da, lo, 3, domain, bc, stream=stream)
+        ctx.hydro_advance_batch(da, db, p, dt_dev, dt_next, stream=stream)
+        ctx.hydro_level_min_dt(dt_next, dt_dev, stream=stream)
+        da, db = db, da
+
+    steps = max(4, min(args.steps, 10))
+    for _ in range(4):  # plans for both parities, tuning, graphs
+        level_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        level_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_level = e0.elapsed_time(e1) / steps
+    dt = dt0
+    for _ in range(2):
+        dt = ctx.hydro_advance_box(hb.box(big, domain, dx, bc), hb.box(big2, domain, dx, bc), p, dt,
+                                   want_dt_next=True, stream=stream)
+        big, big2 = big2, big
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        dt = ctx.hydro_advance_box(hb.box(big, domain, dx, bc), hb.box(big2, domain, dx, bc), p, dt,
+                                   want_dt_next=True, stream=stream)
+        big, big2 = big2, big
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_single = e0.elapsed_time(e1) / steps
+    ctx.close()
+    zones = domain[0] * domain[1] * domain[2]
+    return {"workload": f"192^3 domain tiled by {len(sizes)} uneven boxes (sides from {{16,24,32,48,64}}), "
+                        "periodic x / reflecting y / outflow z, random state",
+            "boxes": len(sizes), "steps_timed": steps, "ms_per_step": ms_level,
+            "zone_updates_per_s": zones / (ms_level * 1e-3), "single_box_ms_per_step": ms_single,
+            "single_box_zone_updates_per_s": zones / (ms_single * 1e-3),
+            "host_syncs_per_step": 0}
+
+
 def bench_serve(args, dev, zone_rate):
     """Serving stream: a seeded prefix of independent 3-D problems (Sod,
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
@@ -440,6 +515,9 @@ def run_ours(args):
     serve = None
     if world == 1 and args.serve_requests > 0:
         serve = bench_serve(args, dev, value)
+    level = None
+    if world == 1 and not args.no_batch:
+        level = bench_level(args, dev, stream)
     large = None
     if world == 1 and not args.no_large:
         large = bench_large(args, dev, stream)
@@ -476,6 +554,7 @@ def run_ours(args):
         "batched_level": batch,
         "serve": serve,
         "large_box": large,
+        "level_multistep": level,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,

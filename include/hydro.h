@@ -166,7 +166,8 @@ int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box
  *  - Each ghost zone's global index is mapped through the domain boundary kind
  *    per axis (the same per-axis maps as a single box's derived ghosts) and
  *    copied from the box owning the zone it lands on.  Only ghost zones are
- *    written.  Synchronises `stream` (the fill tables are staged per call).
+ *    written.  Asynchronous on `stream`; the fill tables of a level are built
+ *    on the first call and kept in the context (the 8 most recent levels).
  *  After the fill, advance the level with hydro_advance_batch on the same
  *  boxes marked HYDRO_BC_PREFILLED. */
 int hydro_fill_boundary(hydro_ctx_t* ctx, const hydro_box_t* boxes, const int* lo, int nbox, int dim,

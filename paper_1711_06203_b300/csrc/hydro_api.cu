@@ -229,6 +229,7 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
   for (auto& e : ctx->events)
     if (e) cudaEventDestroy(e);
   hydro_batch_release(ctx);
+  hydro_level_release(ctx);
   delete ctx;
 }
 

@@ -6,6 +6,7 @@
 #include "hydro_step.cuh"
 
 struct hydro_batch_state;
+struct hydro_level_state;
 
 struct hydro_ctx {
   int device = 0;
@@ -14,6 +15,7 @@ struct hydro_ctx {
   hydro::DevFlags* flags = nullptr;
   int fail_alloc = 0;             // test hook: make the next scratch allocation fail
   hydro_batch_state* batch = nullptr;
+  hydro_level_state* level = nullptr;
   long long launches = 0;         // kernels enqueued by this context
   int profiling = 0;              // record stage events around each step
   cudaEvent_t events[hydro::NSTAGES + 1] = {};
@@ -22,6 +24,7 @@ struct hydro_ctx {
 };
 
 void hydro_batch_release(hydro_ctx* ctx);
+void hydro_level_release(hydro_ctx* ctx);
 size_t hydro_batch_pool_bytes(const hydro_ctx* ctx);
 int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
                     const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <cstdint>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -107,6 +108,21 @@ __global__ void k_level_min_dt(const double* __restrict__ dt_next, double* __res
 
 }  // namespace
 
+struct FillPlan {
+  uint64_t key = 0;
+  char* mem = nullptr;  // FillBox[nbox], box_first[nbox], blk_box[nblocks], owner map
+  int nbox = 0;
+  unsigned nblocks = 0;
+  size_t nown = 0;
+  FillGeom F{};
+  uint64_t last_use = 0;
+};
+
+struct hydro_level_state {
+  std::vector<FillPlan> plans;
+  uint64_t clock = 0;
+};
+
 extern "C" int hydro_fill_boundary(hydro_ctx_t* ctx, const hydro_box_t* boxes, const int* lo, int nbox, int dim,
                                    const int* domain, const int* domain_bc, void* stream) {
   if (!ctx || !boxes || !lo || !domain || !domain_bc || nbox < 1 || (dim != 2 && dim != 3)) return HYDRO_EINVAL;
@@ -173,37 +189,81 @@ extern "C" int hydro_fill_boundary(hydro_ctx_t* ctx, const hydro_box_t* boxes, c
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return HYDRO_ECUDA;
   if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return HYDRO_ECUDA;
+  struct Restore {
+    int dev, prev;
+    ~Restore() { if (prev >= 0 && prev != dev) cudaSetDevice(prev); }
+  } restore{ctx->device, prev};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // table memory lives for the call: stream-ordered allocation, freed after the launch
-  size_t bytes = nbox * sizeof(FillBox) + (nbox + blk.size() + own.size()) * sizeof(int);
-  char* mem = nullptr;
-  int rc = HYDRO_OK;
-  if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) {
-    cudaGetLastError();
-    rc = HYDRO_ENOMEM;
-  } else {
-    FillBox* d_boxes = reinterpret_cast<FillBox*>(mem);
-    int* d_first = reinterpret_cast<int*>(mem + nbox * sizeof(FillBox));
-    int* d_blk = d_first + nbox;
-    int* d_own = d_blk + blk.size();
+
+  // the fill tables of a level (a plan) are kept on the device and reused by
+  // later calls with the same boxes, corners and domain
+  if (!ctx->level) {
+    ctx->level = new (std::nothrow) hydro_level_state();
+    if (!ctx->level) return HYDRO_ENOMEM;
+  }
+  hydro_level_state* L = ctx->level;
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) key = (key ^ c[i]) * 1099511628211ull;
+  };
+  mix(&nbox, sizeof nbox);
+  mix(boxes, nbox * sizeof(hydro_box_t));
+  mix(lo, 3 * nbox * sizeof(int));
+  mix(&F, sizeof F);
+  FillPlan* plan = nullptr;
+  for (FillPlan& p : L->plans)
+    if (p.key == key) plan = &p;
+  if (!plan) {
+    const size_t bytes = nbox * sizeof(FillBox) + (nbox + blk.size() + own.size()) * sizeof(int);
+    char* mem = nullptr;
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return HYDRO_ENOMEM;
+    }
     std::vector<char> host(bytes);
     std::memcpy(host.data(), fb.data(), nbox * sizeof(FillBox));
     std::memcpy(host.data() + nbox * sizeof(FillBox), first.data(), nbox * sizeof(int));
     std::memcpy(host.data() + nbox * sizeof(FillBox) + nbox * sizeof(int), blk.data(), blk.size() * sizeof(int));
     std::memcpy(host.data() + nbox * sizeof(FillBox) + (nbox + blk.size()) * sizeof(int), own.data(),
                 own.size() * sizeof(int));
-    if (cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = HYDRO_ECUDA;
-    if (rc == HYDRO_OK) {
-      kf_fill<<<(unsigned)blk.size(), FBLOCK, 0, st>>>(d_boxes, d_blk, d_first, d_own, F);
-      ctx->launches += 1;
-      if (cudaGetLastError() != cudaSuccess) rc = HYDRO_ECUDA;
+    if (cudaMemcpy(mem, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(mem);
+      return HYDRO_ECUDA;
     }
-    // the pageable host buffer must outlive the copy: wait for it
-    if (cudaStreamSynchronize(st) != cudaSuccess && rc == HYDRO_OK) rc = HYDRO_ECUDA;
-    cudaFreeAsync(mem, st);
+    if (L->plans.size() >= 8) {
+      // drop the least recently used plan once the device is done with it
+      auto lru = std::min_element(L->plans.begin(), L->plans.end(),
+                                  [](const FillPlan& x, const FillPlan& y) { return x.last_use < y.last_use; });
+      if (cudaDeviceSynchronize() != cudaSuccess) return HYDRO_ECUDA;
+      cudaFree(lru->mem);
+      L->plans.erase(lru);
+    }
+    FillPlan np;
+    np.key = key;
+    np.mem = mem;
+    np.nbox = nbox;
+    np.nblocks = (unsigned)blk.size();
+    np.nown = own.size();
+    np.F = F;
+    L->plans.push_back(np);
+    plan = &L->plans.back();
   }
-  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
-  return rc;
+  plan->last_use = ++L->clock;
+  FillBox* d_boxes = reinterpret_cast<FillBox*>(plan->mem);
+  int* d_first = reinterpret_cast<int*>(plan->mem + plan->nbox * sizeof(FillBox));
+  int* d_blk = d_first + plan->nbox;
+  int* d_own = d_blk + plan->nblocks;
+  kf_fill<<<plan->nblocks, FBLOCK, 0, st>>>(d_boxes, d_blk, d_first, d_own, plan->F);
+  ctx->launches += 1;
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+void hydro_level_release(hydro_ctx* ctx) {
+  if (!ctx || !ctx->level) return;
+  for (FillPlan& p : ctx->level->plans) cudaFree(p.mem);
+  delete ctx->level;
+  ctx->level = nullptr;
 }
 
 extern "C" int hydro_level_min_dt(const double* dt_next_dev, double* dt_dev, int nbox, void* stream) {
