@@ -377,6 +377,44 @@ def bench_level(args, dev, stream):
             "host_syncs_per_step": 0}
 
 
+def bench_options(args, dev, stream):
+    """Cost of the step's options on the bench workload (Sedov 128^3): Einfeldt
+    wave speeds, and the flux-form gravity energy source (with g = -1 in z)."""
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    n = 128
+    U0, _ = inputs.sedov(n)
+    ctx = hb.Context(dev.index)
+    out = {}
+    for name, kw in (("davis", {}), ("einfeldt", dict(einfeldt=True)),
+                     ("gravity_cell", dict(grav=(0.0, 0.0, -1.0))),
+                     ("gravity_flux", dict(grav=(0.0, 0.0, -1.0), flux_grav_energy=True))):
+        p = hb.params(3, gamma=1.4, cfl=0.5, **kw)
+        a = torch.from_numpy(U0).to(dev)
+        b = torch.empty_like(a)
+        box = lambda t: hb.box(t, (n, n, n), (1.0 / n,) * 3, hb.BC_OUTFLOW)
+        dt = ctx.hydro_dt(box(a), p, stream)
+        for _ in range(3):
+            dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+            a, b = b, a
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k = 5
+        for _ in range(k):
+            dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / k
+        out[name] = {"ms_per_step": ms, "zone_updates_per_s": n ** 3 / (ms * 1e-3)}
+    ctx.close()
+    return out
+
+
 def bench_serve(args, dev, zone_rate):
     """Serving stream: a seeded prefix of independent 3-D problems (Sod,
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
@@ -516,8 +554,10 @@ def run_ours(args):
     if world == 1 and args.serve_requests > 0:
         serve = bench_serve(args, dev, value)
     level = None
+    options = None
     if world == 1 and not args.no_batch:
         level = bench_level(args, dev, stream)
+        options = bench_options(args, dev, stream)
     large = None
     if world == 1 and not args.no_large:
         large = bench_large(args, dev, stream)
@@ -555,6 +595,7 @@ def run_ours(args):
         "serve": serve,
         "large_box": large,
         "level_multistep": level,
+        "options": options,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,

@@ -71,6 +71,9 @@ enum {
 /* hydro_params_t.flags */
 #define HYDRO_FLAG_NO_FLATTEN 1u  /* disable Colella-Woodward flattening */
 #define HYDRO_FLAG_NO_AUTOTUNE 2u /* hydro_advance_batch: fixed 16-zone sweep segments, no timing runs */
+#define HYDRO_FLAG_EINFELDT 4u     /* HLLC outer speeds from Roe averages (Einfeldt) instead of Davis */
+#define HYDRO_FLAG_FLUX_GRAV_ENERGY 8u /* gravity energy source from the face mass fluxes (balances the
+                                          potential energy exactly) instead of the cell-centred form */
 
 typedef struct {
   double gamma;       /* gamma-law EOS exponent, > 1 */
@@ -182,6 +185,18 @@ int hydro_level_min_dt(const double* dt_next_dev, double* dt_dev, int nbox, void
  * along the sweep, zones per segment) into the host arrays extent/segment.
  * Returns the number of tuned extents. */
 int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
+
+/* hydro_advance_box with the retry mechanism of paper Sec. 3.2 (Castro can
+ * redo a step based on criteria evaluated during the integration): if the
+ * step meets a non-physical state (rho <= 0, p <= 0 or non-finite, in the
+ * input or the result), it is redone from the untouched input with half the
+ * time step, up to max_retries (0..60) times.  *dt_taken_host (host,
+ * nullable) receives the step that succeeded, *dt_next_host (nullable) the
+ * CFL step of its result.  Synchronises `stream` after every attempt.
+ * HYDRO_EBADSTATE if every attempt failed (e.g. a bad input state). */
+int hydro_advance_box_retry(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                            const hydro_params_t* params, double dt, int max_retries, double* dt_taken_host,
+                            double* dt_next_host, void* stream);
 
 /* Report and clear the context's sticky bad-state flag: synchronises the
  * context's device, returns HYDRO_EBADSTATE if any step since the last check

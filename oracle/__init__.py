@@ -27,6 +27,8 @@ class Params(ctypes.Structure):
         ("small_dens", ctypes.c_double),
         ("small_pres", ctypes.c_double),
         ("flatten", ctypes.c_int),
+        ("wave_speeds", ctypes.c_int),
+        ("grav_energy", ctypes.c_int),
     ]
 
 
@@ -56,6 +58,7 @@ def _lib(counting=False):
         lib.oracle_dt.argtypes = [_D, P, _D]
         lib.oracle_step.argtypes = [_D, _D, P, ctypes.c_double, ctypes.POINTER(Debug)]
         lib.oracle_hllc.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, _D]
+        lib.oracle_wave_speeds.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
         lib.oracle_ppm_parabola.argtypes = [_D, ctypes.c_double, _D]
         lib.oracle_flatten.argtypes = [_D, _D, ctypes.c_double]
         lib.oracle_flatten.restype = ctypes.c_double
@@ -80,7 +83,7 @@ def _ptr(a):
 
 
 def params(dim, n, dx=None, bc=BC_OUTFLOW, gamma=1.4, cfl=0.5, grav=(0.0, 0.0, 0.0),
-           small_dens=1e-200, small_pres=1e-200, flatten=True):
+           small_dens=1e-200, small_pres=1e-200, flatten=True, einfeldt=False, flux_grav_energy=False):
     """Build a Params struct.  n: interior (nx, ny[, nz]); bc: one kind for
     every face, or a 3x2 nested sequence."""
     n = tuple(n) + (1,) * (3 - len(n))
@@ -97,6 +100,8 @@ def params(dim, n, dx=None, bc=BC_OUTFLOW, gamma=1.4, cfl=0.5, grav=(0.0, 0.0, 0
     P.gamma, P.cfl = gamma, cfl
     P.small_dens, P.small_pres = small_dens, small_pres
     P.flatten = 1 if flatten else 0
+    P.wave_speeds = 1 if einfeldt else 0
+    P.grav_energy = 1 if flux_grav_energy else 0
     return P
 
 
@@ -192,6 +197,14 @@ def hllc(qL, qR, d, gamma):
     F = np.zeros(5)
     _lib().oracle_hllc(_ptr(qL), _ptr(qR), d, gamma, _ptr(F))
     return F
+
+
+def wave_speeds(qL, qR, d, gamma, einfeldt):
+    out = np.zeros(2)
+    _lib().oracle_wave_speeds(_ptr(np.ascontiguousarray(qL, dtype=np.float64)),
+                              _ptr(np.ascontiguousarray(qR, dtype=np.float64)), d, gamma, 1 if einfeldt else 0,
+                              _ptr(out))
+    return out
 
 
 def ppm_parabola(line7, chi=1.0):

@@ -381,15 +381,41 @@ void trace_pencil(const std::vector<real>* Q, long base, long st, int nd, int d,
   }
 }
 
+/* outer wave-speed estimates of the HLLC fan.
+ * Davis: S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R).
+ * Einfeldt: S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~) with
+ * the Roe averages u~ = (sqrt(rho_L) u_L + sqrt(rho_R) u_R)/(sqrt(rho_L) + sqrt(rho_R)),
+ * H~ likewise from the specific enthalpies H = (rho E + p)/rho, and
+ * c~^2 = (gamma - 1)(H~ - |u~|^2/2). */
+void wave_speeds(const real sL[NS], const real sR[NS], int d, double gamma, int einfeldt, real cl, real cr,
+                 real* sl, real* sr) {
+  real ul = sL[1 + d], ur = sR[1 + d];
+  if (!einfeldt) {
+    *sl = rmin(ul - cl, ur - cr);
+    *sr = rmax(ul + cl, ur + cr);
+    return;
+  }
+  real ql = sqrt(sL[S_RHO]), qr = sqrt(sR[S_RHO]);
+  real iw = 1.0 / (ql + qr);
+  real wl = ql * iw, wr = qr * iw;
+  real ut[3];
+  for (int k = 0; k < 3; ++k) ut[k] = wl * sL[1 + k] + wr * sR[1 + k];
+  real hl = (sL[S_E] + sL[S_P]) * sL[S_INV], hr = (sR[S_E] + sR[S_P]) * sR[S_INV];
+  real ht = wl * hl + wr * hr;
+  real q2 = (ut[0] * ut[0] + ut[1] * ut[1]) + ut[2] * ut[2];
+  real ct = sqrt((gamma - 1.0) * (ht - 0.5 * q2));
+  *sl = rmin(ul - cl, ut[d] - ct);
+  *sr = rmax(ur + cr, ut[d] + ct);
+}
+
 /* ---- Step 7: HLLC flux in direction d (Toro, Spruce & Speares 1994) ----
  * sL, sR: face states (rho, u, v, w, p, rho*E, 1/rho) left and right of the face. */
-void hllc(const real sL[NS], const real sR[NS], int d, double gamma, real F[5]) {
+void hllc(const real sL[NS], const real sR[NS], int d, double gamma, int einfeldt, real F[5]) {
   real rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
   real rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
   real cl = sound_speed(pl, sL[S_INV], gamma), cr = sound_speed(pr, sR[S_INV], gamma);
-  /* Davis wave-speed estimates */
-  real sl = rmin(ul - cl, ur - cr);
-  real sr = rmax(ul + cl, ur + cr);
+  real sl, sr;
+  wave_speeds(sL, sR, d, gamma, einfeldt, cl, cr, &sl, &sr);
   real ml = rl * (sl - ul), mr = rr * (sr - ur); /* mass fluxes through the outer waves */
   real sstar = ((pr - pl) + ml * ul - mr * ur) / (ml - mr);
   /* select the region containing x/t = 0, tested in this order:
@@ -583,7 +609,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
           TM[d].get(id, qR);
           state_from_prim(qL, K, sL);
           state_from_prim(qR, K, sR);
-          hllc(sL, sR, d, P->gamma, F);
+          hllc(sL, sR, d, P->gamma, P->wave_speeds, F);
           F1[d].put(id, F);
         }
   }
@@ -618,7 +644,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
               correct_state(qL, *P, K, coef, a, b, 0.0, nullptr, nullptr, sL);
               F1[t].get(id + g.str[t], c5); F1[t].get(id, e);
               correct_state(qR, *P, K, coef, c5, e, 0.0, nullptr, nullptr, sR);
-              hllc(sL, sR, d, P->gamma, F);
+              hllc(sL, sR, d, P->gamma, P->wave_speeds, F);
               F2[d][t].put(id, F);
             }
       }
@@ -658,7 +684,7 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
               correct_state(q, *P, K, 0.5 * dtdx[t1], ah, al, 0.5 * dtdx[t2], bh, bl, s);
             }
           }
-          hllc(sL, sR, d, P->gamma, F);
+          hllc(sL, sR, d, P->gamma, P->wave_speeds, F);
           F3[d].put(id, F);
         }
   }
@@ -685,10 +711,19 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
         if (grav) {
           real rho_mid = 0.5 * (u0[0] + u1[0]);
           for (int k2 = 0; k2 < 3; ++k2) u1[1 + k2] = u1[1 + k2] + dt * rho_mid * P->grav[k2];
-          real e0 = 0.5 * (u0[1] + u1[1]) * P->grav[0];
-          real e1 = 0.5 * (u0[2] + u1[2]) * P->grav[1];
-          real e2 = 0.5 * (u0[3] + u1[3]) * P->grav[2];
-          u1[4] = u1[4] + dt * ((e0 + e1) + e2);
+          real e[3];
+          if (P->grav_energy) {
+            /* mass-flux form: the work gravity does on the mass crossing the
+             * zone's faces, half of each face flux (exact balance with the
+             * potential energy on closed domains) */
+            for (int d = 0; d < 3; ++d)
+              e[d] = (d < dim) ? 0.5 * (F3[d].a[id] + F3[d].a[id + g.str[d]]) * P->grav[d] : real(0.0);
+          } else {
+            e[0] = 0.5 * (u0[1] + u1[1]) * P->grav[0];
+            e[1] = 0.5 * (u0[2] + u1[2]) * P->grav[1];
+            e[2] = 0.5 * (u0[3] + u1[3]) * P->grav[2];
+          }
+          u1[4] = u1[4] + dt * ((e[0] + e[1]) + e[2]);
         }
         real q[5];
         int zb = 0;
@@ -723,8 +758,23 @@ void oracle_hllc(const double* qL, const double* qR, int d, double gamma, double
   K.gm1inv = 1.0 / (gamma - 1.0);
   state_from_prim(l, K, sl);
   state_from_prim(r, K, sr);
-  hllc(sl, sr, d, gamma, f);
+  hllc(sl, sr, d, gamma, 0, f);
   for (int c = 0; c < 5; ++c) F[c] = double(f[c]);
+}
+
+void oracle_wave_speeds(const double* qL, const double* qR, int d, double gamma, int einfeldt, double* out) {
+  real l[5], r[5], sl[NS], sr[NS];
+  for (int c = 0; c < 5; ++c) { l[c] = qL[c]; r[c] = qR[c]; }
+  Consts K;
+  K.gamma = gamma;
+  K.gm1inv = 1.0 / (gamma - 1.0);
+  state_from_prim(l, K, sl);
+  state_from_prim(r, K, sr);
+  real cl = sound_speed(sl[S_P], sl[S_INV], gamma), cr = sound_speed(sr[S_P], sr[S_INV], gamma);
+  real a, b;
+  wave_speeds(sl, sr, d, gamma, einfeldt, cl, cr, &a, &b);
+  out[0] = double(a);
+  out[1] = double(b);
 }
 
 void oracle_ppm_parabola(const double* line7, double chi, double* am_ap_a6) {

@@ -21,6 +21,8 @@ typedef struct {
   double small_dens;  /* density floor */
   double small_pres;  /* pressure floor */
   int flatten;        /* 1: CW84 flattening on; 0: off */
+  int wave_speeds;    /* HLLC outer wave speeds: 0 Davis, 1 Einfeldt (Roe-averaged) */
+  int grav_energy;    /* gravity energy source: 0 cell-centred momentum form, 1 mass-flux form */
 } oracle_params;
 
 /* optional copies of intermediate arrays (each 5 x grown size, or 6 x for prim) */
@@ -38,6 +40,7 @@ int oracle_dt(const double* U, const oracle_params* P, double* dt_out);
 int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double dt, oracle_debug* dbg);
 
 void oracle_hllc(const double* qL, const double* qR, int d, double gamma, double* F);
+void oracle_wave_speeds(const double* qL, const double* qR, int d, double gamma, int einfeldt, double* sl_sr);
 void oracle_ppm_parabola(const double* line7, double chi, double* am_ap_a6);
 double oracle_flatten(const double* p7, const double* un7, double small_pres);
 double oracle_integ(const double* am_ap_a6, double sigma, int plus);

@@ -19,6 +19,8 @@ NOALLOC_MAX_ZONES = 64000
 BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
 FLAG_NO_FLATTEN = 1
 FLAG_NO_AUTOTUNE = 2
+FLAG_EINFELDT = 4
+FLAG_FLUX_GRAV_ENERGY = 8
 NG = 4
 
 
@@ -107,6 +109,7 @@ def lib(variant="default"):
     L.hydro_dt.argtypes = [vp, B, P, D, vp]
     L.hydro_advance_box.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_box_noalloc.argtypes = [B, B, P, ctypes.c_double, D, vp]
+    L.hydro_advance_box_retry.argtypes = [vp, B, B, P, ctypes.c_double, ctypes.c_int, D, D, vp]
     L.hydro_advance_batch.argtypes = [vp, B, B, ctypes.c_int, P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     IP = ctypes.POINTER(ctypes.c_int)
@@ -133,13 +136,15 @@ def strerror(status):
         return "unknown"
 
 
-def params(dim, gamma=1.4, cfl=0.5, grav=(0.0, 0.0, 0.0), small_dens=1e-200, small_pres=1e-200, flatten=True):
+def params(dim, gamma=1.4, cfl=0.5, grav=(0.0, 0.0, 0.0), small_dens=1e-200, small_pres=1e-200, flatten=True,
+           einfeldt=False, flux_grav_energy=False):
     p = hydro_params_t()
     p.gamma, p.cfl, p.dim = gamma, cfl, dim
     for a in range(3):
         p.grav[a] = grav[a]
     p.small_dens, p.small_pres = small_dens, small_pres
-    p.flags = 0 if flatten else FLAG_NO_FLATTEN
+    p.flags = (0 if flatten else FLAG_NO_FLATTEN) | (FLAG_EINFELDT if einfeldt else 0) | \
+        (FLAG_FLUX_GRAV_ENERGY if flux_grav_energy else 0)
     return p
 
 
@@ -214,6 +219,14 @@ class Context:
         if rc and raise_on_error:
             raise HydroError(rc, "hydro_advance_box")
         return (out.value if want_dt_next else None) if raise_on_error else (rc, out.value)
+
+    def hydro_advance_box_retry(self, bin_, bout, p, dt, max_retries=3, stream=None):
+        """Returns (status, dt_taken, dt_next) of the step with retries on bad states."""
+        taken, nxt = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        rc = self.L.hydro_advance_box_retry(self.h, ctypes.byref(bin_), ctypes.byref(bout), ctypes.byref(p), float(dt),
+                                            int(max_retries), ctypes.byref(taken), ctypes.byref(nxt),
+                                            _stream_handle(stream))
+        return rc, taken.value, nxt.value
 
     def hydro_ctx_check(self):
         return self.L.hydro_ctx_check(self.h)

@@ -106,6 +106,8 @@ StepConst step_const(const hydro_params_t* p, const double dx[3], double dt) {
   K.dim = p->dim;
   K.flatten = (p->flags & HYDRO_FLAG_NO_FLATTEN) ? 0 : 1;
   K.has_grav = (p->grav[0] != 0.0 || p->grav[1] != 0.0 || p->grav[2] != 0.0) ? 1 : 0;
+  K.einfeldt = (p->flags & HYDRO_FLAG_EINFELDT) ? 1 : 0;
+  K.flux_grav = (p->flags & HYDRO_FLAG_FLUX_GRAV_ENERGY) ? 1 : 0;
   return K;
 }
 
@@ -308,6 +310,25 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
     if (h.bad) return HYDRO_EBADSTATE;
   }
   return HYDRO_OK;
+}
+
+int hydro_advance_box_retry(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                            const hydro_params_t* params, double dt, int max_retries, double* dt_taken_host,
+                            double* dt_next_host, void* stream) {
+  if (max_retries < 0 || max_retries > 60) return HYDRO_EINVAL;
+  double d = dt;
+  for (int attempt = 0; attempt <= max_retries; ++attempt) {
+    double next = 0.0;
+    int rc = hydro_advance_box(ctx, in, out, params, d, &next, stream);
+    if (rc == HYDRO_OK) {
+      if (dt_taken_host) *dt_taken_host = d;
+      if (dt_next_host) *dt_next_host = next;
+      return HYDRO_OK;
+    }
+    if (rc != HYDRO_EBADSTATE) return rc;
+    d *= 0.5;  // the input is untouched (out-of-place step): redo from it
+  }
+  return HYDRO_EBADSTATE;
 }
 
 int hydro_ctx_set_profiling(hydro_ctx_t* ctx, int enable) {

@@ -26,6 +26,8 @@ struct StepConst {
   double dt, hdt;             // dt, dt/2
   double dtdx[3];             // dt/dx per axis
   int dim, flatten, has_grav;
+  int einfeldt;   // HLLC outer speeds from Roe averages
+  int flux_grav;  // gravity energy source from the face mass fluxes
 };
 
 // ---------------------------------------------------------------- comparisons
@@ -187,8 +189,23 @@ __device__ __forceinline__ void hllc_flux(const double sL[NS], const double sR[N
   double rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
   double cl = sqrt(K.gamma * pl * sL[S_INV]);
   double cr = sqrt(K.gamma * pr * sR[S_INV]);
-  double sl = dmin(ul - cl, ur - cr);
-  double sr = dmax(ul + cl, ur + cr);
+  double sl, sr;
+  if (!K.einfeldt) {  // Davis
+    sl = dmin(ul - cl, ur - cr);
+    sr = dmax(ul + cl, ur + cr);
+  } else {  // Einfeldt: Roe-averaged normal velocity and sound speed
+    double ql = sqrt(rl), qr = sqrt(rr);
+    double iw = 1.0 / (ql + qr);
+    double wl = ql * iw, wr = qr * iw;
+    double ut0 = wl * sL[1] + wr * sR[1], ut1 = wl * sL[2] + wr * sR[2], ut2 = wl * sL[3] + wr * sR[3];
+    double hl = (sL[S_E] + pl) * sL[S_INV], hr = (sR[S_E] + pr) * sR[S_INV];
+    double ht = wl * hl + wr * hr;
+    double q2 = (ut0 * ut0 + ut1 * ut1) + ut2 * ut2;
+    double ct = sqrt(K.gm1 * (ht - 0.5 * q2));
+    double utn = (d == 0) ? ut0 : (d == 1) ? ut1 : ut2;
+    sl = dmin(ul - cl, utn - ct);
+    sr = dmax(ur + cr, utn + ct);
+  }
   double ml = rl * (sl - ul), mr = rr * (sr - ur);
   double sstar = ((pr - pl) + ml * ul - mr * ur) / (ml - mr);
   int region = ge0(sl) ? 0 : ge0(sstar) ? 1 : gt0(sr) ? 2 : 3;

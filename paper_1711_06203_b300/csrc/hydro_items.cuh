@@ -377,10 +377,18 @@ __device__ __forceinline__ void update_item(BoxGeom in, BoxGeom out, ScratchGeom
       double rho_mid = 0.5 * (u0[0] + u1[0]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) u1[1 + a] = u1[1 + a] + K.dt * rho_mid * K.grav[a];
-      double e0 = 0.5 * (u0[1] + u1[1]) * K.grav[0];
-      double e1 = 0.5 * (u0[2] + u1[2]) * K.grav[1];
-      double e2 = 0.5 * (u0[3] + u1[3]) * K.grav[2];
-      u1[4] = u1[4] + K.dt * ((e0 + e1) + e2);
+      double e[3];
+      if (K.flux_grav) {
+        // mass-flux form: gravity's work on the mass crossing the zone's faces
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          e[d] = (d < K.dim) ? 0.5 * (F[d][id] + F[d][id + st[d]]) * K.grav[d] : 0.0;
+      } else {
+        e[0] = 0.5 * (u0[1] + u1[1]) * K.grav[0];
+        e[1] = 0.5 * (u0[2] + u1[2]) * K.grav[1];
+        e[2] = 0.5 * (u0[3] + u1[3]) * K.grav[2];
+      }
+      u1[4] = u1[4] + K.dt * ((e[0] + e[1]) + e[2]);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) out.u[c * out.sc + oi] = u1[c];

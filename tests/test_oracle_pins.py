@@ -562,3 +562,80 @@ def test_ghost_fill_kinds_and_corner_composition():
         assert W[c, z(-2), y(1), x(-1)] == U[c, z(-2), y(1), x(0)]
         assert W[c, z(0), y(-2), x(7)] == sgn * U[c, z(0), y(3), x(4)]
         assert W[c, z(9), y(-1), x(-2)] == U[c, z(6), y(4), x(0)]
+
+
+# ---------------------------------------------------------------- options beyond the base step
+def test_einfeldt_speed_is_the_exact_shock_speed():
+    """The Roe linearisation satisfies the jump conditions exactly, so for two
+    states joined by a single shock the Roe-averaged characteristic speed u~ + c~
+    is the shock speed; Einfeldt's S_R picks it up (the upstream u_R + c_R is
+    slower by the Lax condition), Davis's estimate does not."""
+    g = 1.4
+    mu = (g - 1) / (g + 1)
+    rR, uR, pR = 0.7, 0.3, 1.3
+    for ratio in (1.5, 4.0, 30.0):
+        p = ratio * pR
+        rL = rR * (p / pR + mu) / (mu * p / pR + 1)
+        cR = np.sqrt(g * pR / rR)
+        S = uR + cR * np.sqrt((g + 1) / (2 * g) * p / pR + (g - 1) / (2 * g))
+        uL = S + rR * (uR - S) / rL
+        qL = np.array([rL, uL, 0.2, -0.1, p])
+        qR = np.array([rR, uR, 0.2, -0.1, pR])
+        sl, sr = oracle.wave_speeds(qL, qR, 0, g, True)
+        assert abs(sr - S) <= 1e-12 * abs(S), (ratio, sr, S)
+        dl, dr = oracle.wave_speeds(qL, qR, 0, g, False)
+        assert abs(dr - S) > 1e-6 * abs(S)
+        assert sl <= uL - np.sqrt(g * p / rL) + 1e-15
+    # identical states: the fan is the state's own acoustic speeds
+    q = np.array([1.1, 0.4, 0.0, 0.0, 0.9])
+    sl, sr = oracle.wave_speeds(q, q, 0, g, True)
+    c = np.sqrt(g * 0.9 / 1.1)
+    assert abs(sl - (0.4 - c)) < 1e-14 and abs(sr - (0.4 + c)) < 1e-14
+
+
+@pytest.mark.parametrize("einfeldt", [False, True])
+def test_flux_form_gravity_balances_potential_energy(einfeldt):
+    """Constant gravity, potential phi = -g.x at zone centres.  With the
+    mass-flux energy source the interior work of gravity telescopes against
+    the change of sum(rho*phi), so total energy plus potential changes only by
+    what crosses the domain boundary:
+      d sum(rhoE + rho phi) = sum over boundary faces of
+        -dt/dx (F_E,hi - F_E,lo) - dt/dx (F_rho,hi phi_last - F_rho,lo phi_first)
+        + dt g (F_rho,lo + F_rho,hi)/2
+    to round-off.  The cell-centred momentum form misses this by O(dt^2)."""
+    n = (12, 10, 14)
+    rng = np.random.default_rng(23)
+    U = inputs.random_box(rng, n, 3)
+    g = (0.3, -0.5, -2.0)
+    dx = (1 / 12, 1 / 10, 1 / 14)
+    x = [(np.arange(k) + 0.5) * h for k, h in zip(n, dx)]
+    Z, Y, X = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    phi = -(g[0] * X + g[1] * Y + g[2] * Z)
+    errs = {}
+    for flux_form in (True, False):
+        P = oracle.params(3, n, dx=dx, bc=oracle.BC_REFLECT, gamma=5 / 3, grav=g, flux_grav_energy=flux_form,
+                          einfeldt=einfeldt)
+        d, _ = oracle.dt(U, P)
+        U1, rc, dbg = oracle.step(U, P, d, debug=True)
+        assert rc == 0
+        inner = lambda V: V[:, 4:-4, 4:-4, 4:-4]
+        change = (inner(U1)[4] - inner(U)[4]).sum() + ((inner(U1)[0] - inner(U)[0]) * phi).sum()
+        boundary = 0.0
+        for ax in range(3):
+            F = dbg["flux_final"][ax]
+            lo = [slice(4, -4)] * 3
+            hi = [slice(4, -4)] * 3
+            lo[2 - ax] = 4               # face 0 along this axis (array axes are z, y, x)
+            hi[2 - ax] = 4 + n[ax]       # face n along this axis
+            f_lo, f_hi = F[(slice(None),) + tuple(lo)], F[(slice(None),) + tuple(hi)]
+            first = [slice(None)] * 3
+            last = [slice(None)] * 3
+            first[2 - ax] = 0
+            last[2 - ax] = n[ax] - 1
+            dtdx = d / dx[ax]
+            boundary += (-dtdx * (f_hi[4] - f_lo[4]) - dtdx * (f_hi[0] * phi[tuple(last)] - f_lo[0] * phi[tuple(first)])
+                         + d * g[ax] * 0.5 * (f_lo[0] + f_hi[0])).sum()
+        scale = np.abs(inner(U)[4]).sum()
+        errs[flux_form] = abs(change - boundary) / scale
+    assert errs[True] <= 1e-14, errs
+    assert errs[False] > 1e3 * max(errs[True], 1e-17), errs
