@@ -194,3 +194,39 @@ def level_tiling(domain, sides=LEVEL_SIDES, seed=1711):
                 lo.append((x0, y0, z0))
                 sizes.append((nx, ny, nz))
     return lo, sizes
+
+
+def amr_field(x, y, z, dim, gamma, p_amp=4.0, r0=0.12, centre=(0.5, 0.5, 0.5)):
+    """Smooth periodic background on the unit domain with a Gaussian pressure
+    bump: rho = 1 + 0.3 sin(2 pi x) cos(2 pi y) [cos(2 pi z)],
+    u = 0.2 sin(2 pi y), v = 0.2 cos(2 pi x), w = 0.1 sin(2 pi x) (3-D),
+    p = 1 + p_amp exp(-(r / r0)^2), r the distance to `centre`."""
+    tp = 2.0 * np.pi
+    cz = np.cos(tp * z) if dim == 3 else 1.0
+    rho = 1.0 + 0.3 * np.sin(tp * x) * np.cos(tp * y) * cz
+    u = 0.2 * np.sin(tp * y)
+    v = 0.2 * np.cos(tp * x)
+    w = 0.1 * np.sin(tp * x) if dim == 3 else np.zeros_like(x)
+    r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + ((z - centre[2]) ** 2 if dim == 3 else 0.0)
+    p = 1.0 + p_amp * np.exp(-r2 / (r0 * r0))
+    return conserved(rho, u + 0.0 * x, v + 0.0 * x, w + 0.0 * x, p + 0.0 * x, gamma)
+
+
+def amr_two_level(domain, dim, fine_lo, fine_n, gamma=1.4, **kw):
+    """A two-level hierarchy on the unit-width domain (coarse spacing
+    1/domain[0] on every axis, fine spacing half of it), both levels sampled
+    from amr_field at their zone centres (ghosts included).
+    fine_lo / fine_n: corners and sizes of the fine boxes in the fine index
+    space.  Returns (coarse grown array, [fine grown arrays], coarse dx)."""
+    n = tuple(domain) + (1,) * (3 - len(domain))
+    dx = (1.0 / n[0],) * 3
+    X = zone_centres(n, dim, dx)
+    Uc = amr_field(X[0], X[1], X[2], dim, gamma, **kw)
+    fines = []
+    dxf = tuple(v / 2 for v in dx)
+    for lo, s in zip(fine_lo, fine_n):
+        s = tuple(s) + (1,) * (3 - len(s))
+        org = tuple(lo[a] * dxf[a] if a < dim else 0.0 for a in range(3))
+        Xf = zone_centres(s, dim, dxf, org)
+        fines.append(amr_field(Xf[0], Xf[1], Xf[2], dim, gamma, **kw))
+    return Uc, fines, dx
