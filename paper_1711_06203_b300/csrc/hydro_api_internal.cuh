@@ -26,9 +26,12 @@ struct hydro_ctx {
 void hydro_batch_release(hydro_ctx* ctx);
 void hydro_level_release(hydro_ctx* ctx);
 size_t hydro_batch_pool_bytes(const hydro_ctx* ctx);
+namespace hydro { struct BatchBox; }
+// batched step with per-box params; *plan_boxes (nullable) receives the device
+// descriptors of the plan that ran (valid until the next batched call)
 int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
                     const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,
-                    int* bad_first_host, int* bad_all_host, cudaStream_t st);
+                    int* bad_first_host, int* bad_all_host, cudaStream_t st, const hydro::BatchBox** plan_boxes);
 
 namespace hydro {
 bool valid_params(const hydro_params_t* p);

@@ -23,23 +23,10 @@
 
 #include "hydro.h"
 #include "hydro_api_internal.cuh"
+#include "hydro_batch.cuh"
 #include "hydro_items.cuh"
 
 namespace hydro {
-
-// everything a batched kernel needs about one box (device resident)
-struct BatchBox {
-  BoxGeom in, out;
-  ScratchGeom sg;
-  Scratch s;
-  StepConst K;  // dt, hdt, dtdx refreshed on the device from dt_dev every call
-  double dx[3];
-  double cfl;
-  Range rp, ru;
-  SweepRange tr[3];
-  Range r1[3], r2[3][3], r3[3];
-  DevFlags flags;
-};
 
 namespace {
 
@@ -448,7 +435,7 @@ void hydro_batch_release(hydro_ctx* ctx) {
 // box's bad-state flag, bad_first_host the first bad box index.
 int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
                     const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,
-                    int* bad_first_host, int* bad_all_host, cudaStream_t st) {
+                    int* bad_first_host, int* bad_all_host, cudaStream_t st, const hydro::BatchBox** plan_boxes) {
   if (!ctx || !in || !out || nbox < 1 || !dt_dev || !params) return HYDRO_EINVAL;
   const int dim = params[0].dim;
   for (int b = 0; b < nbox; ++b) {
@@ -502,6 +489,9 @@ int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* 
     if (p->key == key) plan = p;
 
   if (!plan) {
+    // the tuner and the pool below write scratch from another stream: let the
+    // work already queued on `st` (which may still read scratch) finish first
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
     // scratch pool: one scratch block per box
     std::vector<ScratchGeom> sgs(nbox);
     size_t total = 0;
@@ -606,6 +596,7 @@ int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* 
     S->plans.push_back(plan);
   }
   plan->last_use = ++S->clock;
+  if (plan_boxes) *plan_boxes = plan->d_boxes;
   if (cudaGraphLaunch(plan->exec, st) != cudaSuccess) return HYDRO_ECUDA;
   ctx->launches += (long long)plan->launches.size() + 2;
   if (bad_first_host || bad_all_host) {
@@ -631,7 +622,7 @@ extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, cons
                                    const hydro_params_t* params, const double* dt_dev, double* dt_next_dev,
                                    int* bad_box_host, void* stream) {
   return hydro_batch_run(ctx, in, out, nbox, params, 0, dt_dev, dt_next_dev, bad_box_host, nullptr,
-                         static_cast<cudaStream_t>(stream));
+                         static_cast<cudaStream_t>(stream), nullptr);
 }
 
 extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax) {

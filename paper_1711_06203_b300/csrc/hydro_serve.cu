@@ -258,7 +258,7 @@ void serve::run() {
       rc = HYDRO_ECUDA;
     if (rc == HYDRO_OK)
       rc = hydro_batch_run(ctx, bin.data(), bout.data(), na, prm.data(), 1, dt_dev, dt_next_dev, nullptr,
-                           bad.data(), stream);
+                           bad.data(), stream, nullptr);
     if (rc == HYDRO_OK || rc == HYDRO_EBADSTATE) {
       if (cudaMemcpyAsync(dtn.data(), dt_next_dev, na * sizeof(double), cudaMemcpyDeviceToHost, stream) !=
               cudaSuccess ||
