@@ -415,6 +415,98 @@ def bench_options(args, dev, stream):
     return out
 
 
+def bench_amr(args, dev, stream):
+    """Two-level subcycled advance (refinement ratio 2): a 128^3 periodic
+    coarse level in eight 64^3 boxes with a Gaussian pressure bump at the
+    centre (smooth periodic background), refined over the central 64^3 coarse
+    zones by eight 64^3 fine boxes (128^3 fine zones).  One coarse step =
+    coarse fill + step, two fine fills + steps of dt/2, flux registers,
+    reflux, average down and the two-level dt, with no host synchronisation.
+    Zone-updates count 128^3 coarse + 2 x 128^3 fine per coarse step.  Also
+    timed: the same three batched steps without the synchronisation, giving
+    the cost of the AMR machinery on top of the hydro steps."""
+    import numpy as np
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    domain = (128, 128, 128)
+    clo = [(x, y, z) for z in (0, 64) for y in (0, 64) for x in (0, 64)]
+    csz = [(64, 64, 64)] * 8
+    flo = [(x, y, z) for z in (64, 128) for y in (64, 128) for x in (64, 128)]
+    fsz = [(64, 64, 64)] * 8
+    Uc, Uf, dx = inputs.amr_two_level(domain, 3, flo, fsz, gamma=1.4, p_amp=20.0, r0=0.08)
+    dxf = tuple(v / 2 for v in dx)
+    ca = []
+    for c, s in zip(clo, csz):
+        B = np.zeros((5, s[2] + 8, s[1] + 8, s[0] + 8))
+        B[:, 4:-4, 4:-4, 4:-4] = Uc[:, 4 + c[2]:4 + c[2] + s[2], 4 + c[1]:4 + c[1] + s[1], 4 + c[0]:4 + c[0] + s[0]]
+        ca.append(torch.from_numpy(B).to(dev))
+    cb = [torch.empty_like(t) for t in ca]
+    fa = [torch.from_numpy(U).to(dev) for U in Uf]
+    fb = [torch.empty_like(t) for t in fa]
+    del Uc, Uf
+    bc = ((hb.BC_PERIODIC,) * 2,) * 3
+    p = hb.params(3, gamma=1.4, cfl=0.5)
+    ctx = hb.Context(dev.index)
+    dt = torch.full((1,), 0.3 * dx[0] / 8.0, dtype=torch.float64, device=dev)
+    dt_next = torch.empty_like(dt)
+
+    def amr_step():
+        nonlocal ca, cb, fa, fb
+        ctx.hydro_amr_advance([hb.box(t, s, dx) for t, s in zip(ca, csz)], [hb.box(t, s, dx) for t, s in zip(cb, csz)],
+                              clo, [hb.box(t, s, dxf) for t, s in zip(fa, fsz)],
+                              [hb.box(t, s, dxf) for t, s in zip(fb, fsz)], flo, 3, domain, bc, p, dt, dt_next,
+                              stream=stream)
+        dt.copy_(dt_next)
+        ca, cb, fa, fb = cb, ca, fb, fa
+
+    steps = max(4, min(args.steps, 10))
+    for _ in range(4):  # tables, batch plans for both parities, tuning, graphs
+        amr_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        amr_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_amr = e0.elapsed_time(e1) / steps
+
+    # the three batched steps alone (ghosts as they are: timing only)
+    dtc = torch.full((8,), dt.item(), dtype=torch.float64, device=dev)
+    dtf = dtc * 0.5
+    dn = torch.empty_like(dtc)
+    ft = [torch.empty_like(t) for t in fa]
+    pre = hb.BC_PREFILLED
+
+    def hydro_only():
+        ctx.hydro_advance_batch([hb.box(t, s, dx, pre) for t, s in zip(ca, csz)],
+                                [hb.box(t, s, dx, pre) for t, s in zip(cb, csz)], p, dtc, dn, stream=stream)
+        ctx.hydro_advance_batch([hb.box(t, s, dxf, pre) for t, s in zip(fa, fsz)],
+                                [hb.box(t, s, dxf, pre) for t, s in zip(ft, fsz)], p, dtf, dn, stream=stream)
+        ctx.hydro_advance_batch([hb.box(t, s, dxf, pre) for t, s in zip(ft, fsz)],
+                                [hb.box(t, s, dxf, pre) for t, s in zip(fb, fsz)], p, dtf, dn, stream=stream)
+
+    for _ in range(2):
+        hydro_only()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        hydro_only()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_hydro = e0.elapsed_time(e1) / steps
+    ctx.close()
+    zu = 128 ** 3 + 2 * 128 ** 3
+    return {"workload": "two-level 128^3 coarse (8 x 64^3) + 128^3 fine (8 x 64^3) over the central 64^3 coarse "
+                        "zones, periodic, Gaussian pressure bump",
+            "steps_timed": steps, "ms_per_coarse_step": ms_amr, "zone_updates_per_coarse_step": zu,
+            "zone_updates_per_s": zu / (ms_amr * 1e-3), "hydro_steps_only_ms": ms_hydro,
+            "sync_overhead_frac": (ms_amr - ms_hydro) / ms_amr}
+
+
 def bench_serve(args, dev, zone_rate):
     """Serving stream: a seeded prefix of independent 3-D problems (Sod,
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
@@ -555,9 +647,11 @@ def run_ours(args):
         serve = bench_serve(args, dev, value)
     level = None
     options = None
+    amr = None
     if world == 1 and not args.no_batch:
         level = bench_level(args, dev, stream)
         options = bench_options(args, dev, stream)
+        amr = bench_amr(args, dev, stream)
     large = None
     if world == 1 and not args.no_large:
         large = bench_large(args, dev, stream)
@@ -596,6 +690,7 @@ def run_ours(args):
         "large_box": large,
         "level_multistep": level,
         "options": options,
+        "amr_two_level": amr,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,

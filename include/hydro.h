@@ -198,6 +198,53 @@ int hydro_advance_box_retry(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro
                             const hydro_params_t* params, double dt, int max_retries, double* dt_taken_host,
                             double* dt_next_host, void* stream);
 
+/* A two-level hierarchy, refinement ratio 2 in space and time (paper Sec. 3:
+ * block-structured AMR with subcycling in time; Castro advances the coarse
+ * level, then the fine level in smaller steps to the same time, then
+ * synchronises the two).  All arrays are host arrays of descriptors; box data
+ * live on the device. */
+typedef struct {
+  int dim;                        /* 2 or 3 */
+  int domain[3];                  /* coarse zones per axis (unused axes: 1) */
+  int domain_bc[3][2];            /* OUTFLOW / REFLECT / PERIODIC, low and high face per axis */
+  int ncoarse;                    /* coarse boxes, tiling [0, domain) exactly */
+  const hydro_box_t* coarse_in;   /* state at t; ghost zones are overwritten */
+  const hydro_box_t* coarse_out;  /* receives the synchronised state at t + dt */
+  const int* coarse_lo;           /* 3 ints per box: global index of interior zone (0,0,0) */
+  int nfine;                      /* fine boxes (0 allowed) */
+  const hydro_box_t* fine_in;     /* fine state at t; ghost zones are overwritten */
+  const hydro_box_t* fine_out;    /* receives the fine state at t + dt */
+  const int* fine_lo;             /* 3 ints per box, in the fine index space (2x the coarse) */
+} hydro_amr_t;
+
+/* One coarse step of a two-level hierarchy (Berger-Colella subcycling):
+ *   1. coarse ghost fill (domain boundary kinds) and a batched step of dt;
+ *   2. two fine steps of dt/2, each after a fine ghost fill: a ghost zone is
+ *      copied from the fine box that covers it, else interpolated from the
+ *      coarse level -- in time first (the coarse state at t for the first
+ *      step, 0.5 U(t) + 0.5 U(t+dt) for the second), then in space (linear
+ *      with a monotonised-central slope per axis, conservative);
+ *   3. reflux: each uncovered coarse zone next to the fine region gets the
+ *      coarse flux through each shared face replaced by the fine fluxes
+ *      through it, averaged over the 2^(dim-1) fine faces and both fine steps;
+ *   4. average down: each covered coarse zone becomes the mean of its children.
+ * Coarse boxes share one spacing dx; fine boxes have dx/2 exactly.  Fine boxes
+ * have even corners and sizes, do not overlap, and lie, coarsened and grown by
+ * 3 coarse zones, inside the domain (so their ghosts and the interpolation
+ * stencil only see coarse interior zones).  The box descriptors' bc fields
+ * are ignored.  dt_dev (device, 1 double): the coarse step.  dt_next_dev
+ * (device, 1 double): receives min(CFL step of the synchronised coarse level,
+ * 2 x CFL step of the fine level).  bad_host (host, nullable): if given, the
+ * call synchronises `stream` and stores 1 if any step met a non-physical
+ * state (then returns HYDRO_EBADSTATE), else 0.  The fine state after the
+ * first step lives in context-owned memory.  The tables of a hierarchy are
+ * built on the first call and kept (the 4 most recent).  HYDRO_EINVAL for a
+ * hierarchy that breaks the rules above; HYDRO_ENOTIMPL with
+ * HYDRO_FLAG_FLUX_GRAV_ENERGY (the reflux corrects hydrodynamic fluxes only).
+ * Asynchronous on `stream` otherwise. */
+int hydro_amr_advance(hydro_ctx_t* ctx, const hydro_amr_t* h, const hydro_params_t* params, const double* dt_dev,
+                      double* dt_next_dev, int* bad_host, void* stream);
+
 /* Report and clear the context's sticky bad-state flag: synchronises the
  * context's device, returns HYDRO_EBADSTATE if any step since the last check
  * met a non-physical zone, else HYDRO_OK. */

@@ -53,6 +53,22 @@ class hydro_box_t(ctypes.Structure):
     ]
 
 
+class hydro_amr_t(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("domain", ctypes.c_int * 3),
+        ("domain_bc", (ctypes.c_int * 2) * 3),
+        ("ncoarse", ctypes.c_int),
+        ("coarse_in", ctypes.POINTER(hydro_box_t)),
+        ("coarse_out", ctypes.POINTER(hydro_box_t)),
+        ("coarse_lo", ctypes.POINTER(ctypes.c_int)),
+        ("nfine", ctypes.c_int),
+        ("fine_in", ctypes.POINTER(hydro_box_t)),
+        ("fine_out", ctypes.POINTER(hydro_box_t)),
+        ("fine_lo", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
 PROB_SOD, PROB_SEDOV, PROB_TWO_STATE = 0, 1, 2
 
 
@@ -115,6 +131,7 @@ def lib(variant="default"):
     IP = ctypes.POINTER(ctypes.c_int)
     L.hydro_fill_boundary.argtypes = [vp, B, IP, ctypes.c_int, ctypes.c_int, IP, IP, vp]
     L.hydro_level_min_dt.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.hydro_amr_advance.argtypes = [vp, ctypes.POINTER(hydro_amr_t), P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
     L.serve_submit.argtypes = [vp, ctypes.POINTER(hydro_request_t), ctypes.POINTER(ctypes.c_uint64)]
     L.serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hydro_result_t), ctypes.c_int]
@@ -260,6 +277,36 @@ class Context:
         rc = self.L.hydro_fill_boundary(self.h, arr, lo_arr, n, dim, dom, bcs, _stream_handle(stream))
         if rc:
             raise HydroError(rc, "hydro_fill_boundary")
+
+    def hydro_amr_advance(self, coarse_in, coarse_out, coarse_lo, fine_in, fine_out, fine_lo, dim, domain,
+                          domain_bc, p, dt_dev, dt_next_dev, want_bad=False, stream=None):
+        """One coarse step of a two-level hierarchy (refinement ratio 2).
+        coarse_*/fine_*: lists of hydro_box_t; *_lo: corner triples (fine ones
+        in the fine index space); dt_dev, dt_next_dev: CUDA float64 tensors of
+        one element.  Returns the bad-state flag when want_bad, else None."""
+        def boxes(lst):
+            return (hydro_box_t * max(len(lst), 1))(*lst)
+
+        def corners(lst):
+            return (ctypes.c_int * max(3 * len(lst), 1))(*[int(v) for c in lst for v in (tuple(c) + (0,) * (3 - len(c)))])
+
+        keep = [boxes(coarse_in), boxes(coarse_out), corners(coarse_lo), boxes(fine_in), boxes(fine_out), corners(fine_lo)]
+        h = hydro_amr_t()
+        h.dim = dim
+        for a in range(3):
+            h.domain[a] = int(domain[a]) if a < len(domain) else 1
+            for s_ in range(2):
+                h.domain_bc[a][s_] = int(domain_bc[a][s_]) if a < len(domain_bc) else 0
+        h.ncoarse, h.nfine = len(coarse_in), len(fine_in)
+        h.coarse_in, h.coarse_out, h.coarse_lo = keep[0], keep[1], keep[2]
+        h.fine_in, h.fine_out, h.fine_lo = keep[3], keep[4], keep[5]
+        bad = ctypes.c_int(0)
+        rc = self.L.hydro_amr_advance(self.h, ctypes.byref(h), ctypes.byref(p), ctypes.c_void_p(dt_dev.data_ptr()),
+                                      ctypes.c_void_p(dt_next_dev.data_ptr()), ctypes.byref(bad) if want_bad else None,
+                                      _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_amr_advance")
+        return bad.value if want_bad else None
 
     def hydro_level_min_dt(self, dt_next_dev, dt_dev, stream=None):
         rc = self.L.hydro_level_min_dt(ctypes.c_void_p(dt_next_dev.data_ptr()), ctypes.c_void_p(dt_dev.data_ptr()),

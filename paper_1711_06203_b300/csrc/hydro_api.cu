@@ -232,6 +232,7 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
     if (e) cudaEventDestroy(e);
   hydro_batch_release(ctx);
   hydro_level_release(ctx);
+  hydro_amr_release(ctx);
   delete ctx;
 }
 

@@ -7,6 +7,7 @@
 
 struct hydro_batch_state;
 struct hydro_level_state;
+struct hydro_amr_state;
 
 struct hydro_ctx {
   int device = 0;
@@ -16,6 +17,7 @@ struct hydro_ctx {
   int fail_alloc = 0;             // test hook: make the next scratch allocation fail
   hydro_batch_state* batch = nullptr;
   hydro_level_state* level = nullptr;
+  hydro_amr_state* amr = nullptr;
   long long launches = 0;         // kernels enqueued by this context
   int profiling = 0;              // record stage events around each step
   cudaEvent_t events[hydro::NSTAGES + 1] = {};
@@ -25,6 +27,7 @@ struct hydro_ctx {
 
 void hydro_batch_release(hydro_ctx* ctx);
 void hydro_level_release(hydro_ctx* ctx);
+void hydro_amr_release(hydro_ctx* ctx);
 size_t hydro_batch_pool_bytes(const hydro_ctx* ctx);
 namespace hydro { struct BatchBox; }
 // batched step with per-box params; *plan_boxes (nullable) receives the device
