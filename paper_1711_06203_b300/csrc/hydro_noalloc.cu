@@ -9,7 +9,7 @@
 // pass their own input and output boxes.
 //
 // The storage below is a file-scope __device__ array: every GPU on which this
-// library is loaded holds it (48.3 MiB) until the process exits.  Host code
+// library is loaded holds it (60.1 MiB) until the process exits.  Host code
 // must not use the array's name as a pointer (in host code it is only a
 // stand-in symbol); the device address is fetched once per device with
 // cudaGetSymbolAddress.
