@@ -57,6 +57,7 @@ def _lib(counting=False):
         lib.oracle_fill_ghosts.argtypes = [_D, P]
         lib.oracle_dt.argtypes = [_D, P, _D]
         lib.oracle_step.argtypes = [_D, _D, P, ctypes.c_double, ctypes.POINTER(Debug)]
+        lib.oracle_mol_step.argtypes = [_D, _D, P, ctypes.c_int, ctypes.c_double]
         lib.oracle_hllc.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, _D]
         lib.oracle_wave_speeds.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
         lib.oracle_ppm_parabola.argtypes = [_D, ctypes.c_double, _D]
@@ -142,6 +143,17 @@ def step(U, P, dt_, debug=False):
         raise ValueError("oracle_step: invalid arguments")
     if debug:
         return out, rc, arrs
+    return out, rc
+
+
+def mol_step(U, P, dt_):
+    """One method-of-lines step (SSP-RK2, PPM edges, HLLC) of a state with
+    U.shape[0] - 5 passive species.  Returns (U_new, rc)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty_like(U)
+    rc = _lib().oracle_mol_step(_ptr(U), _ptr(out), ctypes.byref(P), U.shape[0] - 5, float(dt_))
+    if rc == EINVAL:
+        raise ValueError("oracle_mol_step: invalid arguments")
     return out, rc
 
 

@@ -93,7 +93,7 @@ struct Grid {
 };
 
 /* ---- Step 1: ghost-zone fill (outflow / reflect / periodic / prefilled) ---- */
-void fill_ghosts(real* W, const Grid& g, const oracle_params& P) {
+void fill_ghosts(real* W, const Grid& g, const oracle_params& P, int nf = NV) {
   for (int a = 0; a < g.dim; ++a) {
     /* fill axis a over the full grown range of earlier axes (already
      * filled) and, on later axes, over the interior plus any prefilled ghost
@@ -124,7 +124,7 @@ void fill_ghosts(real* W, const Grid& g, const oracle_params& P) {
               int s[3] = {i, j, k};
               s[a] = src;
               long di = g.id(i, j, k), si = g.id(s[0], s[1], s[2]);
-              for (int c = 0; c < NV; ++c) {
+              for (int c = 0; c < nf; ++c) {
                 real v = W[c * g.sc + si];
                 if (bc == ORACLE_BC_REFLECT && c == 1 + a) v = -v; /* mirror the normal momentum */
                 W[c * g.sc + di] = v;
@@ -410,7 +410,8 @@ void wave_speeds(const real sL[NS], const real sR[NS], int d, double gamma, int 
 
 /* ---- Step 7: HLLC flux in direction d (Toro, Spruce & Speares 1994) ----
  * sL, sR: face states (rho, u, v, w, p, rho*E, 1/rho) left and right of the face. */
-void hllc(const real sL[NS], const real sR[NS], int d, double gamma, int einfeldt, real F[5]) {
+void hllc(const real sL[NS], const real sR[NS], int d, double gamma, int einfeldt, real F[5],
+          int* upwind_left = nullptr) {
   real rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
   real rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
   real cl = sound_speed(pl, sL[S_INV], gamma), cr = sound_speed(pr, sR[S_INV], gamma);
@@ -422,6 +423,7 @@ void hllc(const real sL[NS], const real sR[NS], int d, double gamma, int einfeld
    * 0 <= sL -> L;  0 <= S* -> L*;  0 < sR -> R*;  else R */
   int region = (sl >= 0.0) ? 0 : (sstar >= 0.0) ? 1 : (sr > 0.0) ? 2 : 3;
   bool left = region <= 1;
+  if (upwind_left) *upwind_left = left ? 1 : 0;
   const real* s = left ? sL : sR;
   real rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];
   /* physical flux of the chosen side */
@@ -462,6 +464,140 @@ void correct_state(const real q[5], const oracle_params& P, const Consts& K, rea
 }
 
 
+
+/* ==== Method-of-lines step with passive species ====
+ * Sec. 4: StarLord, a proxy of Castro with only the hydrodynamics and the
+ * EOS, writes the hydrodynamics as a simple method of lines and advects 13
+ * nuclear species.  The paper prints no scheme; this is the method-of-lines
+ * reading of the same building blocks:
+ *   dU/dt = L(U) = -sum_d (F_d(face hi) - F_d(face lo)) / dx_d + S(U)
+ *   - F_d: HLLC fluxes of the limited, flattened PPM edge values of the
+ *     primitive variables (rho, u, v, w, p, X_k) at the stage time; no
+ *     characteristic tracing and no transverse terms;
+ *   - species: the mass fraction X_k = (rho X_k)/rho is reconstructed like
+ *     the other primitive variables and carried by the mass flux of the HLLC
+ *     upwind side: F(rho X_k) = F(rho) X_k(side), side = left when S* >= 0
+ *     (the region test of the hydro flux);
+ *   - S(U) = (0, rho g, (rho u).g) on the stage state (skipped when g = 0);
+ *   - time: the two-stage strong-stability-preserving Runge-Kutta scheme
+ *     U1 = U^n + dt L(U^n);  U^{n+1} = 1/2 U^n + 1/2 (U1 + dt L(U1)).
+ * Prefilled ghost layers are caller data at t^n and serve both stages;
+ * derived faces are refilled from each stage's state. */
+
+/* One stage on the interior: V = W - sum_d dtdx_d (F_d,hi - F_d,lo) + dt S(W).
+ * W: the stage state on the grown box with ghosts filled, nf = 5 + nspec fields. */
+void mol_stage(const std::vector<real>& W, const Grid& g, const oracle_params& P, int nspec, real dt,
+               std::vector<real>& V, int* bad_out) {
+  const int nf = NV + nspec, dim = g.dim;
+  const long N = g.sc;
+  Consts K;
+  K.gamma = P.gamma;
+  K.gm1inv = 1.0 / (P.gamma - 1.0);
+  int bad = 0;
+  /* primitive variables (rho, u, v, w, p, X_1 .. X_nspec) on the grown box */
+  std::vector<std::vector<real>> q(nf, std::vector<real>(N));
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for reduction(| : bad)
+#endif
+  for (long id = 0; id < N; ++id) {
+    real u[5], q5[5], inv;
+    for (int c = 0; c < 5; ++c) u[c] = W[c * N + id];
+    int zb = 0;
+    cons_to_prim(u, P, q5, &inv, &zb);
+    bad |= zb;
+    for (int v = 0; v < 5; ++v) q[v][id] = q5[v];
+    for (int k = 0; k < nspec; ++k) q[NV + k][id] = W[(NV + k) * N + id] * inv;
+  }
+  real dtdx[3];
+  for (int a = 0; a < 3; ++a) dtdx[a] = (a < dim) ? dt / P.dx[a] : 0.0;
+  /* fluxes through every d-face [0, n_d] at interior transverse positions
+   * (face f, between zones f-1 and f, stored at zone f) */
+  std::vector<std::vector<real>> F[3];
+  for (int d = 0; d < dim; ++d) {
+    F[d].assign(nf, std::vector<real>(N, real(0.0)));
+    const int ta = (d == 0) ? 1 : 0, tb = (d == 2) ? 1 : 2;
+    const int nb = (tb < dim) ? g.n[tb] : 1;
+    const int nd = g.n[d], len = nd + 2 * NG, off = NG;
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+#endif
+    for (int pb = 0; pb < nb; ++pb)
+      for (int pa = 0; pa < g.n[ta]; ++pa) {
+        int c0[3] = {0, 0, 0};
+        c0[ta] = pa;
+        c0[tb] = (tb < dim) ? pb : 0;
+        const long base = g.id(c0[0], c0[1], c0[2]), st = g.str[d];
+        /* the pencil's lines, zones -4 .. n_d+3 */
+        std::vector<std::vector<real>> a(nf, std::vector<real>(len));
+        for (int v = 0; v < nf; ++v)
+          for (int m = 0; m < len; ++m) a[v][m] = q[v][base + (long)(m - off) * st];
+        /* CW84 flattening with the normal velocity u_d: chi on zones [-1, n_d] */
+        std::vector<real> chit(len, real(1.0)), chi(len, real(1.0));
+        if (P.flatten) {
+          for (int j = -2; j <= nd + 1; ++j) chit[j + off] = flat_tilde(a[4].data(), a[1 + d].data(), j + off, P.small_pres);
+          for (int j = -1; j <= nd; ++j) {
+            int m = j + off;
+            real dp1 = a[4][m + 1] - a[4][m - 1];
+            int s = (dp1 < 0.0) ? 1 : -1;
+            chi[m] = rmin(chit[m], chit[m + s]);
+          }
+        }
+        /* limited edge values of zones [-1, n_d]: am (low face), ap (high face) */
+        std::vector<std::vector<real>> am(nf, std::vector<real>(len)), ap(nf, std::vector<real>(len));
+        for (int v = 0; v < nf; ++v) {
+          std::vector<real> slope(len, real(0.0)), face(len, real(0.0));
+          for (int j = -2; j <= nd + 1; ++j) slope[j + off] = mc_slope(a[v].data(), j + off);
+          for (int j = -2; j <= nd; ++j) {
+            int m = j + off;
+            face[m] = face_value(a[v][m], a[v][m + 1], slope[m], slope[m + 1]);
+          }
+          for (int j = -1; j <= nd; ++j) {
+            int m = j + off;
+            real a6;
+            ppm_limit(a[v][m], face[m - 1], face[m], chi[m], &am[v][m], &ap[v][m], &a6);
+          }
+        }
+        /* Riemann problems at faces [0, n_d] */
+        for (int f = 0; f <= nd; ++f) {
+          int m = f + off;
+          real qL[5], qR[5], sL[NS], sR[NS], Fh[5];
+          for (int v = 0; v < 5; ++v) {
+            qL[v] = ap[v][m - 1];
+            qR[v] = am[v][m];
+          }
+          state_from_prim(qL, K, sL);
+          state_from_prim(qR, K, sR);
+          int left = 1;
+          hllc(sL, sR, d, P.gamma, P.wave_speeds, Fh, &left);
+          long id = base + (long)f * st;
+          for (int c = 0; c < 5; ++c) F[d][c][id] = Fh[c];
+          for (int k = 0; k < nspec; ++k) F[d][NV + k][id] = Fh[0] * (left ? ap[NV + k][m - 1] : am[NV + k][m]);
+        }
+      }
+  }
+  /* the stage update, x then y then z flux differences, then the source */
+  const bool grav = P.grav[0] != 0.0 || P.grav[1] != 0.0 || P.grav[2] != 0.0;
+#ifndef ORACLE_COUNT_FLOPS
+#pragma omp parallel for collapse(2)
+#endif
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        long id = g.id(i, j, k);
+        for (int c = 0; c < nf; ++c) {
+          real v = W[c * N + id];
+          for (int d = 0; d < dim; ++d) v = v - dtdx[d] * (F[d][c][id + g.str[d]] - F[d][c][id]);
+          V[c * N + id] = v;
+        }
+        if (grav) {
+          real rho = W[id];
+          for (int a = 0; a < 3; ++a) V[(1 + a) * N + id] = V[(1 + a) * N + id] + dt * rho * P.grav[a];
+          real e = (W[1 * N + id] * P.grav[0] + W[2 * N + id] * P.grav[1]) + W[3 * N + id] * P.grav[2];
+          V[4 * N + id] = V[4 * N + id] + dt * e;
+        }
+      }
+  *bad_out |= bad;
+}
 
 bool valid_params(const oracle_params* P) {
   if (!P || (P->dim != 2 && P->dim != 3)) return false;
@@ -750,6 +886,42 @@ int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double 
 }
 
 /* ---- component entry points for unit pins ---- */
+/* Method-of-lines step with nspec passive species: U holds 5 + nspec fields
+ * on the grown box (rho, rho u, rho v, rho w, rho E, rho X_1 ..). */
+int oracle_mol_step(const double* Uin, double* Uout, const oracle_params* P, int nspec, double dt) {
+  if (!valid_params(P) || !Uin || !Uout || !(dt > 0.0) || nspec < 0 || nspec > 64) return ORACLE_EINVAL;
+  const Grid g(*P);
+  const int nf = NV + nspec;
+  const long N = g.sc;
+  int bad = 0;
+  /* stage 1 from U^n with its ghosts filled */
+  std::vector<real> W0(Uin, Uin + nf * N);
+  fill_ghosts(W0.data(), g, *P, nf);
+  std::vector<real> U1(W0);
+  mol_stage(W0, g, *P, nspec, dt, U1, &bad);
+  /* stage 2 from U1: its prefilled layers are still the caller's (copied from
+   * W0), its derived faces are refilled from its own interior */
+  fill_ghosts(U1.data(), g, *P, nf);
+  std::vector<real> V2(U1);
+  mol_stage(U1, g, *P, nspec, dt, V2, &bad);
+  /* U^{n+1} = 1/2 U^n + 1/2 V2 on the interior; ghosts as filled at t^n */
+  std::vector<real> Out(W0);
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        long id = g.id(i, j, k);
+        real u[5];
+        for (int c = 0; c < nf; ++c) Out[c * N + id] = 0.5 * W0[c * N + id] + 0.5 * V2[c * N + id];
+        for (int c = 0; c < 5; ++c) u[c] = Out[c * N + id];
+        real q5[5];
+        int zb = 0;
+        cons_to_prim(u, *P, q5, nullptr, &zb);
+        bad |= zb;
+      }
+  for (long i = 0; i < nf * N; ++i) Uout[i] = double(Out[i]);
+  return bad ? ORACLE_EBADSTATE : ORACLE_OK;
+}
+
 void oracle_hllc(const double* qL, const double* qR, int d, double gamma, double* F) {
   real l[5], r[5], sl[NS], sr[NS], f[5];
   for (int c = 0; c < 5; ++c) { l[c] = qL[c]; r[c] = qR[c]; }

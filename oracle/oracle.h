@@ -38,6 +38,9 @@ long long oracle_grown_size(const oracle_params* P);
 int oracle_fill_ghosts(double* U, const oracle_params* P);
 int oracle_dt(const double* U, const oracle_params* P, double* dt_out);
 int oracle_step(const double* Uin, double* Uout, const oracle_params* P, double dt, oracle_debug* dbg);
+/* method-of-lines step (SSP-RK2, PPM edges, HLLC) with nspec passive species:
+ * 5 + nspec fields on the grown box */
+int oracle_mol_step(const double* Uin, double* Uout, const oracle_params* P, int nspec, double dt);
 
 void oracle_hllc(const double* qL, const double* qR, int d, double gamma, double* F);
 void oracle_wave_speeds(const double* qL, const double* qR, int d, double gamma, int einfeldt, double* sl_sr);

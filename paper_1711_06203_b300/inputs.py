@@ -230,3 +230,16 @@ def amr_two_level(domain, dim, fine_lo, fine_n, gamma=1.4, **kw):
         Xf = zone_centres(s, dim, dxf, org)
         fines.append(amr_field(Xf[0], Xf[1], Xf[2], dim, gamma, **kw))
     return Uc, fines, dx
+
+
+def species_fractions(rng, shape, nspec, concentration=1.0):
+    """Mass fractions of nspec species at every zone of `shape`: a
+    Dirichlet(concentration) draw per zone (non-negative, summing to one)."""
+    g = rng.gamma(concentration, 1.0, (nspec,) + tuple(shape))
+    return g / g.sum(axis=0)
+
+
+def with_species(U, X):
+    """The conserved state U (5, ...) extended by the species densities
+    rho X_k (X: (nspec, ...) mass fractions on the same zones)."""
+    return np.concatenate([U, U[0][None] * X], axis=0)
