@@ -507,6 +507,70 @@ def bench_amr(args, dev, stream):
             "sync_overhead_frac": (ms_amr - ms_hydro) / ms_amr}
 
 
+def bench_mol(args, dev, stream, cpu_sample=True):
+    """Method-of-lines step with passive species, the configuration of the
+    paper's GPU proxy (Sedov, 13 advected species): Sedov 128^3 (gamma 1.4,
+    outflow) with 13 species of seeded Dirichlet mass fractions, SSP-RK2,
+    CFL 0.4.  Also the same step without species, and the CPU oracle's
+    method-of-lines rate on a 64^3 sample with 13 species."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    n = 128
+    U0, _ = inputs.sedov(n)
+    X = inputs.species_fractions(np.random.default_rng(1711), U0.shape[1:], 13)
+    ctx = hb.Context(dev.index)
+    p = hb.params(3, gamma=1.4, cfl=0.4)
+    out = {"workload": f"sedov3d_{n}^3 + 13 passive species, SSP-RK2 method of lines, outflow"}
+    for nspec in (13, 0):
+        U = inputs.with_species(U0, X[:nspec])
+        a = torch.from_numpy(U).to(dev)
+        b = torch.empty_like(a)
+        box = lambda t: hb.box(t, (n, n, n), (1.0 / n,) * 3, hb.BC_OUTFLOW)
+        dt = ctx.hydro_dt(box(a), p, stream)
+        for _ in range(3):
+            dt = ctx.hydro_mol_advance_box(box(a), box(b), p, nspec, dt, want_dt_next=True, stream=stream)
+            a, b = b, a
+        torch.cuda.synchronize(dev)
+        k = max(3, min(args.steps, 10))
+        l0 = ctx.hydro_ctx_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            ctx.hydro_mol_advance_box(box(a), box(b), p, nspec, dt, stream=stream)
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / k
+        key = "species_13" if nspec else "hydro_only"
+        out[key] = {"ms_per_step": ms, "zone_updates_per_s": n ** 3 / (ms * 1e-3), "steps_timed": k,
+                    "launches_per_step": (ctx.hydro_ctx_launches() - l0) / k,
+                    "state_gb": a.numel() * 8 / 1e9}
+        del a, b
+    ctx.close()
+    torch.cuda.empty_cache()
+    if cpu_sample:
+        import oracle
+
+        m = 64
+        Us, _ = inputs.sedov(m)
+        Us = inputs.with_species(Us, inputs.species_fractions(np.random.default_rng(1711), Us.shape[1:], 13))
+        P = oracle.params(3, (m, m, m), gamma=1.4, cfl=0.4)
+        d, _ = oracle.dt(Us, P)
+        t0 = time.perf_counter()
+        oracle.mol_step(Us, P, d)
+        sec = time.perf_counter() - t0
+        out["cpu_oracle"] = {"zone_updates_per_s": m ** 3 / sec, "cores": os.cpu_count(),
+                             "sample": f"one {m}^3 method-of-lines oracle step with 13 species"}
+        out["gpu_over_cpu_oracle"] = out["species_13"]["zone_updates_per_s"] / out["cpu_oracle"]["zone_updates_per_s"]
+    return out
+
+
 def bench_serve(args, dev, zone_rate):
     """Serving stream: a seeded prefix of independent 3-D problems (Sod,
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
@@ -648,10 +712,12 @@ def run_ours(args):
     level = None
     options = None
     amr = None
+    mol = None
     if world == 1 and not args.no_batch:
         level = bench_level(args, dev, stream)
         options = bench_options(args, dev, stream)
         amr = bench_amr(args, dev, stream)
+        mol = bench_mol(args, dev, stream, cpu_sample=not args.no_cpu_baseline)
     large = None
     if world == 1 and not args.no_large:
         large = bench_large(args, dev, stream)
@@ -691,6 +757,7 @@ def run_ours(args):
         "level_multistep": level,
         "options": options,
         "amr_two_level": amr,
+        "mol_species": mol,
         "gpu_launches": launches,
         "wall_s_timed": wall,
         "clocks": clocks,

@@ -245,6 +245,30 @@ typedef struct {
 int hydro_amr_advance(hydro_ctx_t* ctx, const hydro_amr_t* h, const hydro_params_t* params, const double* dt_dev,
                       double* dt_next_dev, int* bad_host, void* stream);
 
+/* One method-of-lines step of a box carrying nspec passive species (paper
+ * Sec. 4: StarLord, the GPU proxy of Castro, keeps the hydrodynamics and the
+ * EOS, writes the hydrodynamics as a simple method of lines and advects 13
+ * nuclear species).
+ *  - Semi-discrete form dU/dt = -sum_d (F_d(hi face) - F_d(lo face))/dx_d + S:
+ *    F_d is the HLLC flux of the flattened, limited PPM edge values of the
+ *    primitive variables (rho, u, v, w, p, X_k) at the stage time, without
+ *    characteristic tracing or transverse terms; the species flux is the mass
+ *    flux times the mass fraction of the HLLC upwind side (S* >= 0: left);
+ *    S = (0, rho g, (rho u).g).  Time: two-stage SSP Runge-Kutta,
+ *    U1 = U + dt L(U), U' = U/2 + (U1 + dt L(U1))/2.
+ *  - in/out: boxes of 5 + nspec components (stride[2] apart): rho, rho u,
+ *    rho v, rho w, rho E, then rho X_1 .. rho X_nspec.  Derived boundary faces
+ *    are refilled from each stage's state; prefilled ghost layers are the
+ *    caller's data at t and serve both stages.
+ *  - 0 <= nspec <= HYDRO_MOL_MAX_SPECIES.  dt_next_host (nullable) as in
+ *    hydro_advance_box (CFL step of the result; synchronises the stream; a
+ *    non-physical state returns HYDRO_EBADSTATE).  HYDRO_ENOTIMPL with
+ *    HYDRO_FLAG_FLUX_GRAV_ENERGY.  Scratch: 7 (5 + nspec) + 1 grown-box
+ *    fields of the context's scratch. */
+#define HYDRO_MOL_MAX_SPECIES 32
+int hydro_mol_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                          const hydro_params_t* params, int nspec, double dt, double* dt_next_host, void* stream);
+
 /* Report and clear the context's sticky bad-state flag: synchronises the
  * context's device, returns HYDRO_EBADSTATE if any step since the last check
  * met a non-physical zone, else HYDRO_OK. */

@@ -17,6 +17,7 @@ HYDRO_EBADSTATE, HYDRO_EAGAIN, HYDRO_ETIMEDOUT, HYDRO_ENOTIMPL = -4, -5, -6, -7
 HYDRO_ETOOBIG = -8
 NOALLOC_MAX_ZONES = 64000
 BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
+MOL_MAX_SPECIES = 32  # HYDRO_MOL_MAX_SPECIES
 FLAG_NO_FLATTEN = 1
 FLAG_NO_AUTOTUNE = 2
 FLAG_EINFELDT = 4
@@ -131,6 +132,7 @@ def lib(variant="default"):
     IP = ctypes.POINTER(ctypes.c_int)
     L.hydro_fill_boundary.argtypes = [vp, B, IP, ctypes.c_int, ctypes.c_int, IP, IP, vp]
     L.hydro_level_min_dt.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.hydro_mol_advance_box.argtypes = [vp, B, B, P, ctypes.c_int, ctypes.c_double, D, vp]
     L.hydro_amr_advance.argtypes = [vp, ctypes.POINTER(hydro_amr_t), P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
     L.serve_submit.argtypes = [vp, ctypes.POINTER(hydro_request_t), ctypes.POINTER(ctypes.c_uint64)]
@@ -166,10 +168,10 @@ def params(dim, gamma=1.4, cfl=0.5, grav=(0.0, 0.0, 0.0), small_dens=1e-200, sma
 
 
 def box(t, n, dx, bc=BC_OUTFLOW):
-    """hydro_box_t describing tensor t (5, gz, gy, gx), float64, x contiguous.
+    """hydro_box_t describing tensor t (5 [+ species], gz, gy, gx), float64, x contiguous.
     n: interior (nx, ny, nz); bc: one kind for every face or a 3x2 nested sequence."""
-    if t.dtype.itemsize != 8 or t.dim() != 4 or t.shape[0] != 5 or t.stride(3) != 1:
-        raise ValueError("box tensor must be float64 of shape (5, gz, gy, gx) with x contiguous")
+    if t.dtype.itemsize != 8 or t.dim() != 4 or t.shape[0] < 5 or t.stride(3) != 1:
+        raise ValueError("box tensor must be float64 of shape (5 [+ species], gz, gy, gx) with x contiguous")
     b = hydro_box_t()
     b.u = t.data_ptr()
     for a in range(3):
@@ -235,6 +237,16 @@ class Context:
                                       ctypes.byref(out) if want_dt_next else None, _stream_handle(stream))
         if rc and raise_on_error:
             raise HydroError(rc, "hydro_advance_box")
+        return (out.value if want_dt_next else None) if raise_on_error else (rc, out.value)
+
+    def hydro_mol_advance_box(self, bin_, bout, p, nspec, dt, want_dt_next=False, stream=None, raise_on_error=True):
+        """Method-of-lines step of a box with nspec passive species (5 + nspec components)."""
+        out = ctypes.c_double(0.0)
+        rc = self.L.hydro_mol_advance_box(self.h, ctypes.byref(bin_), ctypes.byref(bout), ctypes.byref(p), int(nspec),
+                                          float(dt), ctypes.byref(out) if want_dt_next else None,
+                                          _stream_handle(stream))
+        if rc and raise_on_error:
+            raise HydroError(rc, "hydro_mol_advance_box")
         return (out.value if want_dt_next else None) if raise_on_error else (rc, out.value)
 
     def hydro_advance_box_retry(self, bin_, bout, p, dt, max_retries=3, stream=None):

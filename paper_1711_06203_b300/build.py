@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hydro_api.cu", "hydro_step.cu", "hydro_batch.cu", "hydro_level.cu", "hydro_serve.cu",
-           "hydro_noalloc.cu", "hydro_amr.cu"]
+           "hydro_noalloc.cu", "hydro_amr.cu", "hydro_mol.cu"]
 
 
 def _nvcc():

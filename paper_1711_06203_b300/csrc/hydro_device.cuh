@@ -183,7 +183,8 @@ __device__ __forceinline__ double integ_minus(double am, double ap, double a6, d
 }
 
 // ---------------------------------------------------------------- HLLC (Toro-Spruce-Speares)
-__device__ __forceinline__ void hllc_flux(const double sL[NS], const double sR[NS], int d, const StepConst& K,
+// returns true when the flux is taken from the left side of the fan (S* >= 0)
+__device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[NS], int d, const StepConst& K,
                                           double F[5]) {
   double rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
   double rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
@@ -221,7 +222,7 @@ __device__ __forceinline__ void hllc_flux(const double sL[NS], const double sR[N
   if (region == 0 || region == 3) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) F[c] = Fk[c];
-    return;
+    return left;
   }
   double sk = left ? sl : sr, mk = left ? ml : mr;
   double Uk[5] = {rho, rho * s[1], rho * s[2], rho * s[3], E};
@@ -234,6 +235,7 @@ __device__ __forceinline__ void hllc_flux(const double sL[NS], const double sR[N
   Us[4] = f * (E * s[S_INV]) + (sstar - un) * (f * sstar + p * r);
 #pragma unroll
   for (int c = 0; c < 5; ++c) F[c] = Fk[c] + sk * (Us[c] - Uk[c]);
+  return left;
 }
 
 }  // namespace hydro
