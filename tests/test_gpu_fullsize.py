@@ -1,5 +1,9 @@
 """Parity at the full sizes of the workloads, in the launch configuration the
 benchmark times:
+  * Sedov 128^3 for the configuration's 200 steps with the device dt: the
+    shock radius follows the self-similar law (exponent 2/5, amplitude from the
+    similarity solution), mass and energy are conserved while the blast is
+    inside the box, and the octants stay mirror images;
   * Sedov 128^3 (the bench box): after GPU steps, one more step by the GPU
     and by the oracle from the same state, compared over the whole box;
   * the 512-box batched level: one graph-replayed batched step, sampled boxes
@@ -14,6 +18,7 @@ import pytest
 import torch
 
 import oracle
+import sedov_similarity
 from gpu_helpers import rel_linf
 from paper_1711_06203_b300 import binding as hb
 from paper_1711_06203_b300 import inputs
@@ -45,6 +50,55 @@ def test_sedov_128_full_box_parity():
     assert np.all(rel_linf(got[I3], ref[I3]) <= 1e-10)
     dref, _ = oracle.dt(ref, P)
     assert abs(dn - dref) <= 1e-10 * dref
+
+
+def test_sedov_128_200_steps_self_similar():
+    n, steps = 128, 200
+    U, _ = inputs.sedov(n)
+    ctx = hb.Context(0)
+    p = hb.params(3, gamma=1.4, cfl=0.5)
+    a = torch.from_numpy(U).cuda()
+    b = torch.empty_like(a)
+    box = lambda t: hb.box(t, (n, n, n), (1.0 / n,) * 3, hb.BC_OUTFLOW)
+    x = (torch.arange(n, dtype=torch.float64, device="cuda") + 0.5) / n - 0.5
+    r = torch.sqrt(x.view(n, 1, 1) ** 2 + x.view(1, n, 1) ** 2 + x.view(1, 1, n) ** 2).ravel()
+    nb = n // 2
+    idx = torch.clamp((r / 0.5 * nb).long(), max=nb)
+    inside = idx < nb
+    cnt = torch.bincount(idx[inside], minlength=nb).double()
+    rc = (torch.arange(nb, dtype=torch.float64) + 0.5) * (0.5 / nb)
+    tot0 = a[:, 4:-4, 4:-4, 4:-4].sum(dim=(1, 2, 3))
+    dt = ctx.hydro_dt(box(a), p)
+    t, ts, Rpk, Rfr = 0.0, [], [], []
+    for s in range(steps):
+        d = dt
+        dt = ctx.hydro_advance_box(box(a), box(b), p, d, want_dt_next=True)
+        a, b = b, a
+        t += d
+        if s >= steps // 2 and s % 10 == 9:
+            rho = a[0, 4:-4, 4:-4, 4:-4].ravel()
+            prof = (torch.bincount(idx[inside], weights=rho[inside], minlength=nb) / cnt).cpu().numpy()
+            k = int(np.argmax(prof))
+            half = 0.5 * (1.0 + prof[k])
+            j = k
+            while prof[j + 1] > half:
+                j += 1
+            ts.append(t)
+            Rpk.append(float(rc[k]))
+            Rfr.append(float(rc[j] + (prof[j] - half) / (prof[j] - prof[j + 1]) * (rc[j + 1] - rc[j])))
+    tot1 = a[:, 4:-4, 4:-4, 4:-4].sum(dim=(1, 2, 3))
+    rho = a[0, 4:-4, 4:-4, 4:-4].cpu().numpy()
+    ctx.close()
+    assert Rfr[-1] < 0.45  # the blast is still inside the box
+    expo = np.polyfit(np.log(ts), np.log(Rpk), 1)[0]
+    assert abs(expo - 0.4) <= 0.02, expo
+    ratio = Rfr[-1] / (sedov_similarity.xi0(1.4) * (t * t) ** 0.2)
+    assert abs(ratio - 1.0) <= 0.05, ratio
+    assert abs((tot1[0] - tot0[0]) / tot0[0]).item() < 1e-13
+    assert abs((tot1[4] - tot0[4]) / tot0[4]).item() < 1e-13
+    scale = np.abs(rho).max()
+    for mir in (rho[::-1], rho[:, ::-1], rho[:, :, ::-1], rho.transpose(1, 0, 2), rho.transpose(2, 1, 0)):
+        assert np.abs(rho - mir).max() / scale <= 1e-10
 
 
 def test_batched_level_512_sampled_boxes():
