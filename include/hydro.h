@@ -378,6 +378,13 @@ int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* cal
 /* Total number of CUDA kernels this context has enqueued (host counter). */
 long long hydro_ctx_launches(const hydro_ctx_t* ctx);
 
+/* Diagnostics (no counterpart in the paper): the kernels scale by 2 and by
+ * 1/2 on the integer pipe instead of the FP64 multiplier; this runs those two
+ * helpers over x[0..n) (device arrays of n doubles) into twice[] and half[],
+ * asynchronously on `stream`, so a test can compare them bit for bit with
+ * IEEE 2.0*x and 0.5*x. */
+int hydro_selftest_scale2(const double* x, double* twice, double* half, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -132,6 +132,7 @@ def lib(variant="default"):
     IP = ctypes.POINTER(ctypes.c_int)
     L.hydro_fill_boundary.argtypes = [vp, B, IP, ctypes.c_int, ctypes.c_int, IP, IP, vp]
     L.hydro_level_min_dt.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.hydro_selftest_scale2.argtypes = [vp, vp, vp, ctypes.c_longlong, vp]
     L.hydro_mol_advance_box.argtypes = [vp, B, B, P, ctypes.c_int, ctypes.c_double, D, vp]
     L.hydro_amr_advance.argtypes = [vp, ctypes.POINTER(hydro_amr_t), P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
@@ -189,6 +190,19 @@ def _stream_handle(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def hydro_selftest_scale2(x, variant="default", stream=None):
+    """Run the kernels' integer-pipe 2x and x/2 over a CUDA float64 tensor;
+    returns (twice, half) tensors."""
+    import torch
+    x = x.contiguous()
+    t, h = torch.empty_like(x), torch.empty_like(x)
+    rc = lib(variant).hydro_selftest_scale2(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                            ctypes.c_void_p(h.data_ptr()), x.numel(), _stream_handle(stream))
+    if rc:
+        raise HydroError(rc, "hydro_selftest_scale2")
+    return t, h
 
 
 def hydro_advance_box_noalloc(bin_, bout, p, dt, want_dt_next=False, stream=None, variant="default"):

@@ -181,6 +181,16 @@ int collect_stage_times(hydro_ctx* ctx, cudaStream_t st) {
 
 }  // namespace hydro
 
+namespace {
+__global__ void k_selftest_scale2(const double* __restrict__ x, double* __restrict__ twice, double* __restrict__ half,
+                                  long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  twice[i] = dtwice(x[i]);
+  half[i] = dhalf(x[i]);
+}
+}  // namespace
+
 extern "C" {
 
 const char* hydro_strerror(int s) {
@@ -354,5 +364,12 @@ int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* cal
 }
 
 long long hydro_ctx_launches(const hydro_ctx_t* ctx) { return ctx ? ctx->launches : -1; }
+
+int hydro_selftest_scale2(const double* x, double* twice, double* half, long long n, void* stream) {
+  if (!x || !twice || !half || n < 0) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  k_selftest_scale2<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, twice, half, n);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
 
 }  // extern "C"

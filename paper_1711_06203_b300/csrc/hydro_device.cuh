@@ -58,6 +58,47 @@ __device__ __forceinline__ bool dless(double a, double b) { return ilt(okey(a), 
 // min/max as explicit selects: ties return the first argument
 __device__ __forceinline__ double dmin(double a, double b) { return dless(b, a) ? b : a; }
 __device__ __forceinline__ double dmax(double a, double b) { return dless(a, b) ? b : a; }
+// |x| by clearing the sign bit on the integer pipe (an FP64 absolute value
+// whose only consumers are bit-pattern compares would otherwise cost an
+// FP64 issue slot)
+__device__ __forceinline__ double dabs(double x) {
+  long long r;
+  asm("and.b64 %0, %1, 0x7FFFFFFFFFFFFFFF;" : "=l"(r) : "l"(dbits(x)));
+  return __longlong_as_double(r);
+}
+// 2x and x/2 on the integer pipe, bitwise equal to the IEEE products 2.0 * x
+// and 0.5 * x (round to nearest even) for every input: scaling by two moves
+// the exponent field, except where the value is or becomes subnormal (the
+// significand shifts, rounding half to even) or overflows.  An FP64 multiply
+// costs an issue slot on the scarce FP64 pipe; these cost a few integer ops.
+__device__ __forceinline__ double dtwice(double x) {
+  const long long b = dbits(x);
+  const long long sign = b & (long long)0x8000000000000000ULL, mag = b & 0x7FFFFFFFFFFFFFFFLL;
+  const long long e = mag >> 52;
+  long long r;
+  if (e == 0) r = sign | (mag << 1);                        // zero or subnormal
+  else if (e < 2046) r = b + (1LL << 52);                   // normal: exponent + 1
+  else if (e == 2046) r = sign | 0x7FF0000000000000LL;      // overflow to infinity
+  else r = b;                                               // infinity, NaN
+  return __longlong_as_double(r);
+}
+__device__ __forceinline__ double dhalf(double x) {
+  const long long b = dbits(x);
+  const long long sign = b & (long long)0x8000000000000000ULL, mag = b & 0x7FFFFFFFFFFFFFFFLL;
+  const long long e = mag >> 52;
+  long long r;
+  if (e >= 2 && e < 2047) {
+    r = b - (1LL << 52);                                    // the half is normal
+  } else if (e == 2047) {
+    r = b;                                                  // infinity, NaN
+  } else {
+    // the half is subnormal: significand M (implicit bit included when
+    // e == 1) halved, a dropped 1 rounding the quotient to even
+    const long long q = mag >> 1;
+    r = sign | (q + (mag & q & 1));
+  }
+  return __longlong_as_double(r);
+}
 // operands known to be >= +0 (magnitudes, pressures, speeds): raw bits order
 __device__ __forceinline__ double dmin_nn(double a, double b) { return ilt(dbits(b), dbits(a)) ? b : a; }
 __device__ __forceinline__ double dmax_nn(double a, double b) { return ilt(dbits(a), dbits(b)) ? b : a; }
@@ -90,7 +131,7 @@ __device__ __forceinline__ void cons_to_prim_flag(const double U[5], const StepC
   rho = dmax(rho, K.small_dens);
   double inv = 1.0 / rho;
   double u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
-  double ke = 0.5 * rho * ((u * u + v * v) + w * w);
+  double ke = dhalf(rho) * ((u * u + v * v) + w * w);
   double p = K.gm1 * (U[4] - ke);
   if (!(gt0(p) && dfinite(p) && dfinite(U[1]) && dfinite(U[2]) && dfinite(U[3]))) *bad = true;
   p = dmax(p, K.small_pres);
@@ -102,7 +143,7 @@ __device__ __forceinline__ void cons_to_prim_flag(const double U[5], const StepC
 enum { S_RHO = 0, S_P = 4, S_E = 5, S_INV = 6, NS = 7 };
 
 __device__ __forceinline__ double energy_of(const double q[5], const StepConst& K) {
-  return q[4] * K.gm1inv + 0.5 * q[0] * ((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
+  return q[4] * K.gm1inv + dhalf(q[0]) * ((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
 }
 
 __device__ __forceinline__ void state_from_prim(const double q[5], const StepConst& K, double s[NS]) {
@@ -116,7 +157,7 @@ __device__ __forceinline__ void state_from_cons(const double U[5], const StepCon
   double rho = dmax(U[0], K.small_dens);
   double inv = 1.0 / rho;
   double u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
-  double ke = 0.5 * rho * ((u * u + v * v) + w * w);
+  double ke = dhalf(rho) * ((u * u + v * v) + w * w);
   double p = K.gm1 * (U[4] - ke);
   p = dmax(p, K.small_pres);
   s[0] = rho; s[1] = u; s[2] = v; s[3] = w; s[4] = p;
@@ -131,7 +172,7 @@ __device__ __forceinline__ double flat_tilde(double pm2, double pm1, double pp1,
   double dp1 = pp1 - pm1;
   double dp2 = pp2 - pm2;
   if (gt0(um1 - up1) && abs_gt(dp1, FLAT_EPS * dmin_nn(pp1, pm1))) {
-    double z = fabs(dp1) / dmax_nn(fabs(dp2), small_pres);
+    double z = dabs(dp1) / dmax_nn(dabs(dp2), small_pres);
     double f = dmax(0.0, dmin(1.0, FLAT_OMEGA2 * (z - FLAT_OMEGA1)));
     return 1.0 - f;
   }
@@ -143,16 +184,16 @@ __device__ __forceinline__ double flat_tilde(double pm2, double pm1, double pp1,
 __device__ __forceinline__ double mc_slope(double am1, double a0, double ap1) {
   double dl = a0 - am1, dr = ap1 - a0;
   if (!same_sign_strict(dl, dr)) return 0.0;
-  double da = 0.5 * (ap1 - am1);
+  double da = dhalf(ap1 - am1);
   // 2 min(|dl|, |dr|) == min(2|dl|, 2|dr|) exactly (doubling is exact)
-  double m2 = 2.0 * dmin_nn(fabs(dl), fabs(dr));
-  double lim = dmin_nn(fabs(da), m2);
+  double m2 = dtwice(dmin_nn(dabs(dl), dabs(dr)));
+  double lim = dmin_nn(dabs(da), m2);
   return copysign(lim, da);
 }
 
 // interface value between zones with averages a0, a1 and slopes s0, s1
 __device__ __forceinline__ double face_value(double a0, double a1, double s0, double s1) {
-  return 0.5 * (a0 + a1) - SIXTH * (s1 - s0);
+  return dhalf(a0 + a1) - SIXTH * (s1 - s0);
 }
 
 // limited, flattened parabola of a zone: average ai, interface values aM, aP
@@ -176,10 +217,10 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
 // averages of the parabola over the part of the zone swept by a wave of
 // Courant number s toward the high (I+) / low (I-) face
 __device__ __forceinline__ double integ_plus(double am, double ap, double a6, double s) {
-  return ap - 0.5 * s * ((ap - am) - (1.0 - TWOTHIRDS * s) * a6);
+  return ap - dhalf(s) * ((ap - am) - (1.0 - TWOTHIRDS * s) * a6);
 }
 __device__ __forceinline__ double integ_minus(double am, double ap, double a6, double s) {
-  return am + 0.5 * s * ((ap - am) + (1.0 - TWOTHIRDS * s) * a6);
+  return am + dhalf(s) * ((ap - am) + (1.0 - TWOTHIRDS * s) * a6);
 }
 
 // ---------------------------------------------------------------- HLLC (Toro-Spruce-Speares)

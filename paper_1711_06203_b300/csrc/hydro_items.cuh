@@ -79,7 +79,7 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
   const double un = zone[1];
   const double c2 = c * c;
-  const double lu = 0.5 * rho_c, lp = 0.5 * inv_c2;
+  const double lu = dhalf(rho_c), lp = dhalf(inv_c2);
   const double lam[3] = {un - c, un, un + c};
   double sig[3];
 #pragma unroll

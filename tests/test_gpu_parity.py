@@ -201,3 +201,22 @@ def test_strided_boxes_and_streams():
     err = rel_linf(got[:, 4:-4, 4:-4, 4:-4], ref[:, 4:-4, 4:-4, 4:-4])
     assert np.all(err <= 1e-10), err
     ctx.close()
+
+
+def test_integer_pipe_scaling_is_ieee_exact():
+    """The kernels' integer-pipe 2x and x/2 equal IEEE 2.0*x and 0.5*x bit for
+    bit, across zeros, subnormals, the normal/subnormal boundary, overflow and
+    random bit patterns."""
+    rng = np.random.default_rng(99)
+    edge = [0.0, -0.0, 5e-324, -5e-324, 1e-323, 1.5e-323, 2.2250738585072014e-308, 2.225073858507201e-308,
+            -2.2250738585072014e-308, 4.450147717014403e-308, 1.7976931348623157e308, 8.98846567431158e307,
+            -1.7976931348623157e308, np.inf, -np.inf, 1.0, 3.0, 0.1, -7.5]
+    pats = rng.integers(0, 2 ** 63 - 1, 200000, dtype=np.int64)
+    pats = pats ^ (rng.integers(0, 2, pats.size, dtype=np.int64) << 63)
+    x = np.concatenate([np.array(edge), pats.view(np.float64)])
+    x = x[~np.isnan(x)]
+    for variant in ("default", "exact"):
+        t, h = hb.hydro_selftest_scale2(torch.from_numpy(x).cuda(), variant)
+        with np.errstate(over="ignore"):
+            assert np.array_equal(t.cpu().numpy().view(np.int64), (2.0 * x).view(np.int64))
+            assert np.array_equal(h.cpu().numpy().view(np.int64), (0.5 * x).view(np.int64))
