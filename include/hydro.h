@@ -385,6 +385,14 @@ long long hydro_ctx_launches(const hydro_ctx_t* ctx);
  * IEEE 2.0*x and 0.5*x. */
 int hydro_selftest_scale2(const double* x, double* twice, double* half, long long n, void* stream);
 
+/* Diagnostics (no counterpart in the paper): the kernels' reciprocal,
+ * quotient and square root -- IEEE in the contraction-free build, Newton
+ * refinements of the hardware's approximations in the product build -- over
+ * x[0..n), y[0..n) (device arrays): rcp = 1/x, quo = y/x, sq = sqrt(x),
+ * asynchronously on `stream`, so a test can bound their error against IEEE. */
+int hydro_selftest_divsqrt(const double* x, const double* y, double* rcp, double* quo, double* sq, long long n,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

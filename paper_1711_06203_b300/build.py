@@ -1,10 +1,11 @@
 """Build the CUDA library in-tree for sm_103a.
 
 libhydro.so        — the product library (FP64, multiply-add contraction on)
-libhydro_exact.so  — the same sources with contraction off (-fmad=false): every
-                     multiply and add rounds separately, so its arithmetic is
-                     the scheme's operation order with no fused steps (used by
-                     the bitwise parity tests)
+libhydro_exact.so  — the same sources with contraction off (-fmad=false) and
+                     IEEE division and square root (HYDRO_IEEE_DIV_SQRT): every
+                     operation rounds separately, so its arithmetic is the
+                     scheme's operation order with no fused or refined steps
+                     (used by the bitwise parity tests)
 """
 import os
 import subprocess
@@ -42,7 +43,7 @@ def _stale(target):
 
 def build(force=False, verbose=False):
     os.makedirs(OUT, exist_ok=True)
-    variants = {"libhydro.so": [], "libhydro_exact.so": ["-fmad=false"]}
+    variants = {"libhydro.so": [], "libhydro_exact.so": ["-fmad=false", "-DHYDRO_IEEE_DIV_SQRT"]}
     for name, extra in variants.items():
         target = os.path.join(OUT, name)
         if not (force or _stale(target)):

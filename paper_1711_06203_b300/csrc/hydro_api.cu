@@ -189,6 +189,15 @@ __global__ void k_selftest_scale2(const double* __restrict__ x, double* __restri
   twice[i] = dtwice(x[i]);
   half[i] = dhalf(x[i]);
 }
+__global__ void k_selftest_divsqrt(const double* __restrict__ x, const double* __restrict__ y,
+                                   double* __restrict__ rcp, double* __restrict__ quo, double* __restrict__ sq,
+                                   long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rcp[i] = drcp(x[i]);
+  quo[i] = ddiv(y[i], x[i]);
+  sq[i] = dsqrt(x[i]);
+}
 }  // namespace
 
 extern "C" {
@@ -364,6 +373,15 @@ int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* cal
 }
 
 long long hydro_ctx_launches(const hydro_ctx_t* ctx) { return ctx ? ctx->launches : -1; }
+
+int hydro_selftest_divsqrt(const double* x, const double* y, double* rcp, double* quo, double* sq, long long n,
+                           void* stream) {
+  if (!x || !y || !rcp || !quo || !sq || n < 0) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  k_selftest_divsqrt<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, rcp, quo, sq,
+                                                                                                  n);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
 
 int hydro_selftest_scale2(const double* x, double* twice, double* half, long long n, void* stream) {
   if (!x || !twice || !half || n < 0) return HYDRO_EINVAL;

@@ -58,14 +58,14 @@ __device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __
   bool bad = false;
   cons_to_prim_flag(U, K, q, &inv, &bad);
   if (bad) atomicOr(&flags->bad, 1);
-  double c = sqrt(K.gamma * q[4] * inv);
+  double c = dsqrt(K.gamma * q[4] * inv);
   long long id = sg.id(i, j, k);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Q[v * sg.sc + id] = q[v];
   Q[QC * sg.sc + id] = c;
-  Q[QRC * sg.sc + id] = q[0] / c;
-  Q[QCR * sg.sc + id] = c / q[0];
-  Q[QIC2 * sg.sc + id] = 1.0 / (c * c);
+  Q[QRC * sg.sc + id] = ddiv(q[0], c);
+  Q[QCR * sg.sc + id] = ddiv(c, q[0]);
+  Q[QIC2 * sg.sc + id] = drcp(c * c);
 }
 
 // ---- stage 3 of a zone: characteristic tracing from its parabolas
@@ -396,7 +396,7 @@ __device__ __forceinline__ void update_item(BoxGeom in, BoxGeom out, ScratchGeom
     bool bad = false;
     cons_to_prim_flag(u1, K, q, &inv, &bad);
     if (bad) atomicOr(&flags->bad, 1);
-    double c = sqrt(K.gamma * q[4] * inv);
+    double c = dsqrt(K.gamma * q[4] * inv);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;
@@ -416,7 +416,7 @@ __device__ __forceinline__ void dt_partial_item(BoxGeom box, StepConst K, Range 
     bool bad = false;
     cons_to_prim_flag(U, K, q, &inv, &bad);
     if (bad) atomicOr(&flags->bad, 1);
-    double c = sqrt(K.gamma * q[4] * inv);
+    double c = dsqrt(K.gamma * q[4] * inv);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;

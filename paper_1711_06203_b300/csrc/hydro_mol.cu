@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(BLOCK) km_update(BoxGeom w0, BoxGeom ws, BoxGe
       bool bad = false;
       cons_to_prim_flag(hyd, K, q, &inv, &bad);
       if (bad) atomicOr(&flags->bad, 1);
-      const double cs = sqrt(K.gamma * q[4] * inv);
+      const double cs = dsqrt(K.gamma * q[4] * inv);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
         if (d < K.dim) spd[d] = fabs(q[1 + d]) + cs;

@@ -220,3 +220,34 @@ def test_integer_pipe_scaling_is_ieee_exact():
         with np.errstate(over="ignore"):
             assert np.array_equal(t.cpu().numpy().view(np.int64), (2.0 * x).view(np.int64))
             assert np.array_equal(h.cpu().numpy().view(np.int64), (0.5 * x).view(np.int64))
+
+
+def _ulps(a, b):
+    """Distance in units in the last place between float64 arrays of one sign."""
+    return np.abs(a.view(np.int64) - b.view(np.int64))
+
+
+def test_reciprocal_quotient_sqrt_error_bounds():
+    """The product build's Newton-refined 1/x, y/x and sqrt(x) stay within 2
+    ulp of IEEE over magnitudes 1e-300..1e300 (arguments outside the refined
+    range, zeros and infinities take the IEEE path); the contraction-free
+    build is IEEE exactly."""
+    rng = np.random.default_rng(7)
+    x = 10.0 ** rng.uniform(-300, 300, 400000)
+    x[::7] *= -1.0
+    y = rng.standard_normal(x.size) * 10.0 ** rng.uniform(-20, 20, x.size)
+    x = np.concatenate([x, [0.0, -0.0, np.inf, 5e-324, 2.2250738585072014e-308, 1.7976931348623157e308]])
+    y = np.concatenate([y, [1.0, 1.0, 1.0, 1.0, 1.0, 1.0]])
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        ref = (1.0 / x, y / x, np.sqrt(x))
+    for variant, bound in (("exact", 0), ("default", 2)):
+        got = hb.hydro_selftest_divsqrt(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), variant)
+        for g, w in zip(got, ref):
+            g = g.cpu().numpy()
+            both_nan = np.isnan(g) & np.isnan(w)
+            assert np.array_equal(np.isnan(g), np.isnan(w))
+            fin = ~both_nan & np.isfinite(w)
+            assert np.array_equal(g[~both_nan & ~np.isfinite(w)], w[~both_nan & ~np.isfinite(w)])
+            same_sign = np.signbit(g[fin]) == np.signbit(w[fin])
+            assert same_sign.all()
+            assert _ulps(g[fin], w[fin]).max() <= bound, (variant, _ulps(g[fin], w[fin]).max())
