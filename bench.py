@@ -164,6 +164,32 @@ def cpu_oracle_rate(U, n, steps, budget_s=25.0):
     return n ** 3 * done / t_total, done, t_total, U
 
 
+def cpu_oracle_rate_one_core(n=64):
+    """Oracle zone-updates/s on one host core: one n^3 Sedov step with the
+    oracle's OpenMP runtime limited to one thread (restored afterwards)."""
+    import ctypes
+
+    import oracle
+    from paper_1711_06203_b300 import inputs
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+    before = gomp.omp_get_max_threads()
+    U, _ = inputs.sedov(n)
+    P = oracle.params(3, (n, n, n), bc=oracle.BC_OUTFLOW, gamma=1.4, cfl=0.5)
+    d, _ = oracle.dt(U, P)
+    gomp.omp_set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.step(U, P, d)
+        sec = time.perf_counter() - t0
+    finally:
+        gomp.omp_set_num_threads(before)
+    return {"value": n ** 3 / sec, "unit": "zone-updates/s", "cores": 1,
+            "sample": f"one {n}^3 Sedov oracle step on one thread"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -700,7 +726,8 @@ def run_ours(args):
     launches = ctx.hydro_ctx_launches() - launches0
     stage_ms, calls = ctx.hydro_ctx_stage_times()
     ctx.hydro_ctx_set_profiling(False)
-    total_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), dist, dev)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     zones = n ** 3
     value = whole_job_rate(zones, world, args.steps, total_ms)
 
@@ -759,10 +786,11 @@ def run_ours(args):
         rate, done, t, _ = cpu_oracle_rate(U0, n, 50, budget_s=20.0)
         cpu = {"value": rate, "unit": "zone-updates/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{done} full {n}^3 oracle steps from the initial Sedov state",
-               "cpu_model": cpu_model()}
+               "cpu_model": cpu_model(), "one_core": cpu_oracle_rate_one_core()}
     line = {
         "metric": "3D PPM zone-updates/s", "value": value, "unit": "zone-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_median": statistics.median(step_ms), "ms_per_step_range": [min(step_ms), max(step_ms)],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"sedov3d_{n}^3", "n": n, "gamma": 1.4, "cfl": 0.5, "bc": "outflow",
