@@ -186,6 +186,18 @@ int hydro_level_min_dt(const double* dt_next_dev, double* dt_dev, int nbox, void
  * Returns the number of tuned extents. */
 int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
 
+/* hydro_advance_box on host buffers: in->u and out->u point to host memory
+ * (pinned or pageable) holding grown boxes in the natural layout (stride[0]
+ * = nx+8, stride[1] = stride[0]*(ny+8), stride[2] = stride[1]*(nz+8, or 1
+ * in 2-D), 5 components).  The call copies the input to context-owned device
+ * memory, runs the step and copies the whole grown output box back (its
+ * ghost zones are unspecified), all on `stream`, and returns once the host
+ * output is complete.  dt_next_host (nullable) receives the CFL step of the
+ * result; a non-physical state returns HYDRO_EBADSTATE.  HYDRO_EINVAL for
+ * other layouts or overlapping host buffers. */
+int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                           const hydro_params_t* params, double dt, double* dt_next_host, void* stream);
+
 /* hydro_advance_box with the retry mechanism of paper Sec. 3.2 (Castro can
  * redo a step based on criteria evaluated during the integration): if the
  * step meets a non-physical state (rho <= 0, p <= 0 or non-finite, in the

@@ -126,6 +126,7 @@ def lib(variant="default"):
     L.hydro_dt.argtypes = [vp, B, P, D, vp]
     L.hydro_advance_box.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_box_noalloc.argtypes = [B, B, P, ctypes.c_double, D, vp]
+    L.hydro_advance_box_host.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_box_retry.argtypes = [vp, B, B, P, ctypes.c_double, ctypes.c_int, D, D, vp]
     L.hydro_advance_batch.argtypes = [vp, B, B, ctypes.c_int, P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
@@ -276,6 +277,16 @@ class Context:
         if rc and raise_on_error:
             raise HydroError(rc, "hydro_mol_advance_box")
         return (out.value if want_dt_next else None) if raise_on_error else (rc, out.value)
+
+    def hydro_advance_box_host(self, bin_, bout, p, dt, want_dt_next=False, stream=None):
+        """The step on host buffers (hydro_box_t of CPU tensors in the natural
+        grown layout); returns once the host output is written."""
+        out = ctypes.c_double(0.0)
+        rc = self.L.hydro_advance_box_host(self.h, ctypes.byref(bin_), ctypes.byref(bout), ctypes.byref(p), float(dt),
+                                           ctypes.byref(out) if want_dt_next else None, _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_advance_box_host")
+        return out.value if want_dt_next else None
 
     def hydro_advance_box_retry(self, bin_, bout, p, dt, max_retries=3, stream=None):
         """Returns (status, dt_taken, dt_next) of the step with retries on bad states."""

@@ -252,6 +252,7 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
   hydro_batch_release(ctx);
   hydro_level_release(ctx);
   hydro_amr_release(ctx);
+  if (ctx->host_stage) cudaFree(ctx->host_stage);
   delete ctx;
 }
 
@@ -330,6 +331,52 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
     if (h.bad) return HYDRO_EBADSTATE;
   }
   return HYDRO_OK;
+}
+
+int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
+                           const hydro_params_t* params, double dt, double* dt_next_host, void* stream) {
+  if (!ctx || !in || !out || !in->u || !out->u || !valid_params(params)) return HYDRO_EINVAL;
+  const int dim = params->dim;
+  if (!valid_box(in, dim)) return HYDRO_EINVAL;
+  const long long gx = in->n[0] + 2 * NG, gy = in->n[1] + 2 * NG, gz = (dim == 3) ? in->n[2] + 2 * NG : 1;
+  for (const hydro_box_t* b : {in, out}) {
+    if (b->stride[0] != gx || b->stride[1] != gx * gy || b->stride[2] != gx * gy * gz || b->ng != NG) return HYDRO_EINVAL;
+    for (int a = 0; a < 3; ++a)
+      if (b->n[a] != in->n[a]) return HYDRO_EINVAL;
+  }
+  const size_t elems = (size_t)5 * gx * gy * gz, bytes = elems * sizeof(double);
+  {
+    const char *a0 = reinterpret_cast<const char*>(in->u), *b0 = reinterpret_cast<const char*>(out->u);
+    if (a0 < b0 + bytes && b0 < a0 + bytes) return HYDRO_EINVAL;  // host buffers overlap
+  }
+  if (!(dt > 0.0) || !std::isfinite(dt)) return HYDRO_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HYDRO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (2 * bytes > ctx->host_stage_bytes) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
+    if (ctx->host_stage) cudaFree(ctx->host_stage);
+    ctx->host_stage = nullptr;
+    ctx->host_stage_bytes = 0;
+    if (ctx->fail_alloc || cudaMalloc(&ctx->host_stage, 2 * bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return HYDRO_ENOMEM;
+    }
+    ctx->host_stage_bytes = 2 * bytes;
+  }
+  hydro_box_t din = *in, dout = *out;
+  din.u = ctx->host_stage;
+  dout.u = ctx->host_stage + elems;
+  for (int a = 0; a < 3; ++a) dout.dx[a] = in->dx[a];
+  if (cudaMemcpyAsync(din.u, in->u, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HYDRO_ECUDA;
+  int rc = hydro_advance_box(ctx, &din, &dout, params, dt, nullptr, st);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(out->u, dout.u, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HYDRO_ECUDA;
+  DevFlags h;
+  rc = read_flags(ctx, st, &h);  // synchronises: the host output is complete on return
+  if (rc) return rc;
+  if (dt_next_host) *dt_next_host = h.dt_next;
+  return h.bad ? HYDRO_EBADSTATE : HYDRO_OK;
 }
 
 int hydro_advance_box_retry(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,

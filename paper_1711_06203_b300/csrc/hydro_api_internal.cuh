@@ -23,6 +23,8 @@ struct hydro_ctx {
   cudaEvent_t events[hydro::NSTAGES + 1] = {};
   double stage_ms[hydro::NSTAGES] = {};
   long long stage_calls = 0;
+  double* host_stage = nullptr;   // device in/out boxes of hydro_advance_box_host (grown on demand)
+  size_t host_stage_bytes = 0;
 };
 
 void hydro_batch_release(hydro_ctx* ctx);

@@ -251,3 +251,34 @@ def test_reciprocal_quotient_sqrt_error_bounds():
             same_sign = np.signbit(g[fin]) == np.signbit(w[fin])
             assert same_sign.all()
             assert _ulps(g[fin], w[fin]).max() <= bound, (variant, _ulps(g[fin], w[fin]).max())
+
+
+def test_host_buffer_step_matches_device_step():
+    """hydro_advance_box_host on pageable and pinned host buffers gives the
+    device path's result bit for bit, and refuses non-natural layouts."""
+    rng = np.random.default_rng(12)
+    n = (13, 10, 11)
+    U = inputs.random_box(rng, n, 3)
+    bc = ((hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW), (hb.BC_OUTFLOW,) * 2)
+    dx = (0.05,) * 3
+    p = hb.params(3, gamma=5 / 3)
+    ctx = hb.Context(0)
+    P = oracle_params(3, n, dx, bc, 5 / 3)
+    d, _ = oracle.dt(U, P)
+    a = to_dev(U)
+    b = torch.empty_like(a)
+    dn_dev = ctx.hydro_advance_box(hb.box(a, n, dx, bc), hb.box(b, n, dx, bc), p, d, want_dt_next=True)
+    want = b.cpu().numpy()
+    for pinned in (False, True):
+        hin = torch.from_numpy(U.copy())
+        hout = torch.full_like(hin, float("nan"))
+        if pinned:
+            hin, hout = hin.pin_memory(), hout.pin_memory()
+        dn = ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, d, want_dt_next=True)
+        assert dn == dn_dev
+        assert np.array_equal(interior(hout.numpy(), 3), interior(want, 3))
+    big = torch.zeros((5, 20, 19, 22), dtype=torch.float64)  # padded rows: not the natural layout
+    with pytest.raises(hb.HydroError) as e:
+        ctx.hydro_advance_box_host(hb.box(big[:, :, :18, :21], n, dx, bc), hb.box(hout, n, dx, bc), p, d)
+    assert e.value.status == hb.HYDRO_EINVAL
+    ctx.close()
