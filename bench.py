@@ -296,6 +296,42 @@ def bench_batch(args, dev, stream):
             "l2": "working set 3.7 GB of state + scratch, larger than L2"}
 
 
+def batch_profile(args):
+    """Batched steps of the first NBOX boxes of the 512-box level (same seed
+    and shapes), one plan build then args.steps graph replays; prints the
+    per-step time.  No per-box runs, so a profiler capture stays small."""
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    dev = torch.device("cuda", 0)
+    sizes, Us = inputs.level_boxes(512, seed=1711)
+    sizes, Us = sizes[:args.batch_profile], Us[:args.batch_profile]
+    dx = (1.0 / 64,) * 3
+    a = [torch.from_numpy(U).to(dev) for U in Us]
+    out = [torch.empty_like(x) for x in a]
+    bin_ = [hb.box(x, s, dx, hb.BC_PREFILLED) for x, s in zip(a, sizes)]
+    bout = [hb.box(x, s, dx, hb.BC_PREFILLED) for x, s in zip(out, sizes)]
+    p = hb.params(3, gamma=5.0 / 3.0, cfl=0.5)
+    ctx = hb.Context(0)
+    dt_dev = torch.full((len(sizes),), 1e-4, dtype=torch.float64, device=dev)
+    ctx.hydro_advance_batch(bin_, bout, p, dt_dev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.hydro_advance_batch(bin_, bout, p, dt_dev)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    zones = sum(x * y * z for x, y, z in sizes)
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"boxes": len(sizes), "interior_zones": zones, "ms_per_step": ms,
+                      "zone_updates_per_s": zones / (ms * 1e-3)}), flush=True)
+    ctx.close()
+    return 0
+
+
 def stratified_device(n, dev, H=0.1, g=1.0, gamma=5.0 / 3.0, perturb=1e-3, seed=1711):
     """Isothermal atmosphere rho = exp(-z/H), p = rho g H (1 + perturb N(0,1)),
     at rest, built directly on the device (the recipe of inputs.stratified; a
@@ -842,18 +878,26 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 512^3 large-box leg")
     ap.add_argument("--mol-only", action="store_true",
                     help="run only the method-of-lines leg at --n and print its JSON (for profiling)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched-level leg and print its JSON (for profiling)")
+    ap.add_argument("--batch-profile", type=int, default=0, metavar="NBOX",
+                    help="only batched steps of the first NBOX boxes of the level, no per-box comparison "
+                         "(a small case for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
-    if args.mol_only:
+    if args.batch_profile:
+        return batch_profile(args)
+    if args.mol_only or args.batch_only:
         import torch
 
         dev = torch.device("cuda", 0)
         with torch.cuda.device(dev):
             stream = torch.cuda.current_stream(dev)
-            print(json.dumps(bench_mol(args, dev, stream, cpu_sample=False)), flush=True)
+            leg = bench_mol(args, dev, stream, cpu_sample=False) if args.mol_only else bench_batch(args, dev, stream)
+            print(json.dumps(leg), flush=True)
         return 0
     return run_ours(args)
 
