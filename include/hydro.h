@@ -405,6 +405,13 @@ int hydro_selftest_scale2(const double* x, double* twice, double* half, long lon
 int hydro_selftest_divsqrt(const double* x, const double* y, double* rcp, double* quo, double* sq, long long n,
                            void* stream);
 
+/* Diagnostics (no counterpart in the paper): the kernels form part of their
+ * FP64 products and sums from the operands' bit patterns on the integer
+ * pipe; this runs those two routines over x[0..n), y[0..n) (device arrays):
+ * prod = x*y, sum = x+y, asynchronously on `stream`, so a test can compare
+ * them bit for bit with the IEEE operations (round to nearest even). */
+int hydro_selftest_intpipe(const double* x, const double* y, double* prod, double* sum, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -135,6 +135,7 @@ def lib(variant="default"):
     L.hydro_level_min_dt.argtypes = [vp, vp, ctypes.c_int, vp]
     L.hydro_selftest_scale2.argtypes = [vp, vp, vp, ctypes.c_longlong, vp]
     L.hydro_selftest_divsqrt.argtypes = [vp, vp, vp, vp, vp, ctypes.c_longlong, vp]
+    L.hydro_selftest_intpipe.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, vp]
     L.hydro_mol_advance_box.argtypes = [vp, B, B, P, ctypes.c_int, ctypes.c_double, D, vp]
     L.hydro_amr_advance.argtypes = [vp, ctypes.POINTER(hydro_amr_t), P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
@@ -218,6 +219,19 @@ def hydro_selftest_divsqrt(x, y, variant="default", stream=None):
     if rc:
         raise HydroError(rc, "hydro_selftest_divsqrt")
     return r, q, s
+
+
+def hydro_selftest_intpipe(x, y, variant="default", stream=None):
+    """Run the kernels' integer-pipe product and sum over CUDA float64 tensors
+    x, y; returns (x*y, x+y) tensors."""
+    import torch
+    x, y = x.contiguous(), y.contiguous()
+    p, s = torch.empty_like(x), torch.empty_like(x)
+    rc = lib(variant).hydro_selftest_intpipe(*[ctypes.c_void_p(t.data_ptr()) for t in (x, y, p, s)], x.numel(),
+                                             _stream_handle(stream))
+    if rc:
+        raise HydroError(rc, "hydro_selftest_intpipe")
+    return p, s
 
 
 def hydro_advance_box_noalloc(bin_, bout, p, dt, want_dt_next=False, stream=None, variant="default"):

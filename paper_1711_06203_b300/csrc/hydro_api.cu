@@ -198,6 +198,13 @@ __global__ void k_selftest_divsqrt(const double* __restrict__ x, const double* _
   quo[i] = ddiv(y[i], x[i]);
   sq[i] = dsqrt(x[i]);
 }
+__global__ void k_selftest_intpipe(const double* __restrict__ x, const double* __restrict__ y,
+                                   double* __restrict__ prod, double* __restrict__ sum, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  prod[i] = mul_i(x[i], y[i]);
+  sum[i] = add_i(x[i], y[i]);
+}
 }  // namespace
 
 extern "C" {
@@ -427,6 +434,13 @@ int hydro_selftest_divsqrt(const double* x, const double* y, double* rcp, double
   if (n == 0) return HYDRO_OK;
   k_selftest_divsqrt<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, rcp, quo, sq,
                                                                                                   n);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+int hydro_selftest_intpipe(const double* x, const double* y, double* prod, double* sum, long long n, void* stream) {
+  if (!x || !y || !prod || !sum || n < 0) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  k_selftest_intpipe<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, prod, sum, n);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 

@@ -99,6 +99,104 @@ __device__ __forceinline__ double dhalf(double x) {
   }
   return __longlong_as_double(r);
 }
+// ---------------------------------------------------------------- FP64 products and sums on the integer pipe
+// B300 issues FP64 arithmetic at 2 lanes per clock per SM, while each SM
+// partition's integer ALU and IMAD pipes take 16 lanes per clock each.  A
+// binary64 product rounded to nearest even, formed from the bit patterns
+// (significand product in 32-bit limbs, normalise, round, repack), costs
+// about 30 ALU and 15 IMAD instructions: roughly one native multiply's worth
+// of issue time, but on other units.  Moving a share of a kernel's products
+// (and, at about twice that cost, a few sums) there runs them beside the
+// FP64 pipe instead of queueing on it.  Both functions return the IEEE
+// result bit for bit (a GPU test compares them with the hardware operations
+// over edge cases and random bit patterns), so the contraction-free build
+// still performs exactly the oracle's operations.
+// 32-bit unsigned a < b and a != b on the integer pipe
+__device__ __forceinline__ bool ult32(unsigned a, unsigned b) {
+  int r;
+  asm("{\n\t.reg .pred p;\n\tsetp.lo.u32 p, %1, %2;\n\tselp.s32 %0, 1, 0, p;\n\t}" : "=r"(r) : "r"(a), "r"(b));
+  return r != 0;
+}
+__device__ __forceinline__ bool ne32(unsigned a, unsigned b) {
+  int r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, %2;\n\tselp.s32 %0, 1, 0, p;\n\t}" : "=r"(r) : "r"(a), "r"(b));
+  return r != 0;
+}
+// a * b, IEEE binary64, round to nearest even.  Normal operands with a normal
+// result, and zero operands, stay on the integer pipe; subnormal, infinite or
+// NaN operands and results that over- or underflow take the FP64 multiply.
+__device__ __forceinline__ double mul_i(double a, double b) {
+  const unsigned long long ua = (unsigned long long)dbits(a), ub = (unsigned long long)dbits(b);
+  const unsigned ah0 = (unsigned)(ua >> 32), bh0 = (unsigned)(ub >> 32), al = (unsigned)ua, bl = (unsigned)ub;
+  const unsigned ea = (ah0 >> 20) & 0x7FFu, eb = (bh0 >> 20) & 0x7FFu;
+  const unsigned ah = (ah0 & 0xFFFFFu) | 0x100000u, bh = (bh0 & 0xFFFFFu) | 0x100000u;
+  // significands (ah:al)(bh:bl) = P = v 2^64 + w1 2^32 + w0, 2^104 <= P < 2^106
+  const unsigned long long t = (unsigned long long)al * bl;
+  const unsigned long long u = (unsigned long long)ah * bl + (t >> 32);
+  const unsigned long long u2 = (unsigned long long)al * bh + u;
+  const unsigned long long v = (unsigned long long)ah * bh + (u2 >> 32);
+  const unsigned w1 = (unsigned)u2, w0 = (unsigned)t;
+  const unsigned top = (unsigned)(v >> 41);  // P >= 2^105
+  // 53-bit significand q = P >> (52 + top); guard bit below it; sticky below that
+  unsigned long long q = (v << (12 - top)) | (unsigned long long)(w1 >> (20 + top));
+  const unsigned guard = (w1 >> (19 + top)) & 1u;
+  const unsigned sticky = (w1 & ((1u << (19 + top)) - 1u)) | w0;
+  q += (unsigned long long)(guard & ((ne32(sticky, 0u) ? 1u : 0u) | ((unsigned)q & 1u)));
+  const int e = (int)(ea + eb) - 1023 + (int)top;
+  const unsigned long long sign = (unsigned long long)((ah0 ^ bh0) & 0x80000000u) << 32;
+  // the significand's leading bit adds one to the exponent field, and a
+  // rounding carry out of the significand adds one more
+  unsigned long long r = ((((unsigned long long)(unsigned)(e - 1)) << 52) + q) | sign;
+  const bool a_zero = !ne32((ah0 & 0x7FFFFFFFu) | al, 0u), b_zero = !ne32((bh0 & 0x7FFFFFFFu) | bl, 0u);
+  const bool zero = (a_zero && ne32(eb, 0x7FFu)) || (b_zero && ne32(ea, 0x7FFu));
+  const bool fast = ult32(ea - 1u, 2046u) && ult32(eb - 1u, 2046u) && ult32((unsigned)(e - 1), 2046u);
+  if (__builtin_expect(!(fast || zero), 0)) r = (unsigned long long)dbits(__dmul_rn(a, b));
+  r = zero ? sign : r;
+  return __longlong_as_double((long long)r);
+}
+// a + b, IEEE binary64, round to nearest even, for every input (an invalid
+// operation returns a NaN).
+__device__ __forceinline__ double add_i(double a, double b) {
+  const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull, FRAC = 0x000FFFFFFFFFFFFFull, IMPL = 1ull << 52;
+  const unsigned long long ua = (unsigned long long)dbits(a), ub = (unsigned long long)dbits(b);
+  const unsigned long long aa = ua & ABS, ab = ub & ABS;
+  // order by magnitude (the sign of the difference of two values < 2^63)
+  const bool swap = (long long)(aa - ab) < 0;
+  const unsigned long long x = swap ? ub : ua, y = swap ? ua : ub;
+  const unsigned long long xm = x & ABS, ym = y & ABS;
+  const unsigned xh = (unsigned)(xm >> 32), yh = (unsigned)(ym >> 32);
+  int ex = (int)(xh >> 20), ey = (int)(yh >> 20);
+  // significands with 10 guard bits; a subnormal has exponent 1 and no leading bit
+  unsigned long long mx = ((xm & FRAC) | (ne32((unsigned)ex, 0u) ? IMPL : 0ull)) << 10;
+  unsigned long long my = ((ym & FRAC) | (ne32((unsigned)ey, 0u) ? IMPL : 0ull)) << 10;
+  ex = max(ex, 1);
+  ey = max(ey, 1);
+  const int d = min(ex - ey, 63);
+  const unsigned long long lost = my << (64 - d);  // the bits the alignment drops (none for d = 0)
+  my = (my >> d) | (ne32((unsigned)(lost >> 32) | (unsigned)lost, 0u) ? 1ull : 0ull);
+  const bool sub = (int)((unsigned)(x >> 32) ^ (unsigned)(y >> 32)) < 0;
+  unsigned long long s = mx + (sub ? (0ull - my) : my);
+  const int carry = (int)(s >> 63);
+  s = carry ? ((s >> 1) | (s & 1ull)) : s;
+  int e = ex + carry;
+  const unsigned sh_hi = (unsigned)(s >> 32), sh_lo = (unsigned)s;
+  const bool nonzero = ne32(sh_hi | sh_lo, 0u);
+  const int lz = (ne32(sh_hi, 0u) ? __clz(sh_hi) : 32 + __clz(sh_lo)) - 1;
+  const int sh = min(lz, e - 1);  // normalise, but not below the smallest exponent
+  s <<= sh;
+  e -= sh;
+  const unsigned long long q = (s + 0x1FFull + ((s >> 10) & 1ull)) >> 10;  // round half to even
+  unsigned long long r = ((unsigned long long)(e - 1) << 52) + q;
+  r = ult32((unsigned)(r >> 32), 0x7FF00000u) ? r : 0x7FF0000000000000ull;  // overflow
+  r |= x & 0x8000000000000000ull;
+  r = nonzero ? r : (sub ? 0ull : (x & 0x8000000000000000ull));  // exact zero: +0 unless both -0
+  // an infinite or NaN operand is the one of larger magnitude
+  const bool special = !ult32(xh, 0x7FF00000u);
+  const bool nan = ne32((xh & 0xFFFFFu) | (unsigned)xm, 0u) || (!ult32(yh, 0x7FF00000u) && sub);
+  r = special ? (nan ? 0x7FFFFFFFFFFFFFFFull : x) : r;
+  return __longlong_as_double((long long)r);
+}
+
 // Reciprocal, quotient and square root.  The contraction-free build keeps the
 // IEEE operations, so it agrees with the oracle bit for bit.  The product
 // build refines the hardware's approximate reciprocal and reciprocal square
@@ -136,15 +234,15 @@ __device__ __forceinline__ double ddiv(double a, double b) {
   const double ab = __longlong_as_double(dbits(b) & 0x7FFFFFFFFFFFFFFFLL);
   if (__builtin_expect(!newton_range(ab), 0)) return a / b;
   const double r = rcp_newton(ab);
-  return a * __longlong_as_double(dbits(r) | (dbits(b) & (long long)0x8000000000000000ULL));
+  return mul_i(a, __longlong_as_double(dbits(r) | (dbits(b) & (long long)0x8000000000000000ULL)));
 }
 __device__ __forceinline__ double dsqrt(double x) {
   if (__builtin_expect(!newton_range(x), 0)) return sqrt(x);
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-(x * y), y, 1.0);
+  const double e = fma(-mul_i(x, y), y, 1.0);
   y = fma(dhalf(e), y, y);
-  const double sq = x * y;
+  const double sq = mul_i(x, y);
   return fma(fma(-sq, sq, x), dhalf(y), sq);
 }
 #endif
@@ -192,7 +290,7 @@ __device__ __forceinline__ void cons_to_prim_flag(const double U[5], const StepC
 enum { S_RHO = 0, S_P = 4, S_E = 5, S_INV = 6, NS = 7 };
 
 __device__ __forceinline__ double energy_of(const double q[5], const StepConst& K) {
-  return q[4] * K.gm1inv + dhalf(q[0]) * ((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
+  return q[4] * K.gm1inv + mul_i(dhalf(q[0]), (mul_i(q[1], q[1]) + q[2] * q[2]) + q[3] * q[3]);
 }
 
 __device__ __forceinline__ void state_from_prim(const double q[5], const StepConst& K, double s[NS]) {
@@ -205,9 +303,9 @@ __device__ __forceinline__ void state_from_prim(const double q[5], const StepCon
 __device__ __forceinline__ void state_from_cons(const double U[5], const StepConst& K, double s[NS]) {
   double rho = dmax(U[0], K.small_dens);
   double inv = drcp(rho);
-  double u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
-  double ke = dhalf(rho) * ((u * u + v * v) + w * w);
-  double p = K.gm1 * (U[4] - ke);
+  double u = mul_i(U[1], inv), v = mul_i(U[2], inv), w = mul_i(U[3], inv);
+  double ke = dhalf(rho) * ((mul_i(u, u) + v * v) + w * w);
+  double p = mul_i(K.gm1, U[4] - ke);
   p = dmax(p, K.small_pres);
   s[0] = rho; s[1] = u; s[2] = v; s[3] = w; s[4] = p;
   s[S_E] = U[4];
@@ -278,8 +376,8 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
                                           double F[5]) {
   double rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
   double rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
-  double cl = dsqrt(K.gamma * pl * sL[S_INV]);
-  double cr = dsqrt(K.gamma * pr * sR[S_INV]);
+  double cl = dsqrt(mul_i(mul_i(K.gamma, pl), sL[S_INV]));
+  double cr = dsqrt(mul_i(mul_i(K.gamma, pr), sR[S_INV]));
   double sl, sr;
   if (!K.einfeldt) {  // Davis
     sl = dmin(ul - cl, ur - cr);
@@ -297,18 +395,18 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
     sl = dmin(ul - cl, utn - ct);
     sr = dmax(ur + cr, utn + ct);
   }
-  double ml = rl * (sl - ul), mr = rr * (sr - ur);
+  double ml = mul_i(rl, sl - ul), mr = mul_i(rr, sr - ur);
   double sstar = ddiv((pr - pl) + ml * ul - mr * ur, ml - mr);
   int region = ge0(sl) ? 0 : ge0(sstar) ? 1 : gt0(sr) ? 2 : 3;
   bool left = region <= 1;
   const double* s = left ? sL : sR;
   double rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];
-  double mass = rho * un;
+  double mass = mul_i(rho, un);
   double Fk[5];
   Fk[0] = mass;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) Fk[1 + k] = (k == d) ? mass * un + p : mass * s[1 + k];
-  Fk[4] = un * (E + p);
+  for (int k = 0; k < 3; ++k) Fk[1 + k] = (k == d) ? mass * un + p : mul_i(mass, s[1 + k]);
+  Fk[4] = mul_i(un, E + p);
   if (region == 0 || region == 3) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) F[c] = Fk[c];
@@ -317,12 +415,12 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   double sk = left ? sl : sr, mk = left ? ml : mr;
   double Uk[5] = {rho, rho * s[1], rho * s[2], rho * s[3], E};
   double r = drcp(sk - sstar);
-  double f = mk * r;
+  double f = mul_i(mk, r);
   double Us[5];
   Us[0] = f;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) Us[1 + k] = (k == d) ? f * sstar : f * s[1 + k];
-  Us[4] = f * (E * s[S_INV]) + (sstar - un) * (f * sstar + p * r);
+  for (int k = 0; k < 3; ++k) Us[1 + k] = (k == d) ? mul_i(f, sstar) : mul_i(f, s[1 + k]);
+  Us[4] = f * mul_i(E, s[S_INV]) + mul_i(sstar - un, f * sstar + mul_i(p, r));
 #pragma unroll
   for (int c = 0; c < 5; ++c) F[c] = Fk[c] + sk * (Us[c] - Uk[c]);
   return left;

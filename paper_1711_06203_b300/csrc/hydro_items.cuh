@@ -235,7 +235,7 @@ __device__ __forceinline__ void traced_state(double* __restrict__ T, long long s
   for (int c = 0; c < 5; ++c) q[c] = T[c * sc + id];
   state_from_prim(q, K, s);
 #pragma unroll
-  for (int c = 1; c < 4; ++c) T[(TS_MOM + c - 1) * sc + id] = q[0] * q[c];
+  for (int c = 1; c < 4; ++c) T[(TS_MOM + c - 1) * sc + id] = mul_i(q[0], q[c]);
   T[TS_E * sc + id] = s[S_E];
 }
 __device__ __forceinline__ void store5(double* __restrict__ A, long long sc, long long id, const double v[5]) {

@@ -222,6 +222,51 @@ def test_integer_pipe_scaling_is_ieee_exact():
             assert np.array_equal(h.cpu().numpy().view(np.int64), (0.5 * x).view(np.int64))
 
 
+def _intpipe_operands(rng):
+    """Operand pairs for the integer-pipe product and sum: signed zeros,
+    subnormals, the normal/subnormal boundary, the largest values,
+    infinities, random bit patterns, products that over- and underflow,
+    rounding ties, and sums with every exponent gap including cancellation."""
+    edge = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, 2.225073858507201e-308,
+                     1.7976931348623157e308, -1.7976931348623157e308, np.inf, -np.inf, 1.0, -1.0, 0.5, 3.0,
+                     0.1, 1e-300, 1e300, 1.0000000000000002, 0.9999999999999999])
+    ex, ey = np.meshgrid(edge, edge)
+    n = 400000
+    bits = rng.integers(0, 2 ** 63 - 1, (2, n), dtype=np.int64)
+    bits ^= rng.integers(0, 2, (2, n), dtype=np.int64) << 63
+    rx, ry = bits.view(np.float64)
+    # moderate magnitudes with exponent gaps 0..70 and near-cancellation
+    m = rng.uniform(1.0, 2.0, n) * 2.0 ** rng.integers(-60, 60, n)
+    gap = m * rng.uniform(1.0, 2.0, n) * 2.0 ** -rng.integers(0, 70, n) * rng.choice([-1.0, 1.0], n)
+    near = -(m * (1.0 + rng.integers(-8, 8, n) * 2.0 ** -52))
+    # products near 1 whose exact significand product ends in a tie or near one
+    t1 = 1.0 + rng.integers(0, 2 ** 26, n) * 2.0 ** -26
+    t2 = 1.0 + rng.integers(0, 2 ** 27, n) * 2.0 ** -27
+    # products across the overflow and underflow thresholds
+    big = rng.uniform(1.0, 2.0, n) * 2.0 ** rng.integers(500, 530, n)
+    tiny = rng.uniform(1.0, 2.0, n) * 2.0 ** rng.integers(-560, -500, n)
+    x = np.concatenate([ex.ravel(), rx, m, m, t1, big, tiny, tiny])
+    y = np.concatenate([ey.ravel(), ry, gap, near, t2, big, tiny, big])
+    keep = ~(np.isnan(x) | np.isnan(y))
+    return x[keep], y[keep]
+
+
+def test_integer_pipe_products_and_sums_are_ieee_exact():
+    """The kernels' integer-pipe x*y and x+y equal the IEEE operations (round
+    to nearest even) bit for bit, in both builds; invalid operations give a
+    NaN."""
+    x, y = _intpipe_operands(np.random.default_rng(1711))
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        ref_p, ref_s = x * y, x + y
+    for variant in ("default", "exact"):
+        p, s = hb.hydro_selftest_intpipe(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), variant)
+        for got, ref in ((p.cpu().numpy(), ref_p), (s.cpu().numpy(), ref_s)):
+            assert np.array_equal(np.isnan(got), np.isnan(ref))
+            ok = ~np.isnan(ref)
+            bad = np.flatnonzero(got[ok].view(np.int64) != ref[ok].view(np.int64))
+            assert bad.size == 0, (variant, x[ok][bad[:4]], y[ok][bad[:4]], got[ok][bad[:4]], ref[ok][bad[:4]])
+
+
 def _ulps(a, b):
     """Distance in units in the last place between float64 arrays of one sign."""
     return np.abs(a.view(np.int64) - b.view(np.int64))
