@@ -99,6 +99,11 @@ __device__ __forceinline__ double dhalf(double x) {
   }
   return __longlong_as_double(r);
 }
+// -x by flipping the sign bit on the integer pipe (a negated operand that
+// feeds the integer-pipe product below would otherwise be formed on the FP64 pipe)
+__device__ __forceinline__ double dneg(double x) {
+  return __longlong_as_double(dbits(x) ^ (long long)0x8000000000000000ULL);
+}
 // ---------------------------------------------------------------- FP64 products and sums on the integer pipe
 // B300 issues FP64 arithmetic at 2 lanes per clock per SM, while each SM
 // partition's integer ALU and IMAD pipes take 16 lanes per clock each.  A
@@ -196,7 +201,6 @@ __device__ __forceinline__ double add_i(double a, double b) {
   r = special ? (nan ? 0x7FFFFFFFFFFFFFFFull : x) : r;
   return __longlong_as_double((long long)r);
 }
-
 // Reciprocal, quotient and square root.  The contraction-free build keeps the
 // IEEE operations, so it agrees with the oracle bit for bit.  The product
 // build refines the hardware's approximate reciprocal and reciprocal square
@@ -277,9 +281,9 @@ __device__ __forceinline__ void cons_to_prim_flag(const double U[5], const StepC
   if (!(gt0(rho) && dfinite(rho))) *bad = true;
   rho = dmax(rho, K.small_dens);
   double inv = drcp(rho);
-  double u = U[1] * inv, v = U[2] * inv, w = U[3] * inv;
-  double ke = dhalf(rho) * ((u * u + v * v) + w * w);
-  double p = K.gm1 * (U[4] - ke);
+  double u = mul_i(U[1], inv), v = mul_i(U[2], inv), w = mul_i(U[3], inv);
+  double ke = dhalf(rho) * ((mul_i(u, u) + v * v) + w * w);
+  double p = mul_i(K.gm1, U[4] - ke);
   if (!(gt0(p) && dfinite(p) && dfinite(U[1]) && dfinite(U[2]) && dfinite(U[3]))) *bad = true;
   p = dmax(p, K.small_pres);
   q[0] = rho; q[1] = u; q[2] = v; q[3] = w; q[4] = p;
@@ -318,24 +322,28 @@ __device__ __forceinline__ double flat_tilde(double pm2, double pm1, double pp1,
                                              double small_pres) {
   double dp1 = pp1 - pm1;
   double dp2 = pp2 - pm2;
-  if (gt0(um1 - up1) && abs_gt(dp1, FLAT_EPS * dmin_nn(pp1, pm1))) {
+  if (gt0(um1 - up1) && abs_gt(dp1, mul_i(FLAT_EPS, dmin_nn(pp1, pm1)))) {
     double z = dabs(dp1) / dmax_nn(dabs(dp2), small_pres);
-    double f = dmax(0.0, dmin(1.0, FLAT_OMEGA2 * (z - FLAT_OMEGA1)));
+    double f = dmax(0.0, dmin(1.0, mul_i(FLAT_OMEGA2, z - FLAT_OMEGA1)));
     return 1.0 - f;
   }
   return 1.0;
 }
 
 // ---------------------------------------------------------------- PPM (CW84 eqs. 1.6-1.10)
-// monotonised centred slope of the middle zone of (am1, a0, ap1)
-__device__ __forceinline__ double mc_slope(double am1, double a0, double ap1) {
-  double dl = a0 - am1, dr = ap1 - a0;
+// monotonised centred slope of the middle zone of (am1, a0, ap1), given its
+// one-sided differences dl = a0 - am1 and dr = ap1 - a0 (a pencil sweep
+// forms each difference once: one zone's dr is the next zone's dl)
+__device__ __forceinline__ double mc_slope_d(double dl, double dr, double am1, double ap1) {
   if (!same_sign_strict(dl, dr)) return 0.0;
   double da = dhalf(ap1 - am1);
   // 2 min(|dl|, |dr|) == min(2|dl|, 2|dr|) exactly (doubling is exact)
   double m2 = dtwice(dmin_nn(dabs(dl), dabs(dr)));
   double lim = dmin_nn(dabs(da), m2);
   return copysign(lim, da);
+}
+__device__ __forceinline__ double mc_slope(double am1, double a0, double ap1) {
+  return mc_slope_d(a0 - am1, ap1 - a0, am1, ap1);
 }
 
 // interface value between zones with averages a0, a1 and slopes s0, s1
@@ -349,16 +357,16 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
   if (!same_sign_strict(aP - ai, ai - aM)) {
     aP = ai; aM = ai;
   } else {
-    double D = aP - aM, M = ai - 0.5 * (aM + aP);
+    double D = aP - aM, M = ai - dhalf(aM + aP);
     double up = M - SIXTH * D, dn = M + SIXTH * D;
-    if (same_sign_strict(D, up)) aM = 3.0 * ai - 2.0 * aP;
-    else if ((gt0(D) && lt0(dn)) || (lt0(D) && gt0(dn))) aP = 3.0 * ai - 2.0 * aM;
+    if (same_sign_strict(D, up)) aM = 3.0 * ai - dtwice(aP);
+    else if ((gt0(D) && lt0(dn)) || (lt0(D) && gt0(dn))) aP = 3.0 * ai - dtwice(aM);
   }
   if (ilt(dbits(chi), dbits(1.0))) {  // chi < 1 (chi is in [0, 1]): blend toward the average
-    aP = chi * aP + (1.0 - chi) * ai;
-    aM = chi * aM + (1.0 - chi) * ai;
+    aP = mul_i(chi, aP) + (1.0 - chi) * ai;
+    aM = mul_i(chi, aM) + (1.0 - chi) * ai;
   }
-  am = aM; ap = aP; a6 = 6.0 * (ai - 0.5 * (aM + aP));
+  am = aM; ap = aP; a6 = mul_i(6.0, ai - dhalf(aM + aP));
 }
 
 // averages of the parabola over the part of the zone swept by a wave of

@@ -58,14 +58,14 @@ __device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __
   bool bad = false;
   cons_to_prim_flag(U, K, q, &inv, &bad);
   if (bad) atomicOr(&flags->bad, 1);
-  double c = dsqrt(K.gamma * q[4] * inv);
+  double c = dsqrt(mul_i(mul_i(K.gamma, q[4]), inv));
   long long id = sg.id(i, j, k);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Q[v * sg.sc + id] = q[v];
   Q[QC * sg.sc + id] = c;
   Q[QRC * sg.sc + id] = ddiv(q[0], c);
   Q[QCR * sg.sc + id] = ddiv(c, q[0]);
-  Q[QIC2 * sg.sc + id] = drcp(c * c);
+  Q[QIC2 * sg.sc + id] = drcp(mul_i(c, c));
 }
 
 // ---- stage 3 of a zone: characteristic tracing from its parabolas
@@ -78,12 +78,12 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
                                            double* __restrict__ TP, long long sc, long long id) {
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
   const double un = zone[1];
-  const double c2 = c * c;
+  const double c2 = mul_i(c, c);
   const double lu = dhalf(rho_c), lp = dhalf(inv_c2);
   const double lam[3] = {un - c, un, un + c};
   double sig[3];
 #pragma unroll
-  for (int w = 0; w < 3; ++w) sig[w] = fabs(lam[w]) * K.dtdx[D];
+  for (int w = 0; w < 3; ++w) sig[w] = mul_i(dabs(lam[w]), K.dtdx[D]);
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     bool reach[3];
@@ -99,16 +99,16 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
     // the reference wave contributes exactly zero (ref - I(sigma_fast) == 0), so
     // only the other acoustic wave and the entropy/shear wave are evaluated
     double bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
-    if (side == 1 && reach[0]) bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
+    if (side == 1 && reach[0]) bm = mul_i(dneg(lu), ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
     if (reach[1]) {
       b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
       bt1 = ref[2] - I(1, 2);
       bt2 = ref[3] - I(1, 3);
     }
-    if (side == 0 && reach[2]) bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
+    if (side == 0 && reach[2]) bp = mul_i(lu, ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
     double s_rho = ref[0] - ((bm + b0) + bp);
-    double s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
-    double s_p = ref[4] - (bm * c2 + bp * c2);
+    double s_un = ref[1] - (mul_i(bm, dneg(c_rho)) + bp * c_rho);
+    double s_p = ref[4] - (mul_i(bm, c2) + bp * c2);
     double s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
     if (K.has_grav) {
       s_un = s_un + K.hdt * K.grav[D];
@@ -155,7 +155,7 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
   // windows relative to the current zone i: a0 = a_i, a1 = a_{i+1}, sl = slope_i,
   // fm = interface i-1/2; pressures pm2 = p_{i-2}, pm1 = p_{i-1}, pp2 = p_{i+2};
   // flattening ctm = chi~_{i-1}, ct0 = chi~_i
-  double a0[5], a1[5], sl[5], fm[5];
+  double a0[5], a1[5], sl[5], fm[5], d01[5];  // d01 = a1 - a0
   double pm2, pm1, pp2, ctm = 1.0, ct0 = 1.0;
   {
     double am2[5], am1[5];
@@ -168,8 +168,10 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double s_m1 = mc_slope(am2[v], am1[v], a0[v]);
-      sl[v] = mc_slope(am1[v], a0[v], a1[v]);
+      const double dm = am1[v] - am2[v], d0 = a0[v] - am1[v];
+      d01[v] = a1[v] - a0[v];
+      double s_m1 = mc_slope_d(dm, d0, am2[v], a0[v]);
+      sl[v] = mc_slope_d(d0, d01[v], am1[v], a1[v]);
       fm[v] = face_value(am1[v], a0[v], s_m1, sl[v]);
     }
     pm2 = am2[4];
@@ -197,7 +199,9 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
     double am[5], ap[5], a6[5], zone[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double s1 = mc_slope(a0[v], a1[v], a2[v]);
+      const double d12 = a2[v] - a1[v];
+      double s1 = mc_slope_d(d01[v], d12, a0[v], a2[v]);
+      d01[v] = d12;
       double fp = face_value(a0[v], a1[v], sl[v], s1);
       ppm_limit(a0[v], fm[v], fp, chi, am[v], ap[v], a6[v]);
       zone[v] = a0[v];
@@ -374,19 +378,20 @@ __device__ __forceinline__ void update_item(BoxGeom in, BoxGeom out, ScratchGeom
       u1[c] = v;
     }
     if (K.has_grav) {
-      double rho_mid = 0.5 * (u0[0] + u1[0]);
+      double rho_mid = dhalf(u0[0] + u1[0]);
+      const double dtr = mul_i(K.dt, rho_mid);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) u1[1 + a] = u1[1 + a] + K.dt * rho_mid * K.grav[a];
+      for (int a = 0; a < 3; ++a) u1[1 + a] = u1[1 + a] + dtr * K.grav[a];
       double e[3];
       if (K.flux_grav) {
         // mass-flux form: gravity's work on the mass crossing the zone's faces
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-          e[d] = (d < K.dim) ? 0.5 * (F[d][id] + F[d][id + st[d]]) * K.grav[d] : 0.0;
+          e[d] = (d < K.dim) ? mul_i(dhalf(F[d][id] + F[d][id + st[d]]), K.grav[d]) : 0.0;
       } else {
-        e[0] = 0.5 * (u0[1] + u1[1]) * K.grav[0];
-        e[1] = 0.5 * (u0[2] + u1[2]) * K.grav[1];
-        e[2] = 0.5 * (u0[3] + u1[3]) * K.grav[2];
+        e[0] = mul_i(dhalf(u0[1] + u1[1]), K.grav[0]);
+        e[1] = dhalf(u0[2] + u1[2]) * K.grav[1];
+        e[2] = dhalf(u0[3] + u1[3]) * K.grav[2];
       }
       u1[4] = u1[4] + K.dt * ((e[0] + e[1]) + e[2]);
     }
@@ -396,7 +401,7 @@ __device__ __forceinline__ void update_item(BoxGeom in, BoxGeom out, ScratchGeom
     bool bad = false;
     cons_to_prim_flag(u1, K, q, &inv, &bad);
     if (bad) atomicOr(&flags->bad, 1);
-    double c = dsqrt(K.gamma * q[4] * inv);
+    double c = dsqrt(mul_i(mul_i(K.gamma, q[4]), inv));
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;
@@ -416,7 +421,7 @@ __device__ __forceinline__ void dt_partial_item(BoxGeom box, StepConst K, Range 
     bool bad = false;
     cons_to_prim_flag(U, K, q, &inv, &bad);
     if (bad) atomicOr(&flags->bad, 1);
-    double c = dsqrt(K.gamma * q[4] * inv);
+    double c = dsqrt(mul_i(mul_i(K.gamma, q[4]), inv));
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (d < K.dim) spd[d] = fabs(q[1 + d]) + c;

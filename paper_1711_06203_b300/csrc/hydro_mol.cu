@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(BLOCK) km_prim(BoxGeom src, BoxGeom pre, Scrat
   const long long id = sg.id(i, j, k);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Q[v * sg.sc + id] = q[v];
-  for (int v = 5; v < nf; ++v) Q[v * sg.sc + id] = B.u[v * B.sc + si] * inv;
+  for (int v = 5; v < nf; ++v) Q[v * sg.sc + id] = mul_i(B.u[v * B.sc + si], inv);
 }
 
 // ---- flattening coefficient of zones [-1, n_d] (interior transverse)
@@ -143,12 +143,16 @@ __global__ void __launch_bounds__(BLOCK) km_recon(ScratchGeom sg, const double* 
   const double* a = Q + (long long)v * sg.sc + base;
   // window a[m-2 .. m+2] for zone m, slopes s[m], s[m+1], interface value m-1/2
   double am2 = a[(z0 - 2) * st], am1 = a[(z0 - 1) * st], a0 = a[z0 * st], ap1 = a[(z0 + 1) * st];
-  double s0 = mc_slope(am1, a0, ap1);
-  const double sm1 = mc_slope(am2, am1, a0);
+  const double dm = am1 - am2, d0 = a0 - am1;
+  double d01 = ap1 - a0;  // one-sided difference a_{m+1} - a_m, carried along the segment
+  double s0 = mc_slope_d(d0, d01, am1, ap1);
+  const double sm1 = mc_slope_d(dm, d0, am2, a0);
   double fm = face_value(am1, a0, sm1, s0);  // interface z0 - 1/2
   for (int m = z0; m < z1; ++m) {
     const double ap2 = a[(m + 2) * st];
-    const double s1 = mc_slope(a0, ap1, ap2);
+    const double d12 = ap2 - ap1;
+    const double s1 = mc_slope_d(d01, d12, a0, ap2);
+    d01 = d12;
     const double fp = face_value(a0, ap1, s0, s1);  // interface m + 1/2
     double lo, hi, a6;
     ppm_limit(a0, fm, fp, CHI[base + m * st], lo, hi, a6);
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(BLOCK) km_flux(ScratchGeom sg, const double* _
   for (int c = 0; c < 5; ++c) F[c * sg.sc + id] = Fh[c];
   for (int v = 5; v < nf; ++v) {
     const double x = left ? EP[v * sg.sc + zl] : EM[v * sg.sc + id];
-    F[v * sg.sc + id] = Fh[0] * x;
+    F[v * sg.sc + id] = mul_i(Fh[0], x);
   }
 }
 
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(BLOCK) km_update(BoxGeom w0, BoxGeom ws, BoxGe
           v = v + K.dt * e;
         }
       }
-      if (second) v = 0.5 * w0.u[c * w0.sc + w0.id(i, j, k)] + 0.5 * v;
+      if (second) v = dhalf(w0.u[c * w0.sc + w0.id(i, j, k)]) + dhalf(v);
       dst.u[c * dst.sc + od] = v;
       if (c < 5) hyd[c] = v;
     }
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(BLOCK) km_update(BoxGeom w0, BoxGeom ws, BoxGe
       bool bad = false;
       cons_to_prim_flag(hyd, K, q, &inv, &bad);
       if (bad) atomicOr(&flags->bad, 1);
-      const double cs = dsqrt(K.gamma * q[4] * inv);
+      const double cs = dsqrt(mul_i(mul_i(K.gamma, q[4]), inv));
 #pragma unroll
       for (int d = 0; d < 3; ++d)
         if (d < K.dim) spd[d] = fabs(q[1 + d]) + cs;
