@@ -204,11 +204,12 @@ __device__ __forceinline__ double add_i(double a, double b) {
 // Reciprocal, quotient and square root.  The contraction-free build keeps the
 // IEEE operations, so it agrees with the oracle bit for bit.  The product
 // build refines the hardware's approximate reciprocal and reciprocal square
-// root by Newton-Raphson steps on the FMA pipe: r' = r + r (1 - x r), twice,
+// root on the FMA pipe: one third-order step r' = r + r (e + e^2), e = 1 - x r,
 // for 1/x; y' = y + y (1 - x y^2)/2 once, then s = x y corrected by
-// s + (x - s^2) y/2 for sqrt(x).  Measured on this GPU they take 4.8 (1/x),
-// 5.3 (a/b) and 6.7 (sqrt) FP64 issue slots against 5.7, 8.6 and 8.6 for the
-// IEEE operations, within a few ulp of them (a GPU test bounds the error).
+// s + (x - s^2) y/2 for sqrt(x).  On the FP64 pipe that is 3 (1/x and a/b,
+// whose final product runs on the integer pipe) and 4 (sqrt) fused
+// multiply-adds, against about 5.7, 8.6 and 8.6 issue slots measured for the
+// IEEE operations; the results stay within 2 ulp (a GPU test bounds the error).
 // Arguments outside [2^-959, 2^960], zero, negative or non-finite take the
 // IEEE path.
 #ifdef HYDRO_IEEE_DIV_SQRT
@@ -223,10 +224,9 @@ __device__ __forceinline__ bool newton_range(double x) {
 __device__ __forceinline__ double rcp_newton(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  // one third-order step: with r = (1 - e)/x, r (1 + e + e^2) = (1 - e^3)/x
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ double drcp(double x) {
   const double ax = __longlong_as_double(dbits(x) & 0x7FFFFFFFFFFFFFFFLL);
