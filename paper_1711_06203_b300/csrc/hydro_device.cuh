@@ -214,8 +214,7 @@ __device__ __forceinline__ double add_i(double a, double b) {
   const bool nan = ne32((xh & 0xFFFFFu) | (unsigned)xm, 0u) || (!ult32(yh, 0x7FF00000u) && sub);
   r = special ? (nan ? 0x7FFFFFFFFFFFFFFFull : x) : r;
   return __longlong_as_double((long long)r);
-}
-// Reciprocal, quotient and square root.  The contraction-free build keeps the
+}// Reciprocal, quotient and square root.  The contraction-free build keeps the
 // IEEE operations, so it agrees with the oracle bit for bit.  The product
 // build refines the hardware's approximate reciprocal and reciprocal square
 // root on the FMA pipe: one third-order step r' = r + r (e + e^2), e = 1 - x r,
@@ -336,7 +335,9 @@ __device__ __forceinline__ double flat_tilde(double pm2, double pm1, double pp1,
                                              double small_pres) {
   double dp1 = pp1 - pm1;
   double dp2 = pp2 - pm2;
-  if (gt0(um1 - up1) && abs_gt(dp1, mul_i(FLAT_EPS, dmin_nn(pp1, pm1)))) {
+  // u_{j-1} - u_{j+1} > 0 as an order comparison (a rounded difference has
+  // the sign of the exact one and vanishes only for equal operands)
+  if (dless(up1, um1) && abs_gt(dp1, mul_i(FLAT_EPS, dmin_nn(pp1, pm1)))) {
     double z = dabs(dp1) / dmax_nn(dabs(dp2), small_pres);
     double f = dmax(0.0, dmin(1.0, mul_i(FLAT_OMEGA2, z - FLAT_OMEGA1)));
     return 1.0 - f;
@@ -366,21 +367,39 @@ __device__ __forceinline__ double face_value(double a0, double a1, double s0, do
 }
 
 // limited, flattened parabola of a zone: average ai, interface values aM, aP
+// The scheme's sign tests on differences -- (aP - ai)(ai - aM) > 0 and the
+// signs of M - D/6 and M + D/6 -- are taken as order comparisons of the
+// operands: a rounded difference has the sign of the exact one and is zero
+// only when the operands are equal, so every decision is the one the
+// differences would give, without forming them on the FP64 pipe.
 __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, double chi, double& am, double& ap,
                                           double& a6) {
-  if (!same_sign_strict(aP - ai, ai - aM)) {
-    aP = ai; aM = ai;
+  const long long ki = okey(ai), kP = okey(aP), kM = okey(aM);
+  double M = 0.0;  // ai - (aM + aP)/2 for the current edges
+  bool m_current = true;
+  if (!((ilt(ki, kP) && ilt(kM, ki)) || (ilt(kP, ki) && ilt(ki, kM)))) {
+    aP = ai; aM = ai;  // a local extremum: flat, and ai - (ai + ai)/2 = +0
   } else {
-    double D = aP - aM, M = ai - dhalf(aM + aP);
-    double up = M - SIXTH * D, dn = M + SIXTH * D;
-    if (same_sign_strict(D, up)) aM = 3.0 * ai - dtwice(aP);
-    else if ((gt0(D) && lt0(dn)) || (lt0(D) && gt0(dn))) aP = 3.0 * ai - dtwice(aM);
+    const double D = aP - aM;
+    M = ai - dhalf(aM + aP);
+    const long long kD = okey(D), km = okey(M), kt = okey(mul_i(SIXTH, D));  // t = D/6
+    // up = M - t, dn = M + t; D != 0 here
+    const bool dpos = ilt(0, kD);
+    if (dpos ? ilt(kt, km) : ilt(km, kt)) {
+      aM = 3.0 * ai - dtwice(aP);
+      m_current = false;
+    } else if (dpos ? ilt(km, -kt) : ilt(-kt, km)) {
+      aP = 3.0 * ai - dtwice(aM);
+      m_current = false;
+    }
   }
   if (ilt(dbits(chi), dbits(1.0))) {  // chi < 1 (chi is in [0, 1]): blend toward the average
     aP = mul_i(chi, aP) + (1.0 - chi) * ai;
     aM = mul_i(chi, aM) + (1.0 - chi) * ai;
+    m_current = false;
   }
-  am = aM; ap = aP; a6 = mul_i(6.0, ai - dhalf(aM + aP));
+  if (!m_current) M = ai - dhalf(aM + aP);
+  am = aM; ap = aP; a6 = mul_i(6.0, M);
 }
 
 // averages of the parabola over the part of the zone swept by a wave of

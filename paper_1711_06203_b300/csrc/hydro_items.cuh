@@ -193,8 +193,8 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
     if (K.flatten) {
       pp3 = qv[4][id + 3 * st];
       ctp = flat_tilde(pm1, a0[4], a2[4], pp3, a0[1], a2[1], sp);
-      double dp1 = a1[4] - pm1;
-      chi = lt0(dp1) ? dmin(ct0, ctp) : dmin(ct0, ctm);
+      // p_{i+1} - p_{i-1} < 0 as an order comparison
+      chi = dless(a1[4], pm1) ? dmin(ct0, ctp) : dmin(ct0, ctm);
     }
     double am[5], ap[5], a6[5], zone[5];
 #pragma unroll
