@@ -382,7 +382,7 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
   } else {
     const double D = aP - aM;
     M = ai - dhalf(aM + aP);
-    const long long kD = okey(D), km = okey(M), kt = okey(mul_i(SIXTH, D));  // t = D/6
+    const long long kD = okey(D), km = okey(M), kt = okey(SIXTH * D);  // t = D/6
     // up = M - t, dn = M + t; D != 0 here
     const bool dpos = ilt(0, kD);
     if (dpos ? ilt(kt, km) : ilt(km, kt)) {
@@ -399,7 +399,7 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
     m_current = false;
   }
   if (!m_current) M = ai - dhalf(aM + aP);
-  am = aM; ap = aP; a6 = mul_i(6.0, M);
+  am = aM; ap = aP; a6 = 6.0 * M;
 }
 
 // averages of the parabola over the part of the zone swept by a wave of

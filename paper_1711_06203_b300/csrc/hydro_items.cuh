@@ -78,12 +78,12 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
                                            double* __restrict__ TP, long long sc, long long id) {
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
   const double un = zone[1];
-  const double c2 = mul_i(c, c);
+  const double c2 = c * c;
   const double lu = dhalf(rho_c), lp = dhalf(inv_c2);
   const double lam[3] = {un - c, un, un + c};
   double sig[3];
 #pragma unroll
-  for (int w = 0; w < 3; ++w) sig[w] = mul_i(dabs(lam[w]), K.dtdx[D]);
+  for (int w = 0; w < 3; ++w) sig[w] = fabs(lam[w]) * K.dtdx[D];
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     bool reach[3];
@@ -99,16 +99,16 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
     // the reference wave contributes exactly zero (ref - I(sigma_fast) == 0), so
     // only the other acoustic wave and the entropy/shear wave are evaluated
     double bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
-    if (side == 1 && reach[0]) bm = mul_i(dneg(lu), ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
+    if (side == 1 && reach[0]) bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
     if (reach[1]) {
       b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
       bt1 = ref[2] - I(1, 2);
       bt2 = ref[3] - I(1, 3);
     }
-    if (side == 0 && reach[2]) bp = mul_i(lu, ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
+    if (side == 0 && reach[2]) bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
     double s_rho = ref[0] - ((bm + b0) + bp);
-    double s_un = ref[1] - (mul_i(bm, dneg(c_rho)) + bp * c_rho);
-    double s_p = ref[4] - (mul_i(bm, c2) + bp * c2);
+    double s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
+    double s_p = ref[4] - (bm * c2 + bp * c2);
     double s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
     if (K.has_grav) {
       s_un = s_un + K.hdt * K.grav[D];
