@@ -426,28 +426,31 @@ void hllc(const real sL[NS], const real sR[NS], int d, double gamma, int einfeld
   if (upwind_left) *upwind_left = left ? 1 : 0;
   const real* s = left ? sL : sR;
   real rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];
-  /* physical flux of the chosen side */
-  real mass = rho * un;
-  real Fk[5];
-  Fk[0] = mass;
-  for (int k = 0; k < 3; ++k) Fk[1 + k] = (k == d) ? mass * un + p : mass * s[1 + k];
-  Fk[4] = un * (E + p);
   if (region == 0 || region == 3) {
-    for (int c = 0; c < 5; ++c) F[c] = Fk[c];
+    /* physical flux of the chosen side */
+    real mass = rho * un;
+    F[0] = mass;
+    for (int k = 0; k < 3; ++k) F[1 + k] = (k == d) ? mass * un + p : mass * s[1 + k];
+    F[4] = un * (E + p);
     return;
   }
   real sk = left ? sl : sr, mk = left ? ml : mr;
-  real Uk[5] = {rho, rho * s[1], rho * s[2], rho * s[3], E};
   /* star state U*_K = f [1, S*, u_t, E/rho + (S* - u)(S* + p/(rho (S_K - u)))],
    * f = rho (S_K - u)/(S_K - S*).  With r = 1/(S_K - S*), f p/(rho(S_K-u)) = p r,
-   * so the energy entry is f E/rho + (S* - u)(f S* + p r): one division fewer. */
+   * so the energy entry is f E/rho + (S* - u)(f S* + p r): one division fewer.
+   * The star flux F_K + S_K (U*_K - U_K) (the Rankine-Hugoniot condition across
+   * the S_K wave) is the physical flux of the star state with the star
+   * pressure p* = p + rho (S_K - u)(S* - u): mass f S*, normal momentum
+   * f S*^2 + p*, transverse momentum (f S*) u_t, energy S* (E* + p*). */
   real r = 1.0 / (sk - sstar);
   real f = mk * r;
-  real Us[5];
-  Us[0] = f;
-  for (int k = 0; k < 3; ++k) Us[1 + k] = (k == d) ? f * sstar : f * s[1 + k];
-  Us[4] = f * (E * s[S_INV]) + (sstar - un) * (f * sstar + p * r);
-  for (int c = 0; c < 5; ++c) F[c] = Fk[c] + sk * (Us[c] - Uk[c]);
+  real du = sstar - un;
+  real mstar = f * sstar;
+  real pstar = p + mk * du;
+  real Estar = f * (E * s[S_INV]) + du * (mstar + p * r);
+  F[0] = mstar;
+  for (int k = 0; k < 3; ++k) F[1 + k] = (k == d) ? mstar * sstar + pstar : mstar * s[1 + k];
+  F[4] = sstar * (Estar + pstar);
 }
 
 /* ---- Step 8 helper: transverse correction of a traced primitive state ----

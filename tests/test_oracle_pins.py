@@ -161,6 +161,36 @@ class TestHLLC:
         Fm = oracle.hllc(mL, mR, 0, self.g)
         assert np.allclose([-Fm[0], Fm[1], -Fm[2], -Fm[3], -Fm[4]], Fx, rtol=1e-13, atol=1e-15)
 
+    def test_star_flux_is_the_rankine_hugoniot_flux_of_the_outer_wave(self):
+        # Toro, Spruce & Speares: in the star regions the HLLC flux is defined
+        # as F_K + S_K (U*_K - U_K), with U*_K = rho_K (S_K - u_K)/(S_K - S*)
+        # [1, S*, v_K, w_K, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))].
+        # Built here from that definition (Davis speeds), for subsonic random
+        # states on both sides of the contact and along every axis.
+        rng = np.random.default_rng(17)
+        g = self.g
+        worst = 0.0
+        for _ in range(400):
+            qL = np.array([rng.lognormal(0, 0.5), *rng.normal(0, 0.3, 3), rng.lognormal(0, 0.5)])
+            qR = np.array([rng.lognormal(0, 0.5), *rng.normal(0, 0.3, 3), rng.lognormal(0, 0.5)])
+            for d in range(3):
+                uL, uR = qL[1 + d], qR[1 + d]
+                cL, cR = np.sqrt(g * qL[4] / qL[0]), np.sqrt(g * qR[4] / qR[0])
+                SL, SR = min(uL - cL, uR - cR), max(uL + cL, uR + cR)
+                Ss = (qR[4] - qL[4] + qL[0] * uL * (SL - uL) - qR[0] * uR * (SR - uR)) / \
+                    (qL[0] * (SL - uL) - qR[0] * (SR - uR))
+                assert SL < 0 < SR
+                q, S = (qL, SL) if Ss >= 0 else (qR, SR)
+                rho, u, p = q[0], q[1 + d], q[4]
+                U = np.array([rho, rho * q[1], rho * q[2], rho * q[3], p / (g - 1) + 0.5 * rho * (q[1:4] ** 2).sum()])
+                fac = rho * (S - u) / (S - Ss)
+                Us = fac * np.array([1.0, *[Ss if k == d else q[1 + k] for k in range(3)],
+                                     U[4] / rho + (Ss - u) * (Ss + p / (rho * (S - u)))])
+                Fref = euler_flux(q, d, g) + S * (Us - U)
+                F = oracle.hllc(qL, qR, d, g)
+                worst = max(worst, np.abs(F - Fref).max() / np.abs(Fref).max())
+        assert worst < 1e-13, worst
+
     def test_weak_waves_match_exact_solver_to_second_order(self):
         # for a jump of size eps the approximate solver errs by O(eps^2)
         errs = []
