@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 # workload (Sedov 128^3 after 20 steps; python -m oracle.count_ops).  Units: grown-box zone (prim),
 # zone-direction (trace), Riemann solve (flux1, flux2, flux3), interior zone
 # (update).
-FLOPS_PER_UNIT = {"prim": 20.0, "trace": 279.9, "flux1": 80.0, "flux2": 140.0, "flux3": 174.0, "update": 58.0}
+FLOPS_PER_UNIT = {"prim": 20.0, "trace": 225.94, "flux1": 60.0, "flux2": 120.0, "flux3": 154.0, "update": 58.0}
 LAUNCHES_PER_STEP_3D = {"prim": 2, "trace": 3, "flux1": 3, "flux2": 6, "flux3": 3, "update": 2}
 # FP64 peak derived from B300's unit counts and clock: 148 SMs x 2 FP64 FMA
 # lanes per SM per clock x 2 flops x 2032 MHz.  (A dependent-free DFMA stream

@@ -442,28 +442,29 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   bool left = region <= 1;
   const double* s = left ? sL : sR;
   double rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];
-  double mass = mul_i(rho, un);
-  double Fk[5];
-  Fk[0] = mass;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) Fk[1 + k] = (k == d) ? mass * un + p : mul_i(mass, s[1 + k]);
-  Fk[4] = mul_i(un, E + p);
   if (region == 0 || region == 3) {
+    // physical flux of the chosen side
+    double mass = mul_i(rho, un);
+    F[0] = mass;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) F[c] = Fk[c];
+    for (int k = 0; k < 3; ++k) F[1 + k] = (k == d) ? mass * un + p : mul_i(mass, s[1 + k]);
+    F[4] = mul_i(un, E + p);
     return left;
   }
+  // star region: F_K + S_K (U*_K - U_K) evaluated as the physical flux of the
+  // star state, with f = rho (S_K - u)/(S_K - S*), p* = p + rho (S_K - u)(S* - u)
+  // and (rho E)* = f E/rho + (S* - u)(f S* + p/(S_K - S*))
   double sk = left ? sl : sr, mk = left ? ml : mr;
-  double Uk[5] = {rho, rho * s[1], rho * s[2], rho * s[3], E};
   double r = drcp(sk - sstar);
   double f = mul_i(mk, r);
-  double Us[5];
-  Us[0] = f;
+  double du = sstar - un;
+  double mstar = mul_i(f, sstar);
+  double pstar = p + mk * du;
+  double Estar = f * mul_i(E, s[S_INV]) + mul_i(du, mstar + p * r);
+  F[0] = mstar;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) Us[1 + k] = (k == d) ? mul_i(f, sstar) : mul_i(f, s[1 + k]);
-  Us[4] = f * mul_i(E, s[S_INV]) + mul_i(sstar - un, f * sstar + mul_i(p, r));
-#pragma unroll
-  for (int c = 0; c < 5; ++c) F[c] = Fk[c] + sk * (Us[c] - Uk[c]);
+  for (int k = 0; k < 3; ++k) F[1 + k] = (k == d) ? mstar * sstar + pstar : mul_i(mstar, s[1 + k]);
+  F[4] = mul_i(sstar, Estar + pstar);
   return left;
 }
 
