@@ -183,16 +183,33 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
       ct0 = flat_tilde(pm2, pm1, a1[4], pp2, am1[1], a1[1], sp);
     }
   }
+  // operands that enter at each zone (a_{i+2} of rho, u_n, u_t1, u_t2; p_{i+3};
+  // the sound-speed fields of zone i) are loaded one zone ahead, so that their
+  // latency overlaps the arithmetic of the zone before
+  double na2[4], np3, nc[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) na2[v] = qv[v][base + 2 * st];
+  np3 = qv[4][base + 3 * st];
+  nc[0] = Q[QC * sc + base]; nc[1] = Q[QRC * sc + base]; nc[2] = Q[QCR * sc + base]; nc[3] = Q[QIC2 * sc + base];
   for (int i = i0; i < i1; ++i) {
     const long long id = base + (long long)(i - i0) * st;
-    double a2[5];
+    double a2[5], cz[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) a2[v] = qv[v][id + 2 * st];
+    for (int v = 0; v < 4; ++v) a2[v] = na2[v];
     a2[4] = pp2;
-    double chi = 1.0, ctp = 1.0, pp3 = 0.0;
+    const double p3 = np3;  // p_{i+3}
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cz[k] = nc[k];
+    if (i + 1 < i1) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) na2[v] = qv[v][id + 3 * st];
+      np3 = qv[4][id + 4 * st];
+      nc[0] = Q[QC * sc + id + st]; nc[1] = Q[QRC * sc + id + st];
+      nc[2] = Q[QCR * sc + id + st]; nc[3] = Q[QIC2 * sc + id + st];
+    }
+    double chi = 1.0, ctp = 1.0;
     if (K.flatten) {
-      pp3 = qv[4][id + 3 * st];
-      ctp = flat_tilde(pm1, a0[4], a2[4], pp3, a0[1], a2[1], sp);
+      ctp = flat_tilde(pm1, a0[4], a2[4], p3, a0[1], a2[1], sp);
       // p_{i+1} - p_{i-1} < 0 as an order comparison
       chi = dless(a1[4], pm1) ? dmin(ct0, ctp) : dmin(ct0, ctm);
     }
@@ -208,8 +225,7 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
       sl[v] = s1;
       fm[v] = fp;
     }
-    trace_zone<D>(am, ap, a6, zone, Q[QC * sc + id], Q[QRC * sc + id], Q[QCR * sc + id], Q[QIC2 * sc + id], K,
-                  TM, TP, sc, id);
+    trace_zone<D>(am, ap, a6, zone, cz[0], cz[1], cz[2], cz[3], K, TM, TP, sc, id);
     // slide the windows one zone
     pm2 = pm1;
     pm1 = a0[4];
@@ -218,8 +234,7 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
       a0[v] = a1[v];
       a1[v] = a2[v];
     }
-    if (K.flatten) pp2 = pp3;
-    else if (i + 1 < i1) pp2 = qv[4][id + 3 * st];
+    pp2 = p3;
     ctm = ct0;
     ct0 = ctp;
   }
