@@ -190,9 +190,12 @@ int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
  * (pinned or pageable) holding grown boxes in the natural layout (stride[0]
  * = nx+8, stride[1] = stride[0]*(ny+8), stride[2] = stride[1]*(nz+8, or 1
  * in 2-D), 5 components).  The call copies the input to context-owned device
- * memory, runs the step and copies the whole grown output box back (its
- * ghost zones are unspecified), all on `stream`, and returns once the host
- * output is complete.  dt_next_host (nullable) receives the CFL step of the
+ * memory (when no face is HYDRO_BC_PREFILLED, only each field's interior
+ * planes along the slowest axis -- derived faces never read ghost zones --
+ * else the whole grown box), runs the step and copies each field's interior
+ * planes of the output back (the ghost planes of the output are not written;
+ * ghost zones inside copied planes are unspecified), all on `stream`, and
+ * returns once the host output is complete.  dt_next_host (nullable) receives the CFL step of the
  * result; a non-physical state returns HYDRO_EBADSTATE.  HYDRO_EINVAL for
  * other layouts or overlapping host buffers. */
 int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,

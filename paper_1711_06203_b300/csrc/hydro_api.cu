@@ -375,10 +375,32 @@ int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_
   din.u = ctx->host_stage;
   dout.u = ctx->host_stage + elems;
   for (int a = 0; a < 3; ++a) dout.dx[a] = in->dx[a];
-  if (cudaMemcpyAsync(din.u, in->u, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HYDRO_ECUDA;
+  // Only the planes the step reads and defines cross the host link: the
+  // input's ghost zones are read only on prefilled faces (derived faces map
+  // their ghosts onto interior zones), and the output's ghost zones are
+  // unspecified.  Each field's interior planes along the slowest axis (z in
+  // 3-D, y in 2-D) are one contiguous range, copied flat (strided copies of
+  // single rows run far below the link's bandwidth).
+  bool prefilled = false;
+  for (int a = 0; a < dim; ++a) prefilled |= in->bc[a][0] == HYDRO_BC_PREFILLED || in->bc[a][1] == HYDRO_BC_PREFILLED;
+  const long long field = gx * gy * gz;
+  const long long plane = (dim == 3) ? gx * gy : gx, nplanes = (dim == 3) ? in->n[2] : in->n[1];
+  auto copy_planes = [&](double* dst, const double* src, cudaMemcpyKind kind) {
+    for (int c = 0; c < 5; ++c) {
+      const long long off = c * field + NG * plane;
+      if (cudaMemcpyAsync(dst + off, src + off, (size_t)(nplanes * plane) * sizeof(double), kind, st) != cudaSuccess)
+        return false;
+    }
+    return true;
+  };
+  if (prefilled) {
+    if (cudaMemcpyAsync(din.u, in->u, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HYDRO_ECUDA;
+  } else if (!copy_planes(din.u, in->u, cudaMemcpyHostToDevice)) {
+    return HYDRO_ECUDA;
+  }
   int rc = hydro_advance_box(ctx, &din, &dout, params, dt, nullptr, st);
   if (rc) return rc;
-  if (cudaMemcpyAsync(out->u, dout.u, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HYDRO_ECUDA;
+  if (!copy_planes(out->u, dout.u, cudaMemcpyDeviceToHost)) return HYDRO_ECUDA;
   DevFlags h;
   rc = read_flags(ctx, st, &h);  // synchronises: the host output is complete on return
   if (rc) return rc;

@@ -300,30 +300,46 @@ def test_reciprocal_quotient_sqrt_error_bounds():
 
 def test_host_buffer_step_matches_device_step():
     """hydro_advance_box_host on pageable and pinned host buffers gives the
-    device path's result bit for bit, and refuses non-natural layouts."""
+    device path's result bit for bit, with derived faces (only the interior
+    crosses the host link), a prefilled face (the whole input box does) and in
+    2-D; it writes none of the output's ghost planes along the slowest axis
+    and refuses non-natural layouts."""
     rng = np.random.default_rng(12)
-    n = (13, 10, 11)
-    U = inputs.random_box(rng, n, 3)
-    bc = ((hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW), (hb.BC_OUTFLOW,) * 2)
-    dx = (0.05,) * 3
-    p = hb.params(3, gamma=5 / 3)
     ctx = hb.Context(0)
-    P = oracle_params(3, n, dx, bc, 5 / 3)
-    d, _ = oracle.dt(U, P)
-    a = to_dev(U)
-    b = torch.empty_like(a)
-    dn_dev = ctx.hydro_advance_box(hb.box(a, n, dx, bc), hb.box(b, n, dx, bc), p, d, want_dt_next=True)
-    want = b.cpu().numpy()
-    for pinned in (False, True):
-        hin = torch.from_numpy(U.copy())
-        hout = torch.full_like(hin, float("nan"))
-        if pinned:
-            hin, hout = hin.pin_memory(), hout.pin_memory()
-        dn = ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, d, want_dt_next=True)
-        assert dn == dn_dev
-        assert np.array_equal(interior(hout.numpy(), 3), interior(want, 3))
+    cases = [
+        (3, (13, 10, 11), ((hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW), (hb.BC_OUTFLOW,) * 2)),
+        (3, (12, 9, 10), ((hb.BC_OUTFLOW,) * 2, (hb.BC_PREFILLED, hb.BC_REFLECT), (hb.BC_PERIODIC,) * 2)),
+        (2, (14, 11, 1), ((hb.BC_OUTFLOW, hb.BC_REFLECT), (hb.BC_PERIODIC,) * 2, (hb.BC_OUTFLOW,) * 2)),
+    ]
+    for dim, n, bc in cases:
+        U = inputs.random_box(rng, n, dim)
+        dx = (0.05,) * 3
+        p = hb.params(dim, gamma=5 / 3)
+        P = oracle_params(dim, n[:dim], dx, bc, 5 / 3)
+        d, _ = oracle.dt(U, P)
+        a = to_dev(U)
+        b = torch.empty_like(a)
+        dn_dev = ctx.hydro_advance_box(hb.box(a, n, dx, bc), hb.box(b, n, dx, bc), p, d, want_dt_next=True)
+        want = b.cpu().numpy()
+        for pinned in (False, True):
+            hin = torch.from_numpy(U.copy())
+            hout = torch.full_like(hin, float("nan"))
+            if pinned:
+                hin, hout = hin.pin_memory(), hout.pin_memory()
+            dn = ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, d, want_dt_next=True)
+            assert dn == dn_dev
+            got = hout.numpy()
+            assert np.array_equal(interior(got, dim), interior(want, dim))
+            # the ghost planes along the slowest axis are not written
+            if dim == 3:
+                assert np.isnan(got[:, :4]).all() and np.isnan(got[:, -4:]).all()
+            else:
+                assert np.isnan(got[:, :, :4]).all() and np.isnan(got[:, :, -4:]).all()
+    n, dx, bc = cases[0][1], (0.05,) * 3, cases[0][2]
+    p = hb.params(3, gamma=5 / 3)
+    hout = torch.empty((5,) + inputs.grown_shape(n, 3), dtype=torch.float64)
     big = torch.zeros((5, 20, 19, 22), dtype=torch.float64)  # padded rows: not the natural layout
     with pytest.raises(hb.HydroError) as e:
-        ctx.hydro_advance_box_host(hb.box(big[:, :, :18, :21], n, dx, bc), hb.box(hout, n, dx, bc), p, d)
+        ctx.hydro_advance_box_host(hb.box(big[:, :, :18, :21], n, dx, bc), hb.box(hout, n, dx, bc), p, 1e-3)
     assert e.value.status == hb.HYDRO_EINVAL
     ctx.close()
