@@ -194,8 +194,11 @@ int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
  * planes along the slowest axis -- derived faces never read ghost zones --
  * else the whole grown box), runs the step and copies each field's interior
  * planes of the output back (the ghost planes of the output are not written;
- * ghost zones inside copied planes are unspecified), all on `stream`, and
- * returns once the host output is complete.  dt_next_host (nullable) receives the CFL step of the
+ * ghost zones inside copied planes are unspecified), and returns once the
+ * host output is complete.  In 3-D with no prefilled face the copies run on
+ * two context-owned copy streams in z-chunks that overlap the kernels on
+ * `stream` (fully so with pinned host buffers); otherwise everything runs on
+ * `stream`.  dt_next_host (nullable) receives the CFL step of the
  * result; a non-physical state returns HYDRO_EBADSTATE.  HYDRO_EINVAL for
  * other layouts or overlapping host buffers. */
 int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,

@@ -2,6 +2,7 @@
 // management and the box-level entry points declared in include/hydro.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -205,6 +206,32 @@ __global__ void k_selftest_intpipe(const double* __restrict__ x, const double* _
   prod[i] = mul_i(x[i], y[i]);
   sum[i] = add_i(x[i], y[i]);
 }
+// z-chunks of the overlapped host-buffer step
+constexpr int PIPE_CHUNKS = 4;
+
+// copy streams, events and sweep cursors of the overlapped host-buffer step
+int ensure_pipe(hydro_ctx* ctx) {
+  if (ctx->pipe_cursors) return HYDRO_OK;
+  bool ok = cudaStreamCreateWithFlags(&ctx->pipe_h2d, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&ctx->pipe_d2h, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& e : ctx->pipe_events) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->pipe_cursors, (2 * PIPE_MAX_CHUNKS + 5) * sizeof(unsigned long long)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (ctx->pipe_h2d) cudaStreamDestroy(ctx->pipe_h2d);
+    if (ctx->pipe_d2h) cudaStreamDestroy(ctx->pipe_d2h);
+    for (auto& e : ctx->pipe_events) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    if (ctx->pipe_cursors) cudaFree(ctx->pipe_cursors);
+    ctx->pipe_h2d = ctx->pipe_d2h = nullptr;
+    ctx->pipe_cursors = nullptr;
+    return HYDRO_ENOMEM;
+  }
+  return HYDRO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -260,6 +287,11 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
   hydro_level_release(ctx);
   hydro_amr_release(ctx);
   if (ctx->host_stage) cudaFree(ctx->host_stage);
+  if (ctx->pipe_h2d) cudaStreamDestroy(ctx->pipe_h2d);
+  if (ctx->pipe_d2h) cudaStreamDestroy(ctx->pipe_d2h);
+  for (auto& e : ctx->pipe_events)
+    if (e) cudaEventDestroy(e);
+  if (ctx->pipe_cursors) cudaFree(ctx->pipe_cursors);
   delete ctx;
 }
 
@@ -393,14 +425,49 @@ int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_
     }
     return true;
   };
-  if (prefilled) {
-    if (cudaMemcpyAsync(din.u, in->u, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HYDRO_ECUDA;
-  } else if (!copy_planes(din.u, in->u, cudaMemcpyHostToDevice)) {
-    return HYDRO_ECUDA;
+  int rc;
+  if (dim == 3 && !prefilled && !ctx->profiling) {
+    // 3-D with derived faces: copies overlap the kernels (launch_step_host_piped)
+    rc = ensure_pipe(ctx);
+    if (rc) return rc;
+    StepArgs a;
+    a.in = geom_of(&din, dim);
+    a.out = geom_of(&dout, dim);
+    a.sg = scratch_geom(in->n, dim);
+    rc = ensure_scratch(ctx, (size_t)a.sg.sc * SCRATCH_FIELDS * sizeof(double));
+    if (rc) return rc;
+    a.s = carve_scratch(ctx->scratch, a.sg.sc);
+    a.K = step_const(params, in->dx, dt);
+    for (int d = 0; d < 3; ++d) a.dx[d] = in->dx[d];
+    a.cfl = params->cfl;
+    a.flags = ctx->flags;
+    a.events = nullptr;
+    HostPipe hp;
+    hp.h_in = in->u;
+    hp.h_out = out->u;
+    hp.field = field;
+    hp.plane = plane;
+    hp.nchunk = (int)std::min<long long>(PIPE_CHUNKS, in->n[2]);
+    hp.h2d = ctx->pipe_h2d;
+    hp.d2h = ctx->pipe_d2h;
+    hp.start = ctx->pipe_events[0];
+    hp.d2h_done = ctx->pipe_events[1];
+    for (int k = 0; k < PIPE_MAX_CHUNKS; ++k) {
+      hp.h2d_done[k] = ctx->pipe_events[2 + k];
+      hp.upd_done[k] = ctx->pipe_events[2 + PIPE_MAX_CHUNKS + k];
+    }
+    hp.cursors = ctx->pipe_cursors;
+    if (launch_step_host_piped(a, hp, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+  } else {
+    if (prefilled) {
+      if (cudaMemcpyAsync(din.u, in->u, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HYDRO_ECUDA;
+    } else if (!copy_planes(din.u, in->u, cudaMemcpyHostToDevice)) {
+      return HYDRO_ECUDA;
+    }
+    rc = hydro_advance_box(ctx, &din, &dout, params, dt, nullptr, st);
+    if (rc) return rc;
+    if (!copy_planes(out->u, dout.u, cudaMemcpyDeviceToHost)) return HYDRO_ECUDA;
   }
-  int rc = hydro_advance_box(ctx, &din, &dout, params, dt, nullptr, st);
-  if (rc) return rc;
-  if (!copy_planes(out->u, dout.u, cudaMemcpyDeviceToHost)) return HYDRO_ECUDA;
   DevFlags h;
   rc = read_flags(ctx, st, &h);  // synchronises: the host output is complete on return
   if (rc) return rc;

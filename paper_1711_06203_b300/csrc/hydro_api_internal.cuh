@@ -25,6 +25,10 @@ struct hydro_ctx {
   long long stage_calls = 0;
   double* host_stage = nullptr;   // device in/out boxes of hydro_advance_box_host (grown on demand)
   size_t host_stage_bytes = 0;
+  // copy streams, events and sweep cursors of the overlapped host-buffer step (made on first use)
+  cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+  cudaEvent_t pipe_events[2 * hydro::PIPE_MAX_CHUNKS + 2] = {};
+  unsigned long long* pipe_cursors = nullptr;
 };
 
 void hydro_batch_release(hydro_ctx* ctx);

@@ -81,7 +81,29 @@ __global__ void k_reset_step(DevFlags* flags) {
   }
 }
 
+__global__ void k_zero_cursors(unsigned long long* c, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) c[i] = 0ull;
+}
+
 inline unsigned blocks_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
+
+// tracing sweep along d over pencils whose transverse coordinates are
+// [-1, n] on the first transverse axis and [lo2, lo2 + ext2) on the second
+void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long long* cur, cudaStream_t st) {
+  const int* n = a.in.n;
+  const int t1 = (d == 0) ? 1 : 0;
+  SweepRange sw;
+  sw.lo1 = -1; sw.ext1 = n[t1] + 2;
+  sw.lo2 = lo2; sw.ext2 = ext2;
+  sw.nd = n[d];
+  sw.seg = TRACE_SEG;
+  sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
+  const unsigned need = blocks_for(sw.count());
+  const Scratch& s = a.s;
+  if (d == 0) k_trace<0><<<std::min<unsigned>(need, trace_resident_blocks<0>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[0], s.TP[0], a.K, sw, cur);
+  if (d == 1) k_trace<1><<<std::min<unsigned>(need, trace_resident_blocks<1>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[1], s.TP[1], a.K, sw, cur);
+  if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
+}
 
 }  // namespace
 
@@ -186,6 +208,129 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
   k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], dim, a.cfl);
   nl += 2;
   mark(NSTAGES);
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t st, long long* launches) {
+  const int* n = a.in.n;
+  const ScratchGeom& sg = a.sg;
+  const Scratch& s = a.s;
+  const int C = p.nchunk;
+  long long nl = 0;
+  auto zc = [&](int k) { return (int)((long long)n[2] * k / C); };  // first interior plane of chunk k
+  const size_t plane_bytes = (size_t)p.plane * sizeof(double);
+  // input planes, chunk by chunk, after the work already queued on the
+  // compute stream (which may still read the staging box)
+  if (cudaEventRecord(p.start, st) != cudaSuccess) return cudaGetLastError();
+  if (cudaStreamWaitEvent(p.h2d, p.start, 0) != cudaSuccess) return cudaGetLastError();
+  for (int k = 0; k < C; ++k) {
+    const long long off = (long long)(zc(k) + NG) * p.plane;
+    const size_t len = (size_t)(zc(k + 1) - zc(k)) * plane_bytes;
+    for (int c = 0; c < 5; ++c)
+      if (cudaMemcpyAsync(a.in.u + c * p.field + off, p.h_in + c * p.field + off, len, cudaMemcpyHostToDevice,
+                          p.h2d) != cudaSuccess)
+        return cudaGetLastError();
+    if (cudaEventRecord(p.h2d_done[k], p.h2d) != cudaSuccess) return cudaGetLastError();
+  }
+  k_reset_step<<<1, 32, 0, st>>>(a.flags);
+  k_zero_cursors<<<1, 64, 0, st>>>(p.cursors, 2 * PIPE_MAX_CHUNKS + 5);
+  nl += 2;
+  auto prim = [&](int zlo, int zext) {
+    Range r;
+    r.lo[0] = -NG; r.ext[0] = n[0] + 2 * NG;
+    r.lo[1] = -NG; r.ext[1] = n[1] + 2 * NG;
+    r.lo[2] = zlo; r.ext[2] = zext;
+    k_prim<<<blocks_for(r.count()), BLOCK, 0, st>>>(a.in, sg, s.Q, a.K, r, a.flags);
+    nl += 1;
+  };
+  // each landed chunk: primitive state and the x and y sweeps of its planes
+  for (int k = 0; k < C; ++k) {
+    if (cudaStreamWaitEvent(st, p.h2d_done[k], 0) != cudaSuccess) return cudaGetLastError();
+    const int z0 = zc(k), ze = zc(k + 1) - zc(k);
+    prim(z0, ze);
+    launch_trace(0, a, z0, ze, p.cursors + 2 * k, st);
+    launch_trace(1, a, z0, ze, p.cursors + 2 * k + 1, st);
+    nl += 2;
+  }
+  // ghost planes (mapped onto interior planes by the boundary kinds), the x
+  // and y sweeps of planes -1 and n, and the z sweep
+  prim(-NG, NG);
+  prim(n[2], NG);
+  unsigned long long* cg = p.cursors + 2 * PIPE_MAX_CHUNKS;
+  launch_trace(0, a, -1, 1, cg, st);
+  launch_trace(1, a, -1, 1, cg + 1, st);
+  launch_trace(0, a, n[2], 1, cg + 2, st);
+  launch_trace(1, a, n[2], 1, cg + 3, st);
+  launch_trace(2, a, -1, n[1] + 2, cg + 4, st);
+  nl += 5;
+  // first fluxes on d-faces [0, n_d] x transverse [-1, n]
+  for (int d = 0; d < 3; ++d) {
+    Range r;
+    for (int ax = 0; ax < 3; ++ax) { r.lo[ax] = -1; r.ext[ax] = n[ax] + 2; }
+    r.lo[d] = 0;
+    r.ext[d] = n[d] + 1;
+    unsigned b = blocks_for(r.count());
+    if (d == 0) k_flux1<0><<<b, BLOCK, 0, st>>>(sg, s.TP[0], s.TM[0], s.F1[0], a.K, r);
+    if (d == 1) k_flux1<1><<<b, BLOCK, 0, st>>>(sg, s.TP[1], s.TM[1], s.F1[1], a.K, r);
+    if (d == 2) k_flux1<2><<<b, BLOCK, 0, st>>>(sg, s.TP[2], s.TM[2], s.F1[2], a.K, r);
+    nl += 1;
+  }
+  // intermediate fluxes F^{d|t}
+  for (int d = 0; d < 3; ++d)
+    for (int t = 0; t < 3; ++t) {
+      if (t == d) continue;
+      int o = 3 - d - t;
+      Range r;
+      r.lo[d] = 0; r.ext[d] = n[d] + 1;
+      r.lo[t] = 0; r.ext[t] = n[t];
+      r.lo[o] = -1; r.ext[o] = n[o] + 2;
+      unsigned b = blocks_for(r.count());
+      const double* f1 = s.F1[t];
+      double* f2 = s.F2[d][t];
+#define F2CASE(DD, TT) \
+  if (d == DD && t == TT) k_flux2<DD, TT><<<b, BLOCK, 0, st>>>(sg, s.TP[DD], s.TM[DD], f1, f2, a.K, r);
+      F2CASE(0, 1) F2CASE(0, 2) F2CASE(1, 0) F2CASE(1, 2) F2CASE(2, 0) F2CASE(2, 1)
+#undef F2CASE
+      nl += 1;
+    }
+  // final fluxes and update chunk by chunk; each chunk's output planes go
+  // back while the next chunk computes.  A chunk computes z-faces
+  // [z0, z0 + ze], so the face it shares with the next chunk is formed by
+  // both, with the same value.  (Chunking the intermediate fluxes as well was
+  // measured: their duplicated planes and extra launches cost about what the
+  // longer overlap saves.)
+  for (int k = 0; k < C; ++k) {
+    const int z0 = zc(k), ze = zc(k + 1) - zc(k);
+    for (int d = 0; d < 3; ++d) {
+      Range r;
+      for (int ax = 0; ax < 2; ++ax) { r.lo[ax] = 0; r.ext[ax] = n[ax]; }
+      r.lo[2] = z0; r.ext[2] = ze;
+      r.ext[d] += 1;
+      unsigned b = blocks_for(r.count());
+      if (d == 0) k_flux3<0><<<b, BLOCK, 0, st>>>(sg, s.TP[0], s.TM[0], s.F2[1][2], s.F2[2][1], s.F3[0], a.K, r);
+      if (d == 1) k_flux3<1><<<b, BLOCK, 0, st>>>(sg, s.TP[1], s.TM[1], s.F2[0][2], s.F2[2][0], s.F3[1], a.K, r);
+      if (d == 2) k_flux3<2><<<b, BLOCK, 0, st>>>(sg, s.TP[2], s.TM[2], s.F2[0][1], s.F2[1][0], s.F3[2], a.K, r);
+      nl += 1;
+    }
+    Range ru;
+    ru.lo[0] = 0; ru.ext[0] = n[0];
+    ru.lo[1] = 0; ru.ext[1] = n[1];
+    ru.lo[2] = z0; ru.ext[2] = ze;
+    k_update<<<blocks_for(ru.count()), BLOCK, 0, st>>>(a.in, a.out, sg, s.F3[0], s.F3[1], s.F3[2], a.K, ru, a.flags);
+    nl += 1;
+    if (cudaEventRecord(p.upd_done[k], st) != cudaSuccess) return cudaGetLastError();
+    if (cudaStreamWaitEvent(p.d2h, p.upd_done[k], 0) != cudaSuccess) return cudaGetLastError();
+    const long long off = (long long)(z0 + NG) * p.plane;
+    for (int c = 0; c < 5; ++c)
+      if (cudaMemcpyAsync(p.h_out + c * p.field + off, a.out.u + c * p.field + off, (size_t)ze * plane_bytes,
+                          cudaMemcpyDeviceToHost, p.d2h) != cudaSuccess)
+        return cudaGetLastError();
+  }
+  k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], 3, a.cfl);
+  nl += 1;
+  if (cudaEventRecord(p.d2h_done, p.d2h) != cudaSuccess) return cudaGetLastError();
+  if (cudaStreamWaitEvent(st, p.d2h_done, 0) != cudaSuccess) return cudaGetLastError();
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

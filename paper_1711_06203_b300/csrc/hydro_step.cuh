@@ -99,6 +99,27 @@ struct StepArgs {
 // enqueue one step (all kernels) on `stream`; adds the number of kernels
 // launched to *launches
 cudaError_t launch_step(const StepArgs& a, cudaStream_t stream, long long* launches);
+
+// A 3-D step whose input arrives from, and whose output returns to, host
+// memory, with the copies overlapping the kernels: the interior z-planes
+// arrive in chunks on one copy stream, each chunk's primitive state and x/y
+// tracing sweeps start as soon as it has landed, and the final fluxes and the
+// update run chunk by chunk, each chunk's planes going back on a second copy
+// stream while the next chunk computes.  Every face has a derived boundary
+// (ghost zones come from interior zones).  Same kernels and per-zone
+// arithmetic as launch_step, so the result is bitwise the same.
+constexpr int PIPE_MAX_CHUNKS = 8;
+struct HostPipe {
+  const double* h_in;            // host grown boxes in the natural layout
+  double* h_out;
+  long long field, plane;        // elements per field and per z-plane of the grown box
+  int nchunk;                    // z-chunks of the interior, 1..PIPE_MAX_CHUNKS
+  cudaStream_t h2d, d2h;         // copy streams
+  cudaEvent_t start, d2h_done;
+  cudaEvent_t h2d_done[PIPE_MAX_CHUNKS], upd_done[PIPE_MAX_CHUNKS];
+  unsigned long long* cursors;   // 2 * PIPE_MAX_CHUNKS + 5 device work cursors of the tracing sweeps
+};
+cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t stream, long long* launches);
 // enqueue a CFL estimate of the interior of a box into flags->dt_next
 cudaError_t launch_dt(const BoxGeom& box, const StepConst& K, const double dx[3], double cfl, DevFlags* flags,
                       cudaStream_t stream, long long* launches);

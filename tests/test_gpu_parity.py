@@ -300,16 +300,20 @@ def test_reciprocal_quotient_sqrt_error_bounds():
 
 def test_host_buffer_step_matches_device_step():
     """hydro_advance_box_host on pageable and pinned host buffers gives the
-    device path's result bit for bit, with derived faces (only the interior
-    crosses the host link), a prefilled face (the whole input box does) and in
-    2-D; it writes none of the output's ghost planes along the slowest axis
-    and refuses non-natural layouts."""
+    device path's result bit for bit: 3-D boxes with derived faces (interior
+    planes only cross the host link, in z-chunks that overlap the kernels;
+    4 to 44 planes), a prefilled face (the whole input box crosses) and 2-D.
+    It writes none of the output's ghost planes along the slowest axis and
+    refuses non-natural layouts."""
     rng = np.random.default_rng(12)
     ctx = hb.Context(0)
     cases = [
         (3, (13, 10, 11), ((hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW), (hb.BC_OUTFLOW,) * 2)),
         (3, (12, 9, 10), ((hb.BC_OUTFLOW,) * 2, (hb.BC_PREFILLED, hb.BC_REFLECT), (hb.BC_PERIODIC,) * 2)),
         (2, (14, 11, 1), ((hb.BC_OUTFLOW, hb.BC_REFLECT), (hb.BC_PERIODIC,) * 2, (hb.BC_OUTFLOW,) * 2)),
+        # one interior plane per chunk of the overlapped path, and a box of several planes per chunk
+        (3, (10, 9, 4), ((hb.BC_REFLECT, hb.BC_OUTFLOW), (hb.BC_OUTFLOW,) * 2, (hb.BC_OUTFLOW,) * 2)),
+        (3, (40, 36, 44), ((hb.BC_OUTFLOW,) * 2, (hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW))),
     ]
     for dim, n, bc in cases:
         U = inputs.random_box(rng, n, dim)
