@@ -372,15 +372,19 @@ __device__ __forceinline__ double face_value(double a0, double a1, double s0, do
 // operands: a rounded difference has the sign of the exact one and is zero
 // only when the operands are equal, so every decision is the one the
 // differences would give, without forming them on the FP64 pipe.
+// (dap, optional, receives ap - am, formed once here: the limiter's D when the
+// edges were left unchanged)
 __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, double chi, double& am, double& ap,
-                                          double& a6) {
+                                          double& a6, double* dap = nullptr) {
   const long long ki = okey(ai), kP = okey(aP), kM = okey(aM);
   double M = 0.0;  // ai - (aM + aP)/2 for the current edges
+  double dd = 0.0;  // aP - aM for the current edges
   bool m_current = true;
   if (!((ilt(ki, kP) && ilt(kM, ki)) || (ilt(kP, ki) && ilt(ki, kM)))) {
     aP = ai; aM = ai;  // a local extremum: flat, and ai - (ai + ai)/2 = +0
   } else {
     const double D = aP - aM;
+    dd = D;
     M = ai - dhalf(aM + aP);
     const long long kD = okey(D), km = okey(M), kt = okey(SIXTH * D);  // t = D/6
     // up = M - t, dn = M + t; D != 0 here
@@ -398,17 +402,22 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
     aM = mul_i(chi, aM) + (1.0 - chi) * ai;
     m_current = false;
   }
-  if (!m_current) M = ai - dhalf(aM + aP);
+  if (!m_current) {
+    M = ai - dhalf(aM + aP);
+    dd = aP - aM;
+  }
+  if (dap) *dap = dd;
   am = aM; ap = aP; a6 = 6.0 * M;
 }
 
 // averages of the parabola over the part of the zone swept by a wave of
 // Courant number s toward the high (I+) / low (I-) face
-__device__ __forceinline__ double integ_plus(double am, double ap, double a6, double s) {
-  return ap - dhalf(s) * ((ap - am) - (1.0 - TWOTHIRDS * s) * a6);
+// dap = ap - am
+__device__ __forceinline__ double integ_plus(double am, double ap, double dap, double a6, double s) {
+  return ap - dhalf(s) * (dap - (1.0 - TWOTHIRDS * s) * a6);
 }
-__device__ __forceinline__ double integ_minus(double am, double ap, double a6, double s) {
-  return am + dhalf(s) * ((ap - am) + (1.0 - TWOTHIRDS * s) * a6);
+__device__ __forceinline__ double integ_minus(double am, double ap, double dap, double a6, double s) {
+  return am + dhalf(s) * (dap + (1.0 - TWOTHIRDS * s) * a6);
 }
 
 // ---------------------------------------------------------------- HLLC (Toro-Spruce-Speares)

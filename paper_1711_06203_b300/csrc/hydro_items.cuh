@@ -69,11 +69,11 @@ __device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __
 }
 
 // ---- stage 3 of a zone: characteristic tracing from its parabolas
-// am/ap/a6/zone: (rho, un, ut1, ut2, p); outputs the zone's low- and high-face
+// am/ap/dap (= ap - am)/a6/zone: (rho, un, ut1, ut2, p); outputs the zone's low- and high-face
 // states to TM/TP at id in absolute component order.
 template <int D>
-__device__ __forceinline__ void trace_zone(const double am[5], const double ap[5], const double a6[5],
-                                           const double zone[5], double c, double rho_c, double c_rho,
+__device__ __forceinline__ void trace_zone(const double am[5], const double ap[5], const double dap[5],
+                                           const double a6[5], const double zone[5], double c, double rho_c, double c_rho,
                                            double inv_c2, const StepConst& K, double* __restrict__ TM,
                                            double* __restrict__ TP, long long sc, long long id) {
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
@@ -91,7 +91,7 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
     for (int w = 0; w < 3; ++w) reach[w] = side ? gt0(lam[w]) : lt0(lam[w]);
     const int fast = side ? 2 : 0;
     auto I = [&](int w, int v) {
-      return side ? integ_plus(am[v], ap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], a6[v], sig[w]);
+      return side ? integ_plus(am[v], ap[v], dap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], dap[v], a6[v], sig[w]);
     };
     double ref[5];
 #pragma unroll
@@ -213,19 +213,19 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
       // p_{i+1} - p_{i-1} < 0 as an order comparison
       chi = dless(a1[4], pm1) ? dmin(ct0, ctp) : dmin(ct0, ctm);
     }
-    double am[5], ap[5], a6[5], zone[5];
+    double am[5], ap[5], dap[5], a6[5], zone[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double d12 = a2[v] - a1[v];
       double s1 = mc_slope_d(d01[v], d12, a0[v], a2[v]);
       d01[v] = d12;
       double fp = face_value(a0[v], a1[v], sl[v], s1);
-      ppm_limit(a0[v], fm[v], fp, chi, am[v], ap[v], a6[v]);
+      ppm_limit(a0[v], fm[v], fp, chi, am[v], ap[v], a6[v], &dap[v]);
       zone[v] = a0[v];
       sl[v] = s1;
       fm[v] = fp;
     }
-    trace_zone<D>(am, ap, a6, zone, cz[0], cz[1], cz[2], cz[3], K, TM, TP, sc, id);
+    trace_zone<D>(am, ap, dap, a6, zone, cz[0], cz[1], cz[2], cz[3], K, TM, TP, sc, id);
     // slide the windows one zone
     pm2 = pm1;
     pm1 = a0[4];
