@@ -783,9 +783,9 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    # outflow faces derive their ghost zones, so only each field's interior
-    # z-planes cross the host link, in both directions
-    nbytes = 5 * n * (n + 8) ** 2 * a.element_size()
+    # outflow faces derive their ghost zones, so only the interior rows of
+    # each field's interior z-planes cross the host link, in both directions
+    nbytes = 5 * n * n * (n + 8) * a.element_size()
 
     # roofline of the dominant stage (FP64 ALU bound: every stage is)
     units = units_per_step(n)

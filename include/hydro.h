@@ -190,17 +190,20 @@ int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
  * (pinned or pageable) holding grown boxes in the natural layout (stride[0]
  * = nx+8, stride[1] = stride[0]*(ny+8), stride[2] = stride[1]*(nz+8, or 1
  * in 2-D), 5 components).  The call copies the input to context-owned device
- * memory (when no face is HYDRO_BC_PREFILLED, only each field's interior
- * planes along the slowest axis -- derived faces never read ghost zones --
- * else the whole grown box), runs the step and copies each field's interior
- * planes of the output back (the ghost planes of the output are not written;
- * ghost zones inside copied planes are unspecified), and returns once the
- * host output is complete.  In 3-D with no prefilled face the copies run on
- * two context-owned copy streams in z-chunks that overlap the kernels on
- * `stream` (fully so with pinned host buffers); otherwise everything runs on
- * `stream`.  dt_next_host (nullable) receives the CFL step of the
- * result; a non-physical state returns HYDRO_EBADSTATE.  HYDRO_EINVAL for
- * other layouts or overlapping host buffers. */
+ * memory, runs the step, copies the result back and returns once the host
+ * output is complete.  Only what the step reads and defines crosses the host
+ * link: with a HYDRO_BC_PREFILLED face the whole input box goes over (its
+ * ghost layers are data); otherwise only interior zones are read (derived
+ * faces map their ghosts onto the interior), so each field's interior planes
+ * along the slowest axis -- in 3-D only their interior rows -- go over.  The
+ * output comes back the same way; the host output's ghost zones outside the
+ * copied rows and planes are not written, and those inside are unspecified.
+ * In 3-D with no prefilled face the copies run on two context-owned copy
+ * streams in z-chunks that overlap the kernels on `stream` (fully so with
+ * pinned host buffers); otherwise everything runs on `stream`.
+ * dt_next_host (nullable) receives the CFL step of the result; a
+ * non-physical state returns HYDRO_EBADSTATE.  HYDRO_EINVAL for other
+ * layouts or overlapping host buffers. */
 int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out,
                            const hydro_params_t* params, double dt, double* dt_next_host, void* stream);
 

@@ -224,12 +224,15 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
   // compute stream (which may still read the staging box)
   if (cudaEventRecord(p.start, st) != cudaSuccess) return cudaGetLastError();
   if (cudaStreamWaitEvent(p.h2d, p.start, 0) != cudaSuccess) return cudaGetLastError();
+  // of each plane, the interior rows: one contiguous run of n_y rows
+  const long long row = p.plane / (n[1] + 2 * NG), rows_off = NG * row;
+  const size_t rows_bytes = (size_t)(n[1] * row) * sizeof(double);
   for (int k = 0; k < C; ++k) {
-    const long long off = (long long)(zc(k) + NG) * p.plane;
-    const size_t len = (size_t)(zc(k + 1) - zc(k)) * plane_bytes;
+    const long long off = (long long)(zc(k) + NG) * p.plane + rows_off;
+    const size_t planes = (size_t)(zc(k + 1) - zc(k));
     for (int c = 0; c < 5; ++c)
-      if (cudaMemcpyAsync(a.in.u + c * p.field + off, p.h_in + c * p.field + off, len, cudaMemcpyHostToDevice,
-                          p.h2d) != cudaSuccess)
+      if (cudaMemcpy2DAsync(a.in.u + c * p.field + off, plane_bytes, p.h_in + c * p.field + off, plane_bytes,
+                            rows_bytes, planes, cudaMemcpyHostToDevice, p.h2d) != cudaSuccess)
         return cudaGetLastError();
     if (cudaEventRecord(p.h2d_done[k], p.h2d) != cudaSuccess) return cudaGetLastError();
   }
@@ -321,10 +324,10 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     nl += 1;
     if (cudaEventRecord(p.upd_done[k], st) != cudaSuccess) return cudaGetLastError();
     if (cudaStreamWaitEvent(p.d2h, p.upd_done[k], 0) != cudaSuccess) return cudaGetLastError();
-    const long long off = (long long)(z0 + NG) * p.plane;
+    const long long off = (long long)(z0 + NG) * p.plane + rows_off;
     for (int c = 0; c < 5; ++c)
-      if (cudaMemcpyAsync(p.h_out + c * p.field + off, a.out.u + c * p.field + off, (size_t)ze * plane_bytes,
-                          cudaMemcpyDeviceToHost, p.d2h) != cudaSuccess)
+      if (cudaMemcpy2DAsync(p.h_out + c * p.field + off, plane_bytes, a.out.u + c * p.field + off, plane_bytes,
+                            rows_bytes, (size_t)ze, cudaMemcpyDeviceToHost, p.d2h) != cudaSuccess)
         return cudaGetLastError();
   }
   k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], 3, a.cfl);
