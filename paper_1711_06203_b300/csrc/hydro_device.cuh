@@ -277,6 +277,11 @@ __device__ __forceinline__ bool ine(long long a, long long b) {
   asm("{\n\t.reg .pred p;\n\tsetp.ne.s64 p, %1, %2;\n\tselp.s32 %0, 1, 0, p;\n\t}" : "=r"(r) : "l"(a), "l"(b));
   return r != 0;
 }
+// x + (+0.0) as an integer select: x itself, except that -0 becomes +0
+__device__ __forceinline__ double pz(double x) {
+  const long long b = dbits(x);
+  return __longlong_as_double(ine(b, (long long)0x8000000000000000ULL) ? b : 0LL);
+}
 // a and b nonzero with the same sign
 __device__ __forceinline__ bool same_sign_strict(double a, double b) {
   long long ba = dbits(a), bb = dbits(b);

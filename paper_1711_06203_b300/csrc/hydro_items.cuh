@@ -96,20 +96,35 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
     double ref[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : zone[v];
-    // the reference wave contributes exactly zero (ref - I(sigma_fast) == 0), so
-    // only the other acoustic wave and the entropy/shear wave are evaluated
-    double bm = 0.0, b0 = 0.0, bp = 0.0, bt1 = 0.0, bt2 = 0.0;
-    if (side == 1 && reach[0]) bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
+    // Edge state = ref - sum of beta_nu r_nu over the waves that reach the
+    // face: s_rho = ref - ((bm + b0) + bp), s_un = ref - (bm (-c/rho) + bp c/rho),
+    // s_p = ref - (bm c^2 + bp c^2), s_t = ref - bt.  The reference wave's beta
+    // is exactly +0 (ref - I(sigma_fast) == 0) and a wave that does not reach
+    // contributes +0.0, so only the terms of the other waves are formed; where
+    // a +0 is dropped from a sum, pz() applies what adding it does (turn -0
+    // into +0), and every edge state is bitwise the full expression's.  The
+    // other acoustic wave reaches only if the entropy wave does, and nothing
+    // but the reference wave reaches if that one does not.
+    double s_rho = ref[0], s_un = ref[1], s_p = ref[4], s_t1 = ref[2], s_t2 = ref[3];
     if (reach[1]) {
-      b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
-      bt1 = ref[2] - I(1, 2);
-      bt2 = ref[3] - I(1, 3);
+      const double b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
+      const double bt1 = ref[2] - I(1, 2), bt2 = ref[3] - I(1, 3);
+      s_t1 = ref[2] - bt1;
+      s_t2 = ref[3] - bt2;
+      if (side == 1 && reach[0]) {
+        const double bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
+        s_rho = ref[0] - pz(bm + b0);
+        s_un = ref[1] - pz(bm * (-c_rho));
+        s_p = ref[4] - pz(bm * c2);
+      } else if (side == 0 && reach[2]) {
+        const double bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
+        s_rho = ref[0] - (pz(b0) + bp);
+        s_un = ref[1] - bp * c_rho;  // (-0) + bp c/rho is bp c/rho
+        s_p = ref[4] - pz(bp * c2);
+      } else {
+        s_rho = ref[0] - pz(b0);
+      }
     }
-    if (side == 0 && reach[2]) bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
-    double s_rho = ref[0] - ((bm + b0) + bp);
-    double s_un = ref[1] - (bm * (-c_rho) + bp * c_rho);
-    double s_p = ref[4] - (bm * c2 + bp * c2);
-    double s_t1 = ref[2] - bt1, s_t2 = ref[3] - bt2;
     if (K.has_grav) {
       s_un = s_un + K.hdt * K.grav[D];
       s_t1 = s_t1 + K.hdt * K.grav[T1];
