@@ -454,7 +454,11 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   double sstar = ddiv((pr - pl) + ml * ul - mr * ur, ml - mr);
   int region = ge0(sl) ? 0 : ge0(sstar) ? 1 : gt0(sr) ? 2 : 3;
   bool left = region <= 1;
-  const double* s = left ? sL : sR;
+  // the chosen side's state, component by component (selecting a pointer to
+  // one of the two arrays would force both into local memory)
+  double s[NS];
+#pragma unroll
+  for (int c = 0; c < NS; ++c) s[c] = left ? sL[c] : sR[c];
   double rho = s[S_RHO], un = s[1 + d], p = s[S_P], E = s[S_E];
   if (region == 0 || region == 3) {
     // physical flux of the chosen side
