@@ -247,26 +247,49 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     k_prim<<<blocks_for(r.count()), BLOCK, 0, st>>>(a.in, sg, s.Q, a.K, r, a.flags);
     nl += 1;
   };
-  // each landed chunk: primitive state and the x and y sweeps of its planes
+  // each landed chunk: primitive state and the x and y sweeps of its planes.
+  // The ghost planes below 0 copy interior plane 0 (outflow), planes [0, NG)
+  // (reflect) or [n-NG, n) (periodic), and those above n-1 likewise.  When
+  // the first (last) chunk holds those planes, the ghost planes are formed
+  // right after it and plane -1 (n) joins that chunk's sweeps; otherwise
+  // they come after all chunks, with sweeps of their own (a one-plane sweep
+  // launch costs nearly as much as a chunk's).
+  const int bclo = a.in.bc[2][0], bchi = a.in.bc[2][1];  // 0 outflow, 1 reflect, 2 periodic
+  const bool low_early = bclo == 0 || (bclo == 1 && zc(1) >= NG);
+  const bool high_early = bchi == 0 || (bchi == 1 && zc(C - 1) <= n[2] - NG);
+  unsigned long long* cg = p.cursors + 2 * PIPE_MAX_CHUNKS;
   for (int k = 0; k < C; ++k) {
     if (cudaStreamWaitEvent(st, p.h2d_done[k], 0) != cudaSuccess) return cudaGetLastError();
-    const int z0 = zc(k), ze = zc(k + 1) - zc(k);
+    int z0 = zc(k), ze = zc(k + 1) - zc(k);
     prim(z0, ze);
+    if (low_early && k == 0) {
+      prim(-NG, NG);
+      z0 -= 1;
+      ze += 1;
+    }
+    if (high_early && k == C - 1) {
+      prim(n[2], NG);
+      ze += 1;
+    }
     launch_trace(0, a, z0, ze, p.cursors + 2 * k, st);
     launch_trace(1, a, z0, ze, p.cursors + 2 * k + 1, st);
     nl += 2;
   }
-  // ghost planes (mapped onto interior planes by the boundary kinds), the x
-  // and y sweeps of planes -1 and n, and the z sweep
-  prim(-NG, NG);
-  prim(n[2], NG);
-  unsigned long long* cg = p.cursors + 2 * PIPE_MAX_CHUNKS;
-  launch_trace(0, a, -1, 1, cg, st);
-  launch_trace(1, a, -1, 1, cg + 1, st);
-  launch_trace(0, a, n[2], 1, cg + 2, st);
-  launch_trace(1, a, n[2], 1, cg + 3, st);
+  if (!low_early) {
+    prim(-NG, NG);
+    launch_trace(0, a, -1, 1, cg, st);
+    launch_trace(1, a, -1, 1, cg + 1, st);
+    nl += 2;
+  }
+  if (!high_early) {
+    prim(n[2], NG);
+    launch_trace(0, a, n[2], 1, cg + 2, st);
+    launch_trace(1, a, n[2], 1, cg + 3, st);
+    nl += 2;
+  }
+  // the z sweep
   launch_trace(2, a, -1, n[1] + 2, cg + 4, st);
-  nl += 5;
+  nl += 1;
   // first fluxes on d-faces [0, n_d] x transverse [-1, n]
   for (int d = 0; d < 3; ++d) {
     Range r;

@@ -302,7 +302,8 @@ def test_host_buffer_step_matches_device_step():
     """hydro_advance_box_host on pageable and pinned host buffers gives the
     device path's result bit for bit: 3-D boxes with derived faces (interior
     planes only cross the host link, in z-chunks that overlap the kernels;
-    4 to 44 planes), a prefilled face (the whole input box crosses) and 2-D.
+    4 to 44 planes, every z boundary kind), a prefilled face (the whole input
+    box crosses) and 2-D.
     It writes none of the output's ghost planes along the slowest axis and
     refuses non-natural layouts."""
     rng = np.random.default_rng(12)
@@ -314,6 +315,9 @@ def test_host_buffer_step_matches_device_step():
         # one interior plane per chunk of the overlapped path, and a box of several planes per chunk
         (3, (10, 9, 4), ((hb.BC_REFLECT, hb.BC_OUTFLOW), (hb.BC_OUTFLOW,) * 2, (hb.BC_OUTFLOW,) * 2)),
         (3, (40, 36, 44), ((hb.BC_OUTFLOW,) * 2, (hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW))),
+        # reflecting z faces with chunks thinner than a ghost layer, and periodic z
+        (3, (10, 8, 6), ((hb.BC_OUTFLOW,) * 2, (hb.BC_OUTFLOW,) * 2, (hb.BC_REFLECT,) * 2)),
+        (3, (9, 12, 20), ((hb.BC_REFLECT,) * 2, (hb.BC_OUTFLOW,) * 2, (hb.BC_PERIODIC,) * 2)),
     ]
     for dim, n, bc in cases:
         U = inputs.random_box(rng, n, dim)
