@@ -148,14 +148,20 @@ __global__ void __launch_bounds__(BLOCK) km_recon(ScratchGeom sg, const double* 
   double s0 = mc_slope_d(d0, d01, am1, ap1);
   const double sm1 = mc_slope_d(dm, d0, am2, a0);
   double fm = face_value(am1, a0, sm1, s0);  // interface z0 - 1/2
+  // each zone's new operands (a_{m+2}, chi_m) are loaded one zone ahead
+  double nap2 = a[(z0 + 2) * st], nchi = CHI[base + z0 * st];
   for (int m = z0; m < z1; ++m) {
-    const double ap2 = a[(m + 2) * st];
+    const double ap2 = nap2, chi = nchi;
+    if (m + 1 < z1) {
+      nap2 = a[(m + 3) * st];
+      nchi = CHI[base + (m + 1) * st];
+    }
     const double d12 = ap2 - ap1;
     const double s1 = mc_slope_d(d01, d12, a0, ap2);
     d01 = d12;
     const double fp = face_value(a0, ap1, s0, s1);  // interface m + 1/2
     double lo, hi, a6;
-    ppm_limit(a0, fm, fp, CHI[base + m * st], lo, hi, a6);
+    ppm_limit(a0, fm, fp, chi, lo, hi, a6);
     const long long o = (long long)v * sg.sc + base + m * st;
     EM[o] = lo;
     EP[o] = hi;
