@@ -214,7 +214,7 @@ def run_reference(args):
     return 0
 
 
-def bench_batch(args, dev, stream):
+def bench_batch(args, dev, stream, cpu_sample=False):
     """Batched level: 512 boxes, sides drawn from {16,24,32,48,64} per axis
     (seed 1711), random prefilled states, gamma = 5/3, dx = 1/64, one step at
     the level dt (min over boxes).  The batched step (one launch per stage over
@@ -284,6 +284,24 @@ def bench_batch(args, dev, stream):
         graph_error = f"{type(e).__name__}: {e}"[:200]
     tuning = ctx.hydro_batch_tuning()
     ctx.close()
+    cpu = None
+    if cpu_sample:
+        # the CPU oracle on the level's boxes in order, one step each, until
+        # about 8 s of host time are spent
+        import oracle
+        done_zones, t_cpu, nb = 0, 0.0, 0
+        for x, sz in zip(a, sizes):
+            U = x.cpu().numpy()
+            P = oracle.params(3, sz, dx=dx, bc=oracle.BC_PREFILLED, gamma=5.0 / 3.0, cfl=0.5)
+            t0 = time.perf_counter()
+            oracle.step(U, P, level_dt)
+            t_cpu += time.perf_counter() - t0
+            done_zones += sz[0] * sz[1] * sz[2]
+            nb += 1
+            if t_cpu > 8.0:
+                break
+        cpu = {"zone_updates_per_s": done_zones / t_cpu, "cores": os.cpu_count(),
+               "sample": f"one oracle step of each of the first {nb} boxes ({done_zones} zones)"}
     return {"workload": "level of 512 boxes, sides from {16,24,32,48,64} (seed 1711), prefilled, gamma 5/3",
             "interior_zones": zones, "zone_updates_per_s": zones / (ms_batch * 1e-3), "ms_per_step": ms_batch,
             "per_box_zone_updates_per_s": zones / (ms_plain * 1e-3), "per_box_ms_per_step": ms_plain,
@@ -293,7 +311,8 @@ def bench_batch(args, dev, stream):
             "speedup_vs_per_box_graph": ms_graph / ms_batch if ms_graph else None, "per_box_graph_error": graph_error,
             "per_box_launches_per_step": launches_plain, "plan_build_ms": plan_ms,
             "sweep_segment_by_extent": {str(k): v for k, v in sorted(tuning.items())},
-            "l2": "working set 3.7 GB of state + scratch, larger than L2"}
+            "l2": "working set 3.7 GB of state + scratch, larger than L2", "cpu_oracle": cpu,
+            "gpu_over_cpu_oracle": (zones / (ms_batch * 1e-3)) / cpu["zone_updates_per_s"] if cpu else None}
 
 
 def batch_profile(args):
@@ -800,7 +819,7 @@ def run_ours(args):
 
     batch = None
     if world == 1 and not args.no_batch:
-        batch = bench_batch(args, dev, stream)
+        batch = bench_batch(args, dev, stream, cpu_sample=not args.no_cpu_baseline)
     serve = None
     if world == 1 and args.serve_requests > 0:
         serve = bench_serve(args, dev, value)
