@@ -73,8 +73,8 @@ __device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __
 // states to TM/TP at id in absolute component order.
 template <int D>
 __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5], const double dap[5],
-                                           const double a6[5], const double zone[5], double c, double rho_c, double c_rho,
-                                           double inv_c2, const StepConst& K, double* __restrict__ TM,
+                                           const double a6[5], const double zone[5], double c, double rho_c,
+                                           double c_rho, double inv_c2, const StepConst& K, double* __restrict__ TM,
                                            double* __restrict__ TP, long long sc, long long id) {
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
   const double un = zone[1];

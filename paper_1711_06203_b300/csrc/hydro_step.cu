@@ -105,6 +105,46 @@ void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long lon
   if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
 }
 
+// first fluxes through d-faces [0, n_d] x transverse [-1, n] of every active
+// direction d (rt: the tracing range, zones [-1, n] on active axes)
+int launch_flux1_all(const StepArgs& a, const Range& rt, int dim, cudaStream_t st) {
+  const int* n = a.in.n;
+  const Scratch& s = a.s;
+  for (int d = 0; d < dim; ++d) {
+    Range r = rt;
+    r.lo[d] = 0;
+    r.ext[d] = n[d] + 1;
+    unsigned b = blocks_for(r.count());
+    if (d == 0) k_flux1<0><<<b, BLOCK, 0, st>>>(a.sg, s.TP[0], s.TM[0], s.F1[0], a.K, r);
+    if (d == 1) k_flux1<1><<<b, BLOCK, 0, st>>>(a.sg, s.TP[1], s.TM[1], s.F1[1], a.K, r);
+    if (d == 2) k_flux1<2><<<b, BLOCK, 0, st>>>(a.sg, s.TP[2], s.TM[2], s.F1[2], a.K, r);
+  }
+  return dim;
+}
+
+// 3-D intermediate fluxes F^{d|t}: d-faces [0, n_d] x t in [0, n_t) x third axis [-1, n]
+int launch_flux2_all(const StepArgs& a, cudaStream_t st) {
+  const int* n = a.in.n;
+  const Scratch& s = a.s;
+  for (int d = 0; d < 3; ++d)
+    for (int t = 0; t < 3; ++t) {
+      if (t == d) continue;
+      int o = 3 - d - t;
+      Range r;
+      r.lo[d] = 0; r.ext[d] = n[d] + 1;
+      r.lo[t] = 0; r.ext[t] = n[t];
+      r.lo[o] = -1; r.ext[o] = n[o] + 2;
+      unsigned b = blocks_for(r.count());
+      const double* f1 = s.F1[t];
+      double* f2 = s.F2[d][t];
+#define F2CASE(DD, TT) \
+  if (d == DD && t == TT) k_flux2<DD, TT><<<b, BLOCK, 0, st>>>(a.sg, s.TP[DD], s.TM[DD], f1, f2, a.K, r);
+      F2CASE(0, 1) F2CASE(0, 2) F2CASE(1, 0) F2CASE(1, 2) F2CASE(2, 0) F2CASE(2, 1)
+#undef F2CASE
+    }
+  return 6;
+}
+
 }  // namespace
 
 cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches) {
@@ -153,37 +193,10 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
   nl += dim;
   mark(ST_FLUX1);
   // stage 4a: first fluxes on d-faces [0, n_d] x transverse [-1, n]
-  for (int d = 0; d < dim; ++d) {
-    Range r = rt;
-    r.lo[d] = 0;
-    r.ext[d] = n[d] + 1;
-    unsigned b = blocks_for(r.count());
-    if (d == 0) k_flux1<0><<<b, BLOCK, 0, st>>>(sg, s.TP[0], s.TM[0], s.F1[0], a.K, r);
-    if (d == 1) k_flux1<1><<<b, BLOCK, 0, st>>>(sg, s.TP[1], s.TM[1], s.F1[1], a.K, r);
-    if (d == 2) k_flux1<2><<<b, BLOCK, 0, st>>>(sg, s.TP[2], s.TM[2], s.F1[2], a.K, r);
-    nl += 1;
-  }
+  nl += launch_flux1_all(a, rt, dim, st);
   mark(ST_FLUX2);
   // stage 4b (3-D): intermediate fluxes F^{d|t}
-  if (dim == 3) {
-    for (int d = 0; d < 3; ++d)
-      for (int t = 0; t < 3; ++t) {
-        if (t == d) continue;
-        int o = 3 - d - t;
-        Range r;
-        r.lo[d] = 0; r.ext[d] = n[d] + 1;
-        r.lo[t] = 0; r.ext[t] = n[t];
-        r.lo[o] = -1; r.ext[o] = n[o] + 2;
-        unsigned b = blocks_for(r.count());
-        const double* f1 = s.F1[t];
-        double* f2 = s.F2[d][t];
-#define F2CASE(DD, TT) \
-  if (d == DD && t == TT) k_flux2<DD, TT><<<b, BLOCK, 0, st>>>(sg, s.TP[DD], s.TM[DD], f1, f2, a.K, r);
-        F2CASE(0, 1) F2CASE(0, 2) F2CASE(1, 0) F2CASE(1, 2) F2CASE(2, 0) F2CASE(2, 1)
-#undef F2CASE
-        nl += 1;
-      }
-  }
+  if (dim == 3) nl += launch_flux2_all(a, st);
   mark(ST_FLUX3);
   // stage 4c: final fluxes on d-faces [0, n_d] x transverse interior
   for (int d = 0; d < dim; ++d) {
@@ -290,36 +303,13 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
   // the z sweep
   launch_trace(2, a, -1, n[1] + 2, cg + 4, st);
   nl += 1;
-  // first fluxes on d-faces [0, n_d] x transverse [-1, n]
-  for (int d = 0; d < 3; ++d) {
-    Range r;
-    for (int ax = 0; ax < 3; ++ax) { r.lo[ax] = -1; r.ext[ax] = n[ax] + 2; }
-    r.lo[d] = 0;
-    r.ext[d] = n[d] + 1;
-    unsigned b = blocks_for(r.count());
-    if (d == 0) k_flux1<0><<<b, BLOCK, 0, st>>>(sg, s.TP[0], s.TM[0], s.F1[0], a.K, r);
-    if (d == 1) k_flux1<1><<<b, BLOCK, 0, st>>>(sg, s.TP[1], s.TM[1], s.F1[1], a.K, r);
-    if (d == 2) k_flux1<2><<<b, BLOCK, 0, st>>>(sg, s.TP[2], s.TM[2], s.F1[2], a.K, r);
-    nl += 1;
+  // first fluxes on d-faces [0, n_d] x transverse [-1, n], intermediate fluxes F^{d|t}
+  {
+    Range rt;
+    for (int ax = 0; ax < 3; ++ax) { rt.lo[ax] = -1; rt.ext[ax] = n[ax] + 2; }
+    nl += launch_flux1_all(a, rt, 3, st);
   }
-  // intermediate fluxes F^{d|t}
-  for (int d = 0; d < 3; ++d)
-    for (int t = 0; t < 3; ++t) {
-      if (t == d) continue;
-      int o = 3 - d - t;
-      Range r;
-      r.lo[d] = 0; r.ext[d] = n[d] + 1;
-      r.lo[t] = 0; r.ext[t] = n[t];
-      r.lo[o] = -1; r.ext[o] = n[o] + 2;
-      unsigned b = blocks_for(r.count());
-      const double* f1 = s.F1[t];
-      double* f2 = s.F2[d][t];
-#define F2CASE(DD, TT) \
-  if (d == DD && t == TT) k_flux2<DD, TT><<<b, BLOCK, 0, st>>>(sg, s.TP[DD], s.TM[DD], f1, f2, a.K, r);
-      F2CASE(0, 1) F2CASE(0, 2) F2CASE(1, 0) F2CASE(1, 2) F2CASE(2, 0) F2CASE(2, 1)
-#undef F2CASE
-      nl += 1;
-    }
+  nl += launch_flux2_all(a, st);
   // final fluxes and update chunk by chunk; each chunk's output planes go
   // back while the next chunk computes.  A chunk computes z-faces
   // [z0, z0 + ze], so the face it shares with the next chunk is formed by
