@@ -303,7 +303,7 @@ def test_host_buffer_step_matches_device_step():
     device path's result bit for bit: 3-D boxes with derived faces (interior
     planes only cross the host link, in z-chunks that overlap the kernels;
     4 to 44 planes, every z boundary kind), a prefilled face (the whole input
-    box crosses) and 2-D.
+    box crosses) and 2-D; a non-physical input is reported.
     It writes none of the output's ghost planes along the slowest axis and
     refuses non-natural layouts."""
     rng = np.random.default_rng(12)
@@ -343,6 +343,20 @@ def test_host_buffer_step_matches_device_step():
                 assert np.isnan(got[:, :4]).all() and np.isnan(got[:, -4:]).all()
             else:
                 assert np.isnan(got[:, :, :4]).all() and np.isnan(got[:, :, -4:]).all()
+    # a non-physical input state is reported by the overlapped path too, and
+    # the context is clean again for the next call
+    n, dx = (16, 12, 20), (0.05,) * 3
+    bc = ((hb.BC_OUTFLOW,) * 2, (hb.BC_REFLECT,) * 2, (hb.BC_OUTFLOW,) * 2)
+    U = inputs.random_box(rng, n, 3)
+    U[0, 4 + 13, 4 + 5, 4 + 7] = -1.0  # negative density in the interior (plane 13 of 20)
+    hin, hout = torch.from_numpy(U.copy()).pin_memory(), torch.empty((5,) + U.shape[1:], dtype=torch.float64).pin_memory()
+    p = hb.params(3, gamma=5 / 3)
+    with pytest.raises(hb.HydroError) as e:
+        ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, 1e-3, want_dt_next=True)
+    assert e.value.status == hb.HYDRO_EBADSTATE
+    U[0, 4 + 13, 4 + 5, 4 + 7] = 1.0
+    hin.copy_(torch.from_numpy(U))
+    assert ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, 1e-3, want_dt_next=True) > 0
     n, dx, bc = cases[0][1], (0.05,) * 3, cases[0][2]
     p = hb.params(3, gamma=5 / 3)
     hout = torch.empty((5,) + inputs.grown_shape(n, 3), dtype=torch.float64)
