@@ -349,7 +349,8 @@ def test_host_buffer_step_matches_device_step():
     bc = ((hb.BC_OUTFLOW,) * 2, (hb.BC_REFLECT,) * 2, (hb.BC_OUTFLOW,) * 2)
     U = inputs.random_box(rng, n, 3)
     U[0, 4 + 13, 4 + 5, 4 + 7] = -1.0  # negative density in the interior (plane 13 of 20)
-    hin, hout = torch.from_numpy(U.copy()).pin_memory(), torch.empty((5,) + U.shape[1:], dtype=torch.float64).pin_memory()
+    hin = torch.from_numpy(U.copy()).pin_memory()
+    hout = torch.empty((5,) + U.shape[1:], dtype=torch.float64).pin_memory()
     p = hb.params(3, gamma=5 / 3)
     with pytest.raises(hb.HydroError) as e:
         ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, 1e-3, want_dt_next=True)
