@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 # zone-direction (trace), Riemann solve (flux1, flux2, flux3), interior zone
 # (update).
 FLOPS_PER_UNIT = {"prim": 20.0, "trace": 225.94, "flux1": 60.0, "flux2": 120.0, "flux3": 154.0, "update": 58.0}
-LAUNCHES_PER_STEP_3D = {"prim": 2, "trace": 3, "flux1": 3, "flux2": 6, "flux3": 3, "update": 2}
+LAUNCHES_PER_STEP_3D = {"prim": 2, "trace": 3, "flux1": 1, "flux2": 1, "flux3": 1, "update": 2}
 # FP64 peak derived from B300's unit counts and clock: 148 SMs x 2 FP64 FMA
 # lanes per SM per clock x 2 flops x 2032 MHz.  (A dependent-free DFMA stream
 # measured 476 G lane-FMA/s = 0.95 TFLOP/s on the B300s.)

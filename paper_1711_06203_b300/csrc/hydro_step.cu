@@ -35,25 +35,77 @@ int trace_resident_blocks() {
   return cached[dev];
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLOCK) k_flux1(ScratchGeom sg, double* __restrict__ TP, double* __restrict__ TM,
-                                                 double* __restrict__ F1, StepConst K, Range R) {
-  flux1_item<D>(sg, TP, TM, F1, K, R, (long long)blockIdx.x * BLOCK + threadIdx.x);
+// Face sets of one direction each (first or final fluxes) in one launch:
+// blocks [first[d], first[d+1]) solve direction d (empty sets allowed).
+struct DirSets {
+  Range r[3];
+  unsigned first[4];
+};
+// direction of this block and its item index (constant indices only: a
+// computed index into the launch parameters would copy them to local memory)
+__device__ __forceinline__ int dir_of(unsigned f1, unsigned f2, long long& t) {
+  const unsigned b = blockIdx.x;
+  const int d = ((b >= f1) ? 1 : 0) + ((b >= f2) ? 1 : 0);
+  const unsigned f = (d == 0) ? 0u : (d == 1) ? f1 : f2;
+  t = (long long)(b - f) * BLOCK + threadIdx.x;
+  return d;
+}
+__global__ void __launch_bounds__(BLOCK) k_flux1(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
+  long long t;
+  switch (dir_of(S.first[1], S.first[2], t)) {
+    case 0: flux1_item<0>(sg, s.TP[0], s.TM[0], s.F1[0], K, S.r[0], t); break;
+    case 1: flux1_item<1>(sg, s.TP[1], s.TM[1], s.F1[1], K, S.r[1], t); break;
+    default: flux1_item<2>(sg, s.TP[2], s.TM[2], s.F1[2], K, S.r[2], t); break;
+  }
 }
 
-template <int D, int T>
-__global__ void __launch_bounds__(BLOCK) k_flux2(ScratchGeom sg, const double* __restrict__ TP,
-                                                 const double* __restrict__ TM, const double* __restrict__ F1t,
-                                                 double* __restrict__ F2, StepConst K, Range R) {
-  flux2_item<D, T>(sg, TP, TM, F1t, F2, K, R, (long long)blockIdx.x * BLOCK + threadIdx.x);
+// The six intermediate-flux sets F^{d|t} of a 3-D step are independent of
+// one another, so they run as one launch: blocks [first[c], first[c+1])
+// solve set c = (d, t) in the order (0,1), (0,2), (1,0), (1,2), (2,0), (2,1).
+// (Six launches each ended on a partly filled last wave.)
+struct Flux2Sets {
+  Range r[6];
+  unsigned first[7];
+};
+__global__ void __launch_bounds__(BLOCK) k_flux2(ScratchGeom sg, Scratch s, StepConst K, Flux2Sets S) {
+  const unsigned b = blockIdx.x;
+  int c = 0;
+  unsigned f = 0;
+#pragma unroll
+  for (int i = 1; i < 6; ++i)
+    if (b >= S.first[i]) { c = i; f = S.first[i]; }
+  const long long t = (long long)(b - f) * BLOCK + threadIdx.x;
+  switch (c) {
+    case 0: flux2_item<0, 1>(sg, s.TP[0], s.TM[0], s.F1[1], s.F2[0][1], K, S.r[0], t); break;
+    case 1: flux2_item<0, 2>(sg, s.TP[0], s.TM[0], s.F1[2], s.F2[0][2], K, S.r[1], t); break;
+    case 2: flux2_item<1, 0>(sg, s.TP[1], s.TM[1], s.F1[0], s.F2[1][0], K, S.r[2], t); break;
+    case 3: flux2_item<1, 2>(sg, s.TP[1], s.TM[1], s.F1[2], s.F2[1][2], K, S.r[3], t); break;
+    case 4: flux2_item<2, 0>(sg, s.TP[2], s.TM[2], s.F1[0], s.F2[2][0], K, S.r[4], t); break;
+    default: flux2_item<2, 1>(sg, s.TP[2], s.TM[2], s.F1[1], s.F2[2][1], K, S.r[5], t); break;
+  }
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLOCK) k_flux3(ScratchGeom sg, const double* __restrict__ TP,
-                                                 const double* __restrict__ TM, const double* __restrict__ Fa,
-                                                 const double* __restrict__ Fb, double* __restrict__ F3,
-                                                 StepConst K, Range R) {
-  flux3_item<D>(sg, TP, TM, Fa, Fb, F3, K, R, (long long)blockIdx.x * BLOCK + threadIdx.x);
+// final fluxes: in 3-D from the intermediate fluxes of the two other
+// directions, in 2-D from the first fluxes of the other direction
+// (held to 64 registers: the three-operand form otherwise takes 94 and halves
+// the resident warps)
+template <bool THREE>
+__global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK))
+    k_flux3(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
+  long long t;
+  switch (dir_of(S.first[1], S.first[2], t)) {
+    case 0:
+      if (THREE) flux3_item<0>(sg, s.TP[0], s.TM[0], s.F2[1][2], s.F2[2][1], s.F3[0], K, S.r[0], t);
+      else flux3_item<0>(sg, s.TP[0], s.TM[0], s.F1[1], nullptr, s.F3[0], K, S.r[0], t);
+      break;
+    case 1:
+      if (THREE) flux3_item<1>(sg, s.TP[1], s.TM[1], s.F2[0][2], s.F2[2][0], s.F3[1], K, S.r[1], t);
+      else flux3_item<1>(sg, s.TP[1], s.TM[1], s.F1[0], nullptr, s.F3[1], K, S.r[1], t);
+      break;
+    default:
+      if (THREE) flux3_item<2>(sg, s.TP[2], s.TM[2], s.F2[0][1], s.F2[1][0], s.F3[2], K, S.r[2], t);
+      break;
+  }
 }
 
 __global__ void __launch_bounds__(BLOCK) k_update(BoxGeom in, BoxGeom out, ScratchGeom sg, const double* __restrict__ Fx,
@@ -106,43 +158,58 @@ void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long lon
 }
 
 // first fluxes through d-faces [0, n_d] x transverse [-1, n] of every active
-// direction d (rt: the tracing range, zones [-1, n] on active axes)
+// direction d (rt: the tracing range, zones [-1, n] on active axes), one launch
 int launch_flux1_all(const StepArgs& a, const Range& rt, int dim, cudaStream_t st) {
   const int* n = a.in.n;
-  const Scratch& s = a.s;
-  for (int d = 0; d < dim; ++d) {
-    Range r = rt;
-    r.lo[d] = 0;
-    r.ext[d] = n[d] + 1;
-    unsigned b = blocks_for(r.count());
-    if (d == 0) k_flux1<0><<<b, BLOCK, 0, st>>>(a.sg, s.TP[0], s.TM[0], s.F1[0], a.K, r);
-    if (d == 1) k_flux1<1><<<b, BLOCK, 0, st>>>(a.sg, s.TP[1], s.TM[1], s.F1[1], a.K, r);
-    if (d == 2) k_flux1<2><<<b, BLOCK, 0, st>>>(a.sg, s.TP[2], s.TM[2], s.F1[2], a.K, r);
+  DirSets S;
+  S.first[0] = 0;
+  for (int d = 0; d < 3; ++d) {
+    S.r[d] = rt;
+    S.r[d].lo[d] = 0;
+    S.r[d].ext[d] = n[d] + 1;
+    S.first[d + 1] = S.first[d] + ((d < dim) ? blocks_for(S.r[d].count()) : 0u);
   }
-  return dim;
+  k_flux1<<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  return 1;
+}
+
+// final fluxes through d-faces [0, n_d] of every active direction d, over
+// transverse zones [0, n) except the z range [zlo, zlo + zext) (in 3-D), one launch
+int launch_flux3_all(const StepArgs& a, int dim, int zlo, int zext, cudaStream_t st) {
+  const int* n = a.in.n;
+  DirSets S;
+  S.first[0] = 0;
+  for (int d = 0; d < 3; ++d) {
+    Range& r = S.r[d];
+    for (int ax = 0; ax < 3; ++ax) { r.lo[ax] = 0; r.ext[ax] = (ax < dim) ? n[ax] : 1; }
+    if (dim == 3) { r.lo[2] = zlo; r.ext[2] = zext; }
+    r.ext[d] += 1;
+    S.first[d + 1] = S.first[d] + ((d < dim) ? blocks_for(r.count()) : 0u);
+  }
+  if (dim == 3) k_flux3<true><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  else k_flux3<false><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  return 1;
 }
 
 // 3-D intermediate fluxes F^{d|t}: d-faces [0, n_d] x t in [0, n_t) x third axis [-1, n]
 int launch_flux2_all(const StepArgs& a, cudaStream_t st) {
   const int* n = a.in.n;
-  const Scratch& s = a.s;
+  Flux2Sets S;
+  S.first[0] = 0;
+  int c = 0;
   for (int d = 0; d < 3; ++d)
     for (int t = 0; t < 3; ++t) {
       if (t == d) continue;
       int o = 3 - d - t;
-      Range r;
+      Range& r = S.r[c];
       r.lo[d] = 0; r.ext[d] = n[d] + 1;
       r.lo[t] = 0; r.ext[t] = n[t];
       r.lo[o] = -1; r.ext[o] = n[o] + 2;
-      unsigned b = blocks_for(r.count());
-      const double* f1 = s.F1[t];
-      double* f2 = s.F2[d][t];
-#define F2CASE(DD, TT) \
-  if (d == DD && t == TT) k_flux2<DD, TT><<<b, BLOCK, 0, st>>>(a.sg, s.TP[DD], s.TM[DD], f1, f2, a.K, r);
-      F2CASE(0, 1) F2CASE(0, 2) F2CASE(1, 0) F2CASE(1, 2) F2CASE(2, 0) F2CASE(2, 1)
-#undef F2CASE
+      S.first[c + 1] = S.first[c] + blocks_for(r.count());
+      ++c;
     }
-  return 6;
+  k_flux2<<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  return 1;
 }
 
 }  // namespace
@@ -199,19 +266,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
   if (dim == 3) nl += launch_flux2_all(a, st);
   mark(ST_FLUX3);
   // stage 4c: final fluxes on d-faces [0, n_d] x transverse interior
-  for (int d = 0; d < dim; ++d) {
-    Range r;
-    for (int ax = 0; ax < 3; ++ax) { r.lo[ax] = 0; r.ext[ax] = (ax < dim) ? n[ax] : 1; }
-    r.ext[d] = n[d] + 1;
-    unsigned b = blocks_for(r.count());
-    int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-    const double* fa = (dim == 2) ? s.F1[t1] : s.F2[t1][t2];
-    const double* fb = (dim == 2) ? nullptr : s.F2[t2][t1];
-    if (d == 0) k_flux3<0><<<b, BLOCK, 0, st>>>(sg, s.TP[0], s.TM[0], fa, fb, s.F3[0], a.K, r);
-    if (d == 1) k_flux3<1><<<b, BLOCK, 0, st>>>(sg, s.TP[1], s.TM[1], fa, fb, s.F3[1], a.K, r);
-    if (d == 2) k_flux3<2><<<b, BLOCK, 0, st>>>(sg, s.TP[2], s.TM[2], fa, fb, s.F3[2], a.K, r);
-    nl += 1;
-  }
+  nl += launch_flux3_all(a, dim, 0, (dim == 3) ? n[2] : 1, st);
   mark(ST_UPDATE);
   // stage 5: update + CFL partials (speed maxima were reset at the start of the step)
   Range ru;
@@ -318,17 +373,7 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
   // longer overlap saves.)
   for (int k = 0; k < C; ++k) {
     const int z0 = zc(k), ze = zc(k + 1) - zc(k);
-    for (int d = 0; d < 3; ++d) {
-      Range r;
-      for (int ax = 0; ax < 2; ++ax) { r.lo[ax] = 0; r.ext[ax] = n[ax]; }
-      r.lo[2] = z0; r.ext[2] = ze;
-      r.ext[d] += 1;
-      unsigned b = blocks_for(r.count());
-      if (d == 0) k_flux3<0><<<b, BLOCK, 0, st>>>(sg, s.TP[0], s.TM[0], s.F2[1][2], s.F2[2][1], s.F3[0], a.K, r);
-      if (d == 1) k_flux3<1><<<b, BLOCK, 0, st>>>(sg, s.TP[1], s.TM[1], s.F2[0][2], s.F2[2][0], s.F3[1], a.K, r);
-      if (d == 2) k_flux3<2><<<b, BLOCK, 0, st>>>(sg, s.TP[2], s.TM[2], s.F2[0][1], s.F2[1][0], s.F3[2], a.K, r);
-      nl += 1;
-    }
+    nl += launch_flux3_all(a, 3, z0, ze, st);
     Range ru;
     ru.lo[0] = 0; ru.ext[0] = n[0];
     ru.lo[1] = 0; ru.ext[1] = n[1];
