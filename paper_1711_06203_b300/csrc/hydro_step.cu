@@ -157,9 +157,10 @@ void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long lon
   if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
 }
 
-// first fluxes through d-faces [0, n_d] x transverse [-1, n] of every active
-// direction d (rt: the tracing range, zones [-1, n] on active axes), one launch
-int launch_flux1_all(const StepArgs& a, const Range& rt, int dim, cudaStream_t st) {
+// first fluxes through d-faces [0, n_d] x the transverse zones of rt (the
+// tracing range: zones [-1, n] on active axes, or a slab of z-planes) of the
+// directions d in dirs (bit d), one launch
+int launch_flux1_all(const StepArgs& a, const Range& rt, unsigned dirs, cudaStream_t st) {
   const int* n = a.in.n;
   DirSets S;
   S.first[0] = 0;
@@ -167,7 +168,7 @@ int launch_flux1_all(const StepArgs& a, const Range& rt, int dim, cudaStream_t s
     S.r[d] = rt;
     S.r[d].lo[d] = 0;
     S.r[d].ext[d] = n[d] + 1;
-    S.first[d + 1] = S.first[d] + ((d < dim) ? blocks_for(S.r[d].count()) : 0u);
+    S.first[d + 1] = S.first[d] + (((dirs >> d) & 1u) ? blocks_for(S.r[d].count()) : 0u);
   }
   k_flux1<<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   return 1;
@@ -260,7 +261,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
   nl += dim;
   mark(ST_FLUX1);
   // stage 4a: first fluxes on d-faces [0, n_d] x transverse [-1, n]
-  nl += launch_flux1_all(a, rt, dim, st);
+  nl += launch_flux1_all(a, rt, (1u << dim) - 1u, st);
   mark(ST_FLUX2);
   // stage 4b (3-D): intermediate fluxes F^{d|t}
   if (dim == 3) nl += launch_flux2_all(a, st);
@@ -322,6 +323,14 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
   // right after it and plane -1 (n) joins that chunk's sweeps; otherwise
   // they come after all chunks, with sweeps of their own (a one-plane sweep
   // launch costs nearly as much as a chunk's).
+  // the first x and y fluxes of a slab of planes need only its own x and y
+  // sweeps, so they fill the wait for the next input chunk
+  auto flux1_xy = [&](int zlo, int zext) {
+    Range rt;
+    for (int ax = 0; ax < 2; ++ax) { rt.lo[ax] = -1; rt.ext[ax] = n[ax] + 2; }
+    rt.lo[2] = zlo; rt.ext[2] = zext;
+    return launch_flux1_all(a, rt, 3u, st);
+  };
   const int bclo = a.in.bc[2][0], bchi = a.in.bc[2][1];  // 0 outflow, 1 reflect, 2 periodic
   const bool low_early = bclo == 0 || (bclo == 1 && zc(1) >= NG);
   const bool high_early = bchi == 0 || (bchi == 1 && zc(C - 1) <= n[2] - NG);
@@ -341,28 +350,28 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     }
     launch_trace(0, a, z0, ze, p.cursors + 2 * k, st);
     launch_trace(1, a, z0, ze, p.cursors + 2 * k + 1, st);
-    nl += 2;
+    nl += 2 + flux1_xy(z0, ze);
   }
   if (!low_early) {
     prim(-NG, NG);
     launch_trace(0, a, -1, 1, cg, st);
     launch_trace(1, a, -1, 1, cg + 1, st);
-    nl += 2;
+    nl += 2 + flux1_xy(-1, 1);
   }
   if (!high_early) {
     prim(n[2], NG);
     launch_trace(0, a, n[2], 1, cg + 2, st);
     launch_trace(1, a, n[2], 1, cg + 3, st);
-    nl += 2;
+    nl += 2 + flux1_xy(n[2], 1);
   }
   // the z sweep
   launch_trace(2, a, -1, n[1] + 2, cg + 4, st);
   nl += 1;
-  // first fluxes on d-faces [0, n_d] x transverse [-1, n], intermediate fluxes F^{d|t}
+  // first z fluxes on z-faces [0, n_z] x transverse [-1, n], intermediate fluxes F^{d|t}
   {
     Range rt;
     for (int ax = 0; ax < 3; ++ax) { rt.lo[ax] = -1; rt.ext[ax] = n[ax] + 2; }
-    nl += launch_flux1_all(a, rt, 3, st);
+    nl += launch_flux1_all(a, rt, 4u, st);
   }
   nl += launch_flux2_all(a, st);
   // final fluxes and update chunk by chunk; each chunk's output planes go
