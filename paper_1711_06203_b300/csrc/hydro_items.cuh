@@ -84,47 +84,73 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
   double sig[3];
 #pragma unroll
   for (int w = 0; w < 3; ++w) sig[w] = fabs(lam[w]) * K.dtdx[D];
+  // Reference states: the fastest wave toward each face (lambda_- toward the
+  // low face, lambda_+ toward the high face), else the zone average.
+  // o0 / o1: the low / high face's edge state (rho, un, ut1, ut2, p).
+  const bool fast_lo = lt0(lam[0]), fast_hi = gt0(lam[2]);
+  double o0[5], o1[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    o0[v] = fast_lo ? integ_minus(am[v], ap[v], dap[v], a6[v], sig[0]) : zone[v];
+    o1[v] = fast_hi ? integ_plus(am[v], ap[v], dap[v], a6[v], sig[2]) : zone[v];
+  }
+  // Edge state = ref - sum of beta_nu r_nu over the waves that reach the
+  // face: s_rho = ref - ((bm + b0) + bp), s_un = ref - (bm (-c/rho) + bp c/rho),
+  // s_p = ref - (bm c^2 + bp c^2), s_t = ref - bt.  The reference wave's beta
+  // is exactly +0 (ref - I(sigma_fast) == 0) and a wave that does not reach
+  // contributes +0.0, so only the terms of the other waves are formed; where
+  // a +0 is dropped from a sum, pz() applies what adding it does (turn -0
+  // into +0), and every edge state is bitwise the full expression's.
+  // The entropy and shear wave (lambda_0 = u_n) reaches the high face when
+  // u_n > 0 and the low face when u_n < 0, never both, so its terms are formed
+  // once, on the inputs of the face it reaches (lanes of a warp with opposite
+  // signs of u_n then share one pass).  The low face's integral
+  // a- + s/2 (da + (1 - 2s/3) a6) is the high face's form a+ - s/2 (da - (1 - 2s/3) a6)
+  // with a+ -> a- and da -> -da, negation being exact.  The other acoustic
+  // wave reaches only if the entropy wave does, and nothing but the reference
+  // wave reaches if that one does not.
+  const bool hi = gt0(un);
+  if (hi || lt0(un)) {
+    const double t = 1.0 - TWOTHIRDS * sig[1], hs = dhalf(sig[1]);
+    double ref[5], i0[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      ref[v] = hi ? o1[v] : o0[v];
+      const double e = hi ? ap[v] : am[v], x = hi ? dap[v] : dneg(dap[v]);
+      i0[v] = e - hs * (x - t * a6[v]);  // I(sigma_0) of the reached face (unused for u_n)
+    }
+    const double b0 = (ref[0] - i0[0]) - inv_c2 * (ref[4] - i0[4]);
+    const double bt1 = ref[2] - i0[2], bt2 = ref[3] - i0[3];
+    double s[5];
+    s[1] = ref[1];
+    s[2] = ref[2] - bt1;
+    s[3] = ref[3] - bt2;
+    s[4] = ref[4];
+    if (hi && gt0(lam[0])) {  // supersonic toward the high face: lambda_- reaches it too
+      const double bm = -lu * (ref[1] - integ_plus(am[1], ap[1], dap[1], a6[1], sig[0])) +
+                        lp * (ref[4] - integ_plus(am[4], ap[4], dap[4], a6[4], sig[0]));
+      s[0] = ref[0] - pz(bm + b0);
+      s[1] = ref[1] - pz(bm * (-c_rho));
+      s[4] = ref[4] - pz(bm * c2);
+    } else if (!hi && lt0(lam[2])) {  // supersonic toward the low face: lambda_+ reaches it too
+      const double bp = lu * (ref[1] - integ_minus(am[1], ap[1], dap[1], a6[1], sig[2])) +
+                        lp * (ref[4] - integ_minus(am[4], ap[4], dap[4], a6[4], sig[2]));
+      s[0] = ref[0] - (pz(b0) + bp);
+      s[1] = ref[1] - bp * c_rho;  // (-0) + bp c/rho is bp c/rho
+      s[4] = ref[4] - pz(bp * c2);
+    } else {
+      s[0] = ref[0] - pz(b0);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      o1[v] = hi ? s[v] : o1[v];
+      o0[v] = hi ? o0[v] : s[v];
+    }
+  }
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    bool reach[3];
-#pragma unroll
-    for (int w = 0; w < 3; ++w) reach[w] = side ? gt0(lam[w]) : lt0(lam[w]);
-    const int fast = side ? 2 : 0;
-    auto I = [&](int w, int v) {
-      return side ? integ_plus(am[v], ap[v], dap[v], a6[v], sig[w]) : integ_minus(am[v], ap[v], dap[v], a6[v], sig[w]);
-    };
-    double ref[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) ref[v] = reach[fast] ? I(fast, v) : zone[v];
-    // Edge state = ref - sum of beta_nu r_nu over the waves that reach the
-    // face: s_rho = ref - ((bm + b0) + bp), s_un = ref - (bm (-c/rho) + bp c/rho),
-    // s_p = ref - (bm c^2 + bp c^2), s_t = ref - bt.  The reference wave's beta
-    // is exactly +0 (ref - I(sigma_fast) == 0) and a wave that does not reach
-    // contributes +0.0, so only the terms of the other waves are formed; where
-    // a +0 is dropped from a sum, pz() applies what adding it does (turn -0
-    // into +0), and every edge state is bitwise the full expression's.  The
-    // other acoustic wave reaches only if the entropy wave does, and nothing
-    // but the reference wave reaches if that one does not.
-    double s_rho = ref[0], s_un = ref[1], s_p = ref[4], s_t1 = ref[2], s_t2 = ref[3];
-    if (reach[1]) {
-      const double b0 = (ref[0] - I(1, 0)) - inv_c2 * (ref[4] - I(1, 4));
-      const double bt1 = ref[2] - I(1, 2), bt2 = ref[3] - I(1, 3);
-      s_t1 = ref[2] - bt1;
-      s_t2 = ref[3] - bt2;
-      if (side == 1 && reach[0]) {
-        const double bm = -lu * (ref[1] - I(0, 1)) + lp * (ref[4] - I(0, 4));
-        s_rho = ref[0] - pz(bm + b0);
-        s_un = ref[1] - pz(bm * (-c_rho));
-        s_p = ref[4] - pz(bm * c2);
-      } else if (side == 0 && reach[2]) {
-        const double bp = lu * (ref[1] - I(2, 1)) + lp * (ref[4] - I(2, 4));
-        s_rho = ref[0] - (pz(b0) + bp);
-        s_un = ref[1] - bp * c_rho;  // (-0) + bp c/rho is bp c/rho
-        s_p = ref[4] - pz(bp * c2);
-      } else {
-        s_rho = ref[0] - pz(b0);
-      }
-    }
+    double* o = side ? o1 : o0;
+    double s_rho = o[0], s_un = o[1], s_t1 = o[2], s_t2 = o[3], s_p = o[4];
     if (K.has_grav) {
       s_un = s_un + K.hdt * K.grav[D];
       s_t1 = s_t1 + K.hdt * K.grav[T1];
