@@ -392,13 +392,16 @@ __device__ __forceinline__ void ppm_limit(double ai, double aM, double aP, doubl
     dd = D;
     M = ai - dhalf(aM + aP);
     const long long kD = okey(D), km = okey(M), kt = okey(SIXTH * D);  // t = D/6
-    // up = M - t, dn = M + t; D != 0 here
+    // up = M - t, dn = M + t; D != 0 here.  Either edge may be reset from
+    // the other (a- = 3 ai - 2 a+, else a+ = 3 ai - 2 a-): one operation on
+    // the selected edge, so lanes taking different cases share it
     const bool dpos = ilt(0, kD);
-    if (dpos ? ilt(kt, km) : ilt(km, kt)) {
-      aM = 3.0 * ai - dtwice(aP);
-      m_current = false;
-    } else if (dpos ? ilt(km, -kt) : ilt(-kt, km)) {
-      aP = 3.0 * ai - dtwice(aM);
+    const bool set_m = dpos ? ilt(kt, km) : ilt(km, kt);
+    const bool set_p = !set_m && (dpos ? ilt(km, -kt) : ilt(-kt, km));
+    if (set_m || set_p) {
+      const double y = 3.0 * ai - dtwice(set_m ? aP : aM);
+      aM = set_m ? y : aM;
+      aP = set_p ? y : aP;
       m_current = false;
     }
   }
