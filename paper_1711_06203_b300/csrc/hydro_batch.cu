@@ -78,20 +78,22 @@ __global__ void __launch_bounds__(BLOCK) kb_flux2(const BatchBox* __restrict__ b
   flux2_item<D, T>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[T], B.s.F2[D][T], B.K, B.r2[D][T], item_of(box_first, b));
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLOCK) kb_flux3(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
+// (held to 64 registers, like the single-box final fluxes: the x-face form
+// otherwise takes 94 and loses a third of its resident warps)
+template <int D, bool THREE>
+__global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK)) kb_flux3(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first) {
   const int b = blk_box[blockIdx.x];
   const BatchBox& B = boxes[b];
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
-  const bool three = B.K.dim == 3;
-  const double* fa = three ? B.s.F2[T1][T2] : B.s.F1[T1];
-  const double* fb = three ? B.s.F2[T2][T1] : nullptr;
+  const double* fa = THREE ? B.s.F2[T1][T2] : B.s.F1[T1];
+  const double* fb = THREE ? B.s.F2[T2][T1] : nullptr;
   flux3_item<D>(B.sg, B.s.TP[D], B.s.TM[D], fa, fb, B.s.F3[D], B.K, B.r3[D], item_of(box_first, b));
 }
 
-__global__ void __launch_bounds__(BLOCK) kb_update(BatchBox* boxes, const int* __restrict__ blk_box,
-                                                   const int* __restrict__ box_first) {
+// (held to 64 registers: 100 unbounded; a bound of 6 blocks per SM was no faster)
+__global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK))
+    kb_update(BatchBox* boxes, const int* __restrict__ blk_box, const int* __restrict__ box_first) {
   const int b = blk_box[blockIdx.x];
   BatchBox& B = boxes[b];
   update_item(B.in, B.out, B.sg, B.s.F3[0], B.s.F3[1], B.K.dim == 3 ? B.s.F3[2] : B.s.F3[0], B.K, B.ru, &B.flags,
@@ -255,9 +257,14 @@ void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
 #undef F2
       break;
     case L_FLUX3:
-      if (L.d == 0) kb_flux3<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 1) kb_flux3<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 2) kb_flux3<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (p->dim == 3) {
+        if (L.d == 0) kb_flux3<0, true><<<g, BLOCK, 0, st>>>(B, bb, bf);
+        if (L.d == 1) kb_flux3<1, true><<<g, BLOCK, 0, st>>>(B, bb, bf);
+        if (L.d == 2) kb_flux3<2, true><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      } else {
+        if (L.d == 0) kb_flux3<0, false><<<g, BLOCK, 0, st>>>(B, bb, bf);
+        if (L.d == 1) kb_flux3<1, false><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      }
       break;
     case L_UPDATE: kb_update<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
   }
