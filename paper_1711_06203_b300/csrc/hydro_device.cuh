@@ -443,12 +443,13 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   } else {  // Einfeldt: Roe-averaged normal velocity and sound speed
     double ql = dsqrt(rl), qr = dsqrt(rr);
     double iw = drcp(ql + qr);
-    double wl = ql * iw, wr = qr * iw;
-    double ut0 = wl * sL[1] + wr * sR[1], ut1 = wl * sL[2] + wr * sR[2], ut2 = wl * sL[3] + wr * sR[3];
-    double hl = (sL[S_E] + pl) * sL[S_INV], hr = (sR[S_E] + pr) * sR[S_INV];
-    double ht = wl * hl + wr * hr;
-    double q2 = (ut0 * ut0 + ut1 * ut1) + ut2 * ut2;
-    double ct = dsqrt(K.gm1 * (ht - 0.5 * q2));
+    double wl = mul_i(ql, iw), wr = mul_i(qr, iw);
+    double ut0 = wl * sL[1] + mul_i(wr, sR[1]), ut1 = wl * sL[2] + mul_i(wr, sR[2]);
+    double ut2 = wl * sL[3] + mul_i(wr, sR[3]);
+    double hl = mul_i(sL[S_E] + pl, sL[S_INV]), hr = mul_i(sR[S_E] + pr, sR[S_INV]);
+    double ht = wl * hl + mul_i(wr, hr);
+    double q2 = (mul_i(ut0, ut0) + ut1 * ut1) + ut2 * ut2;
+    double ct = dsqrt(mul_i(K.gm1, ht - dhalf(q2)));
     double utn = (d == 0) ? ut0 : (d == 1) ? ut1 : ut2;
     sl = dmin(ul - cl, utn - ct);
     sr = dmax(ur + cr, utn + ct);
