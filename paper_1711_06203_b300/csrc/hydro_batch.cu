@@ -62,25 +62,25 @@ __global__ void __launch_bounds__(BLOCK) kb_trace(const BatchBox* __restrict__ b
   trace_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], item_of(box_first, b));
 }
 
-template <int D>
+template <int D, bool EINF>
 __global__ void __launch_bounds__(BLOCK) kb_flux1(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first) {
   const int b = blk_box[blockIdx.x];
   const BatchBox& B = boxes[b];  // the traced-state arrays are written through B.s pointers
-  flux1_item<D>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[D], B.K, B.r1[D], item_of(box_first, b));
+  flux1_item<D, EINF>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[D], B.K, B.r1[D], item_of(box_first, b));
 }
 
-template <int D, int T>
+template <int D, int T, bool EINF>
 __global__ void __launch_bounds__(BLOCK) kb_flux2(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first) {
   const int b = blk_box[blockIdx.x];
   const BatchBox& B = boxes[b];
-  flux2_item<D, T>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[T], B.s.F2[D][T], B.K, B.r2[D][T], item_of(box_first, b));
+  flux2_item<D, T, EINF>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[T], B.s.F2[D][T], B.K, B.r2[D][T], item_of(box_first, b));
 }
 
 // (held to 64 registers, like the single-box final fluxes: the x-face form
 // otherwise takes 94 and loses a third of its resident warps)
-template <int D, bool THREE>
+template <int D, bool THREE, bool EINF>
 __global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK)) kb_flux3(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first) {
   const int b = blk_box[blockIdx.x];
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK)) kb_flux3(const Ba
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
   const double* fa = THREE ? B.s.F2[T1][T2] : B.s.F1[T1];
   const double* fb = THREE ? B.s.F2[T2][T1] : nullptr;
-  flux3_item<D>(B.sg, B.s.TP[D], B.s.TM[D], fa, fb, B.s.F3[D], B.K, B.r3[D], item_of(box_first, b));
+  flux3_item<D, EINF>(B.sg, B.s.TP[D], B.s.TM[D], fa, fb, B.s.F3[D], B.K, B.r3[D], item_of(box_first, b));
 }
 
 // (held to 64 registers: 100 unbounded; a bound of 6 blocks per SM was no faster)
@@ -126,6 +126,7 @@ struct LaunchSpec {
 struct Plan {
   uint64_t key = 0;
   int nbox = 0, dim = 0;
+  bool einfeldt = false;  // Einfeldt outer wave speeds (every box shares the flags)
   BatchBox* d_boxes = nullptr;
   int* d_maps = nullptr;
   int* d_bad = nullptr;
@@ -233,6 +234,32 @@ long long items_of(const BatchBox& B, LaunchKind k, int d, int t) {
   }
 }
 
+// solver launches, per wave-speed choice (EINF: Einfeldt, else Davis)
+template <bool EINF>
+void launch_flux1(int d, unsigned g, const BatchBox* B, const int* bb, const int* bf, cudaStream_t st) {
+  if (d == 0) kb_flux1<0, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+  if (d == 1) kb_flux1<1, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+  if (d == 2) kb_flux1<2, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+}
+template <bool EINF>
+void launch_flux2(int d, int t, unsigned g, const BatchBox* B, const int* bb, const int* bf, cudaStream_t st) {
+#define F2(DD, TT) \
+  if (d == DD && t == TT) kb_flux2<DD, TT, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+  F2(0, 1) F2(0, 2) F2(1, 0) F2(1, 2) F2(2, 0) F2(2, 1)
+#undef F2
+}
+template <bool EINF>
+void launch_flux3(int d, int dim, unsigned g, const BatchBox* B, const int* bb, const int* bf, cudaStream_t st) {
+  if (dim == 3) {
+    if (d == 0) kb_flux3<0, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+    if (d == 1) kb_flux3<1, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+    if (d == 2) kb_flux3<2, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+  } else {
+    if (d == 0) kb_flux3<0, false, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+    if (d == 1) kb_flux3<1, false, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+  }
+}
+
 void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
   const int* bb = p->d_maps + L.map_off;
   const int* bf = p->d_maps + L.first_off;
@@ -246,25 +273,16 @@ void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
       if (L.d == 2) kb_trace<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
       break;
     case L_FLUX1:
-      if (L.d == 0) kb_flux1<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 1) kb_flux1<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 2) kb_flux1<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (p->einfeldt) launch_flux1<true>(L.d, g, B, bb, bf, st);
+      else launch_flux1<false>(L.d, g, B, bb, bf, st);
       break;
     case L_FLUX2:
-#define F2(DD, TT) \
-  if (L.d == DD && L.t == TT) kb_flux2<DD, TT><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      F2(0, 1) F2(0, 2) F2(1, 0) F2(1, 2) F2(2, 0) F2(2, 1)
-#undef F2
+      if (p->einfeldt) launch_flux2<true>(L.d, L.t, g, B, bb, bf, st);
+      else launch_flux2<false>(L.d, L.t, g, B, bb, bf, st);
       break;
     case L_FLUX3:
-      if (p->dim == 3) {
-        if (L.d == 0) kb_flux3<0, true><<<g, BLOCK, 0, st>>>(B, bb, bf);
-        if (L.d == 1) kb_flux3<1, true><<<g, BLOCK, 0, st>>>(B, bb, bf);
-        if (L.d == 2) kb_flux3<2, true><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      } else {
-        if (L.d == 0) kb_flux3<0, false><<<g, BLOCK, 0, st>>>(B, bb, bf);
-        if (L.d == 1) kb_flux3<1, false><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      }
+      if (p->einfeldt) launch_flux3<true>(L.d, p->dim, g, B, bb, bf, st);
+      else launch_flux3<false>(L.d, p->dim, g, B, bb, bf, st);
       break;
     case L_UPDATE: kb_update<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
   }
@@ -557,6 +575,7 @@ int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* 
     plan->key = key;
     plan->nbox = nbox;
     plan->dim = dim;
+    plan->einfeldt = (params0->flags & HYDRO_FLAG_EINFELDT) != 0;
     plan->launches = launch_list(dim);
     std::vector<int> maps;
     build_maps(boxes, plan->launches, maps);

@@ -429,7 +429,13 @@ __device__ __forceinline__ double integ_minus(double am, double ap, double dap, 
 }
 
 // ---------------------------------------------------------------- HLLC (Toro-Spruce-Speares)
-// returns true when the flux is taken from the left side of the fan (S* >= 0)
+// returns true when the flux is taken from the left side of the fan (S* >= 0).
+// Outer wave speeds: Einfeldt's (EINF) or Davis's, fixed at compile time; the
+// solver kernels are instantiated for each and chosen at launch from
+// K.einfeldt, so a Davis kernel carries none of the Einfeldt code and its
+// registers (compiled together they raised every solver kernel's
+// allocation from 64 to 76-96 registers).
+template <bool EINF>
 __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[NS], int d, const StepConst& K,
                                           double F[5]) {
   double rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
@@ -437,7 +443,7 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   double cl = dsqrt(mul_i(mul_i(K.gamma, pl), sL[S_INV]));
   double cr = dsqrt(mul_i(mul_i(K.gamma, pr), sR[S_INV]));
   double sl, sr;
-  if (!K.einfeldt) {  // Davis
+  if (!EINF) {  // Davis
     sl = dmin(ul - cl, ur - cr);
     sr = dmax(ul + cl, ur + cr);
   } else {  // Einfeldt: Roe-averaged normal velocity and sound speed

@@ -304,7 +304,8 @@ __device__ __forceinline__ void store5(double* __restrict__ A, long long sc, lon
 }
 
 // ---- stage 4a: first Riemann solves from the traced states
-template <int D>
+// (EINF: Einfeldt outer wave speeds, else Davis; launches choose it from K.einfeldt)
+template <int D, bool EINF>
 __device__ __forceinline__ void flux1_item(ScratchGeom sg, double* __restrict__ TP, double* __restrict__ TM,
                                            double* __restrict__ F1, StepConst K, Range R, long long t) {
   int i, j, k;
@@ -314,7 +315,7 @@ __device__ __forceinline__ void flux1_item(ScratchGeom sg, double* __restrict__ 
   double sL[NS], sR[NS], F[5];
   traced_state(TP, sg.sc, id - st, K, sL);
   traced_state(TM, sg.sc, id, K, sR);
-  hllc_flux(sL, sR, D, K, F);
+  hllc_flux<EINF>(sL, sR, D, K, F);
   store5(F1, sg.sc, id, F);
 }
 
@@ -339,7 +340,7 @@ __device__ __forceinline__ void correct(const double* __restrict__ T, long long 
 }
 
 // ---- stage 4b (3-D): intermediate fluxes F^{d|t}
-template <int D, int T>
+template <int D, int T, bool EINF>
 __device__ __forceinline__ void flux2_item(ScratchGeom sg, const double* __restrict__ TP,
                                                  const double* __restrict__ TM, const double* __restrict__ F1t,
                                                  double* __restrict__ F2, StepConst K, Range R, long long t) {
@@ -352,13 +353,13 @@ __device__ __forceinline__ void flux2_item(ScratchGeom sg, const double* __restr
   double sL[NS], sR[NS], F[5];
   correct(TP, zl, K, coef, F1t, sg.sc, zl + stt, zl, 0.0, nullptr, 0, 0, sL);
   correct(TM, id, K, coef, F1t, sg.sc, id + stt, id, 0.0, nullptr, 0, 0, sR);
-  hllc_flux(sL, sR, D, K, F);
+  hllc_flux<EINF>(sL, sR, D, K, F);
   store5(F2, sg.sc, id, F);
 }
 
 // ---- stage 4c: final fluxes from fully corrected states
 // 2-D: Fa = F1 of the other axis, Fb = null; 3-D: Fa = F^{t1|t2}, Fb = F^{t2|t1}
-template <int D>
+template <int D, bool EINF>
 __device__ __forceinline__ void flux3_item(ScratchGeom sg, const double* __restrict__ TP,
                                                  const double* __restrict__ TM, const double* __restrict__ Fa,
                                                  const double* __restrict__ Fb, double* __restrict__ F3,
@@ -374,7 +375,7 @@ __device__ __forceinline__ void flux3_item(ScratchGeom sg, const double* __restr
   double sL[NS], sR[NS], F[5];
   correct(TP, zl, K, ca, Fa, sg.sc, zl + s1, zl, cb, Fb, zl + s2, zl, sL);
   correct(TM, id, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
-  hllc_flux(sL, sR, D, K, F);
+  hllc_flux<EINF>(sL, sR, D, K, F);
   store5(F3, sg.sc, id, F);
 }
 

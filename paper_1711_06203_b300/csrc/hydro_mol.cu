@@ -17,7 +17,7 @@
 //   km_flat<d>   zones [-1, n_d] x interior: flattening coefficient
 //   km_recon<d>  one thread per (variable, pencil segment): a sliding-window
 //                sweep forms each slope, interface value and limited edge once
-//   km_flux<d>   faces [0, n_d] x interior: HLLC + species upwinding
+//   km_flux<d>   faces [0, n_d] x interior: HLLC + species upwinding (per wave-speed choice)
 //   km_update    interior: flux differences x, y, z, source, stage combination,
 //                bad-state check and CFL partials (second stage)
 // Scratch (grown-box fields): Q, EM, EP, U1 (nf = 5 + nspec each), F (3 nf),
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(BLOCK) km_recon(ScratchGeom sg, const double* 
 }
 
 // ---- HLLC fluxes through d-faces [0, n_d] (interior transverse)
-template <int D>
+template <int D, bool EINF>  // EINF: Einfeldt outer wave speeds (K.einfeldt set), else Davis
 __global__ void __launch_bounds__(BLOCK) km_flux(ScratchGeom sg, const double* __restrict__ EM,
                                                  const double* __restrict__ EP, double* __restrict__ F, int nf,
                                                  StepConst K, Range R) {
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(BLOCK) km_flux(ScratchGeom sg, const double* _
   }
   state_from_prim(qL, K, sL);
   state_from_prim(qR, K, sR);
-  const bool left = hllc_flux(sL, sR, D, K, Fh);
+  const bool left = hllc_flux<EINF>(sL, sR, D, K, Fh);
 #pragma unroll
   for (int c = 0; c < 5; ++c) F[c * sg.sc + id] = Fh[c];
   for (int v = 5; v < nf; ++v) {
@@ -289,9 +289,16 @@ cudaError_t launch_mol_stage(const MolArgs& a, int second, cudaStream_t st, long
       rx.ext[ax] = (ax < dim) ? n[ax] : 1;
     }
     rx.ext[d] = n[d] + 1;
-    if (d == 0) km_flux<0><<<blocks_of(rx.count()), BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[0], a.nf, a.K, rx);
-    if (d == 1) km_flux<1><<<blocks_of(rx.count()), BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[1], a.nf, a.K, rx);
-    if (d == 2) km_flux<2><<<blocks_of(rx.count()), BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[2], a.nf, a.K, rx);
+    const unsigned g = blocks_of(rx.count());
+    if (a.K.einfeldt) {
+      if (d == 0) km_flux<0, true><<<g, BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[0], a.nf, a.K, rx);
+      if (d == 1) km_flux<1, true><<<g, BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[1], a.nf, a.K, rx);
+      if (d == 2) km_flux<2, true><<<g, BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[2], a.nf, a.K, rx);
+    } else {
+      if (d == 0) km_flux<0, false><<<g, BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[0], a.nf, a.K, rx);
+      if (d == 1) km_flux<1, false><<<g, BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[1], a.nf, a.K, rx);
+      if (d == 2) km_flux<2, false><<<g, BLOCK, 0, st>>>(a.sg, a.s.EM, a.s.EP, a.s.F[2], a.nf, a.K, rx);
+    }
     *nl += 3;
   }
   Range ru;

@@ -50,12 +50,13 @@ __device__ __forceinline__ int dir_of(unsigned f1, unsigned f2, long long& t) {
   t = (long long)(b - f) * BLOCK + threadIdx.x;
   return d;
 }
+template <bool EINF>
 __global__ void __launch_bounds__(BLOCK) k_flux1(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
   long long t;
   switch (dir_of(S.first[1], S.first[2], t)) {
-    case 0: flux1_item<0>(sg, s.TP[0], s.TM[0], s.F1[0], K, S.r[0], t); break;
-    case 1: flux1_item<1>(sg, s.TP[1], s.TM[1], s.F1[1], K, S.r[1], t); break;
-    default: flux1_item<2>(sg, s.TP[2], s.TM[2], s.F1[2], K, S.r[2], t); break;
+    case 0: flux1_item<0, EINF>(sg, s.TP[0], s.TM[0], s.F1[0], K, S.r[0], t); break;
+    case 1: flux1_item<1, EINF>(sg, s.TP[1], s.TM[1], s.F1[1], K, S.r[1], t); break;
+    default: flux1_item<2, EINF>(sg, s.TP[2], s.TM[2], s.F1[2], K, S.r[2], t); break;
   }
 }
 
@@ -67,6 +68,7 @@ struct Flux2Sets {
   Range r[6];
   unsigned first[7];
 };
+template <bool EINF>
 __global__ void __launch_bounds__(BLOCK) k_flux2(ScratchGeom sg, Scratch s, StepConst K, Flux2Sets S) {
   const unsigned b = blockIdx.x;
   int c = 0;
@@ -76,12 +78,12 @@ __global__ void __launch_bounds__(BLOCK) k_flux2(ScratchGeom sg, Scratch s, Step
     if (b >= S.first[i]) { c = i; f = S.first[i]; }
   const long long t = (long long)(b - f) * BLOCK + threadIdx.x;
   switch (c) {
-    case 0: flux2_item<0, 1>(sg, s.TP[0], s.TM[0], s.F1[1], s.F2[0][1], K, S.r[0], t); break;
-    case 1: flux2_item<0, 2>(sg, s.TP[0], s.TM[0], s.F1[2], s.F2[0][2], K, S.r[1], t); break;
-    case 2: flux2_item<1, 0>(sg, s.TP[1], s.TM[1], s.F1[0], s.F2[1][0], K, S.r[2], t); break;
-    case 3: flux2_item<1, 2>(sg, s.TP[1], s.TM[1], s.F1[2], s.F2[1][2], K, S.r[3], t); break;
-    case 4: flux2_item<2, 0>(sg, s.TP[2], s.TM[2], s.F1[0], s.F2[2][0], K, S.r[4], t); break;
-    default: flux2_item<2, 1>(sg, s.TP[2], s.TM[2], s.F1[1], s.F2[2][1], K, S.r[5], t); break;
+    case 0: flux2_item<0, 1, EINF>(sg, s.TP[0], s.TM[0], s.F1[1], s.F2[0][1], K, S.r[0], t); break;
+    case 1: flux2_item<0, 2, EINF>(sg, s.TP[0], s.TM[0], s.F1[2], s.F2[0][2], K, S.r[1], t); break;
+    case 2: flux2_item<1, 0, EINF>(sg, s.TP[1], s.TM[1], s.F1[0], s.F2[1][0], K, S.r[2], t); break;
+    case 3: flux2_item<1, 2, EINF>(sg, s.TP[1], s.TM[1], s.F1[2], s.F2[1][2], K, S.r[3], t); break;
+    case 4: flux2_item<2, 0, EINF>(sg, s.TP[2], s.TM[2], s.F1[0], s.F2[2][0], K, S.r[4], t); break;
+    default: flux2_item<2, 1, EINF>(sg, s.TP[2], s.TM[2], s.F1[1], s.F2[2][1], K, S.r[5], t); break;
   }
 }
 
@@ -89,21 +91,21 @@ __global__ void __launch_bounds__(BLOCK) k_flux2(ScratchGeom sg, Scratch s, Step
 // directions, in 2-D from the first fluxes of the other direction
 // (held to 64 registers: the three-operand form otherwise takes 94 and halves
 // the resident warps)
-template <bool THREE>
+template <bool THREE, bool EINF>
 __global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK))
     k_flux3(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
   long long t;
   switch (dir_of(S.first[1], S.first[2], t)) {
     case 0:
-      if (THREE) flux3_item<0>(sg, s.TP[0], s.TM[0], s.F2[1][2], s.F2[2][1], s.F3[0], K, S.r[0], t);
-      else flux3_item<0>(sg, s.TP[0], s.TM[0], s.F1[1], nullptr, s.F3[0], K, S.r[0], t);
+      if (THREE) flux3_item<0, EINF>(sg, s.TP[0], s.TM[0], s.F2[1][2], s.F2[2][1], s.F3[0], K, S.r[0], t);
+      else flux3_item<0, EINF>(sg, s.TP[0], s.TM[0], s.F1[1], nullptr, s.F3[0], K, S.r[0], t);
       break;
     case 1:
-      if (THREE) flux3_item<1>(sg, s.TP[1], s.TM[1], s.F2[0][2], s.F2[2][0], s.F3[1], K, S.r[1], t);
-      else flux3_item<1>(sg, s.TP[1], s.TM[1], s.F1[0], nullptr, s.F3[1], K, S.r[1], t);
+      if (THREE) flux3_item<1, EINF>(sg, s.TP[1], s.TM[1], s.F2[0][2], s.F2[2][0], s.F3[1], K, S.r[1], t);
+      else flux3_item<1, EINF>(sg, s.TP[1], s.TM[1], s.F1[0], nullptr, s.F3[1], K, S.r[1], t);
       break;
     default:
-      if (THREE) flux3_item<2>(sg, s.TP[2], s.TM[2], s.F2[0][1], s.F2[1][0], s.F3[2], K, S.r[2], t);
+      if (THREE) flux3_item<2, EINF>(sg, s.TP[2], s.TM[2], s.F2[0][1], s.F2[1][0], s.F3[2], K, S.r[2], t);
       break;
   }
 }
@@ -170,7 +172,8 @@ int launch_flux1_all(const StepArgs& a, const Range& rt, unsigned dirs, cudaStre
     S.r[d].ext[d] = n[d] + 1;
     S.first[d + 1] = S.first[d] + (((dirs >> d) & 1u) ? blocks_for(S.r[d].count()) : 0u);
   }
-  k_flux1<<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  if (a.K.einfeldt) k_flux1<true><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  else k_flux1<false><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   return 1;
 }
 
@@ -187,8 +190,14 @@ int launch_flux3_all(const StepArgs& a, int dim, int zlo, int zext, cudaStream_t
     r.ext[d] += 1;
     S.first[d + 1] = S.first[d] + ((d < dim) ? blocks_for(r.count()) : 0u);
   }
-  if (dim == 3) k_flux3<true><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
-  else k_flux3<false><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  const unsigned g = S.first[3];
+  if (a.K.einfeldt) {
+    if (dim == 3) k_flux3<true, true><<<g, BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+    else k_flux3<false, true><<<g, BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  } else {
+    if (dim == 3) k_flux3<true, false><<<g, BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+    else k_flux3<false, false><<<g, BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  }
   return 1;
 }
 
@@ -209,7 +218,8 @@ int launch_flux2_all(const StepArgs& a, cudaStream_t st) {
       S.first[c + 1] = S.first[c] + blocks_for(r.count());
       ++c;
     }
-  k_flux2<<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  if (a.K.einfeldt) k_flux2<true><<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  else k_flux2<false><<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   return 1;
 }
 
