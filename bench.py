@@ -40,9 +40,9 @@ LAUNCHES_PER_STEP_3D = {"prim": 2, "trace": 3, "flux1": 1, "flux2": 1, "flux3": 
 FP64_PEAK_GFLOPS = 148 * 2 * 2 * 2.032
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per unit of the dominant stage from one ncu
-# capture of the current kernel (k_flux2<0,1>, Sedov 96^3: 135.1 MB for
-# 912,576 solves), scaled to a launch by its units.
-DRAM_BYTES_PER_UNIT = {"flux2": 148.1}
+# capture of the current kernel (k_flux2, all six sets in one launch, Sedov
+# 96^3: 921.2 MB for 5,475,456 solves), scaled to a launch by its units.
+DRAM_BYTES_PER_UNIT = {"flux2": 168.2}
 
 
 def units_per_step(n):
