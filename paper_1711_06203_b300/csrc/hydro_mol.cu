@@ -15,8 +15,12 @@
 //   km_prim      grown box: stage state -> (rho, u, v, w, p, X_k); ghosts by
 //                boundary map (prefilled layers from the caller's input box)
 //   km_flat<d>   zones [-1, n_d] x interior: flattening coefficient
-//   km_recon<d>  one thread per (variable, pencil segment): a sliding-window
-//                sweep forms each slope, interface value and limited edge once
+//   km_recon<d>  (y, z) one thread per (variable, pencil segment): a
+//                sliding-window sweep forms each slope, interface value and
+//                limited edge once
+//   km_recon_x   (x) one warp per (variable, row, run of 28 zones), lanes
+//                along x: the same operations per zone, neighbours' values
+//                by warp shuffles, loads and stores coalesced
 //   km_flux<d>   faces [0, n_d] x interior: HLLC + species upwinding (per wave-speed choice)
 //   km_update    interior: flux differences x, y, z, source, stage combination,
 //                bad-state check and CFL partials (second stage)
@@ -37,6 +41,7 @@ namespace hydro {
 namespace {
 
 constexpr int MOL_SEG = 16;  // zones per reconstruction sweep segment
+constexpr int XRUN = 28;     // zones per warp of the x reconstruction (32 lanes less a 2-zone halo each side)
 
 struct MolScratch {
   double* Q;     // nf fields
@@ -116,7 +121,7 @@ __global__ void __launch_bounds__(BLOCK) km_flat(ScratchGeom sg, const double* _
   CHI[id] = chi;
 }
 
-// ---- limited PPM edges of one variable along a pencil segment
+// ---- limited PPM edges of one variable along a pencil segment (y and z sweeps)
 // item t: t1 (fastest), t2, segment, variable
 template <int D>
 __global__ void __launch_bounds__(BLOCK) km_recon(ScratchGeom sg, const double* __restrict__ Q,
@@ -169,6 +174,53 @@ __global__ void __launch_bounds__(BLOCK) km_recon(ScratchGeom sg, const double* 
     ap1 = ap2;
     s0 = s1;
     fm = fp;
+  }
+}
+
+// ---- limited PPM edges along x with lanes along x.  A thread per pencil
+// (km_recon<0>) makes every load of a warp hit 32 rows; here warp w of a
+// (variable, row) takes output zones [z0, z0 + XRUN) and lane l holds zone
+// z0 - 2 + l.  Each lane forms its zone's left difference, slope, high
+// interface value and limited edges; a lane takes its neighbours' values by
+// shuffle (a zone's slope needs a_{m-1}, a_{m+1} and the next difference,
+// its interface m + 1/2 the next slope, its low interface the previous
+// lane's high one).  Lanes 2..29 hold complete stencils and store.  The
+// operations and operands per zone are those of the sweep, so the edges are
+// bitwise the same.
+__global__ void __launch_bounds__(BLOCK) km_recon_x(ScratchGeom sg, const double* __restrict__ Q,
+                                                    const double* __restrict__ CHI, double* __restrict__ EM,
+                                                    double* __restrict__ EP, int n1, int n2, int nd, int nrun,
+                                                    int nf) {
+  const long long w = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;  // the same for the whole warp
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)n1 * n2 * nrun * nf) return;
+  long long r = w;
+  const int run = (int)(r % nrun);
+  r /= nrun;
+  const int j = (int)(r % n1);
+  r /= n1;
+  const int k = (int)(r % n2);
+  const int v = (int)(r / n2);
+  const int z0 = -1 + run * XRUN;        // first output zone; outputs are zones [-1, nd]
+  const int m = z0 - 2 + lane;           // this lane's zone
+  const int mr = min(m, nd + 3);         // lanes past the grown box read its last zone (never stored)
+  const long long id = sg.id(mr, j, k);
+  const double a = Q[(long long)v * sg.sc + id];
+  const double chi = CHI[id];
+  const unsigned all = 0xffffffffu;
+  const double am1 = __shfl_up_sync(all, a, 1), ap1 = __shfl_down_sync(all, a, 1);
+  const double dl = a - am1;                              // a_m - a_{m-1}
+  const double dr = __shfl_down_sync(all, dl, 1);         // a_{m+1} - a_m
+  const double s0 = mc_slope_d(dl, dr, am1, ap1);         // slope of zone m
+  const double s1 = __shfl_down_sync(all, s0, 1);         // slope of zone m + 1
+  const double fp = face_value(a, ap1, s0, s1);           // interface m + 1/2
+  const double fm = __shfl_up_sync(all, fp, 1);           // interface m - 1/2
+  if (lane >= 2 && lane < 2 + XRUN && m <= nd) {
+    double lo, hi, a6;
+    ppm_limit(a, fm, fp, chi, lo, hi, a6);
+    const long long o = (long long)v * sg.sc + id;
+    EM[o] = lo;
+    EP[o] = hi;
   }
 }
 
@@ -280,7 +332,11 @@ cudaError_t launch_mol_stage(const MolArgs& a, int second, cudaStream_t st, long
     const int n1 = n[t1], n2 = (t2 < dim) ? n[t2] : 1;
     const int nseg = (n[d] + 2 + MOL_SEG - 1) / MOL_SEG;
     const long long items = (long long)n1 * n2 * nseg * a.nf;
-    if (d == 0) km_recon<0><<<blocks_of(items), BLOCK, 0, st>>>(a.sg, a.s.Q, a.s.CHI, a.s.EM, a.s.EP, n1, n2, n[0], nseg, a.nf);
+    if (d == 0) {
+      const int nrun = (n[0] + 2 + XRUN - 1) / XRUN;
+      const long long threads = (long long)n1 * n2 * nrun * a.nf * 32;
+      km_recon_x<<<blocks_of(threads), BLOCK, 0, st>>>(a.sg, a.s.Q, a.s.CHI, a.s.EM, a.s.EP, n1, n2, n[0], nrun, a.nf);
+    }
     if (d == 1) km_recon<1><<<blocks_of(items), BLOCK, 0, st>>>(a.sg, a.s.Q, a.s.CHI, a.s.EM, a.s.EP, n1, n2, n[1], nseg, a.nf);
     if (d == 2) km_recon<2><<<blocks_of(items), BLOCK, 0, st>>>(a.sg, a.s.Q, a.s.CHI, a.s.EM, a.s.EP, n1, n2, n[2], nseg, a.nf);
     Range rx;  // faces [0, n_d] along d, interior transverse
