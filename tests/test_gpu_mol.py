@@ -37,7 +37,7 @@ def _rel(a, b):
 
 
 SEEDS = {"random3d_periodic": 31, "sod2d_species": 32, "mixed3d_gravity_13": 33, "sedov24_13": 34,
-         "einfeldt_noflat_2d": 35, "hydro_only": 36}
+         "einfeldt_noflat_2d": 35, "hydro_only": 36, "wide_x_3d": 37}
 
 
 def _case(name):
@@ -68,12 +68,19 @@ def _case(name):
         n, dim, bc, kw = (10, 12, 9), 3, R, {}
         U = inputs.random_box(rng, n, 3)
         nspec = 0
+    elif name == "wide_x_3d":
+        # 63 x-zones (-1..61) span three 28-zone warps of the x reconstruction, the last one ragged
+        n, dim = (61, 7, 6), 3
+        bc = ((PER, PER), (R, O), (O, R))
+        kw = {}
+        U = inputs.random_box(rng, n, 3)
+        nspec = 2
     X = inputs.species_fractions(rng, U.shape[1:], max(nspec, 1))[:nspec]
     return inputs.with_species(U, X), n, dim, bc, kw, nspec
 
 
 CASES = ["random3d_periodic", "sod2d_species", "mixed3d_gravity_13", "sedov24_13", "einfeldt_noflat_2d",
-         "hydro_only"]
+         "hydro_only", "wide_x_3d"]
 
 
 def _gpu(U, n, dim, bc, kw, nspec, dts, variant, dx=0.05):
