@@ -16,6 +16,7 @@ host cores.  Under torchrun each rank advances its own box (weak scaling, no
 collective on the data path); rank 0 prints the line.
 """
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -82,11 +83,17 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    """nvidia-smi clock / throttle-reason samples while the timed region runs.
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Sampling starts before the timed region (start(), which waits for the
+    first sample), every 50 ms; stop(t0, t1) keeps the samples whose
+    timestamps fall inside the timed region's wall-clock window [t0, t1]
+    (time.time() values), widened by one interval on each side."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, gpu_id):
         self.proc = None
@@ -94,38 +101,62 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
-                                         stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def wait_first(self, timeout_s=5.0):
+        """Block until nvidia-smi has written its first sample (or timeout)."""
+        t_end = time.perf_counter() + timeout_s
+        while self.proc and time.perf_counter() < t_end:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
+
+    @staticmethod
+    def _when(stamp):
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t0=None, t1=None):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(2 * self.INTERVAL_MS / 1e3)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                rows.append((self._when(parts[0]), float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for name, v in zip(names, parts[4:8]):
+        os.unlink(self.path)
+        pad = self.INTERVAL_MS / 1e3
+        inside = [r for r in rows if t0 is not None and r[0] is not None and t0 - pad <= r[0] <= t1 + pad]
+        window = "timed region" if inside else "whole run (no sample fell inside the timed region)"
+        use = inside or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in use:
+            for name, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        os.unlink(self.path)
+        sm = [r[1] for r in use]
+        mx = [r[2] for r in use]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window,
+                "interval_ms": self.INTERVAL_MS}
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -766,6 +797,9 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(gpu_id) if rank == 0 else None
+    if sampler:
+        sampler.wait_first()
+    t_wall0 = time.time()
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()  # evict L2 between timed steps (outside the events)
@@ -775,7 +809,8 @@ def run_ours(args):
         a, b = b, a
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
-    clocks = sampler.stop() if sampler else None
+    t_wall1 = time.time()
+    clocks = sampler.stop(t_wall0, t_wall1) if sampler else None
     if dist:
         dist.barrier()
     launches = ctx.hydro_ctx_launches() - launches0
