@@ -50,32 +50,37 @@ def _lib(counting=False):
     name = "liboracle_count.so" if counting else "liboracle.so"
     if name not in _libs:
         out = _build.build()
-        lib = ctypes.CDLL(os.path.join(out, name))
-        P = ctypes.POINTER(Params)
-        lib.oracle_grown_size.argtypes = [P]
-        lib.oracle_grown_size.restype = ctypes.c_longlong
-        lib.oracle_fill_ghosts.argtypes = [_D, P]
-        lib.oracle_dt.argtypes = [_D, P, _D]
-        lib.oracle_step.argtypes = [_D, _D, P, ctypes.c_double, ctypes.POINTER(Debug)]
-        lib.oracle_mol_step.argtypes = [_D, _D, P, ctypes.c_int, ctypes.c_double]
-        lib.oracle_hllc.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, _D]
-        lib.oracle_wave_speeds.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
-        lib.oracle_ppm_parabola.argtypes = [_D, ctypes.c_double, _D]
-        lib.oracle_flatten.argtypes = [_D, _D, ctypes.c_double]
-        lib.oracle_flatten.restype = ctypes.c_double
-        lib.oracle_integ.argtypes = [_D, ctypes.c_double, ctypes.c_int]
-        lib.oracle_integ.restype = ctypes.c_double
-        lib.oracle_trace_lines.argtypes = [_D, ctypes.c_int, P, ctypes.c_double, ctypes.c_double, _D, _D]
-        lib.oracle_cons_to_prim.argtypes = [_D, P, _D, ctypes.POINTER(ctypes.c_int)]
-        lib.oracle_prim_to_cons.argtypes = [_D, ctypes.c_double, _D]
-        lib.oracle_exact_star.argtypes = [_D, _D, ctypes.c_double, _D]
-        lib.oracle_exact_sample.argtypes = [_D, _D, ctypes.c_double, _D, ctypes.c_int, _D]
-        if counting:
-            lib.oracle_tally_reset.argtypes = []
-            lib.oracle_tally_get.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
-            lib.oracle_tally_stages.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
-        _libs[name] = lib
+        _libs[name] = load(os.path.join(out, name), counting)
     return _libs[name]
+
+
+def load(path, counting=False):
+    """Open an oracle shared library at `path` and declare its entry points."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER(Params)
+    lib.oracle_grown_size.argtypes = [P]
+    lib.oracle_grown_size.restype = ctypes.c_longlong
+    lib.oracle_fill_ghosts.argtypes = [_D, P]
+    lib.oracle_dt.argtypes = [_D, P, _D]
+    lib.oracle_step.argtypes = [_D, _D, P, ctypes.c_double, ctypes.POINTER(Debug)]
+    lib.oracle_mol_step.argtypes = [_D, _D, P, ctypes.c_int, ctypes.c_double]
+    lib.oracle_hllc.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, _D]
+    lib.oracle_wave_speeds.argtypes = [_D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
+    lib.oracle_ppm_parabola.argtypes = [_D, ctypes.c_double, _D]
+    lib.oracle_flatten.argtypes = [_D, _D, ctypes.c_double]
+    lib.oracle_flatten.restype = ctypes.c_double
+    lib.oracle_integ.argtypes = [_D, ctypes.c_double, ctypes.c_int]
+    lib.oracle_integ.restype = ctypes.c_double
+    lib.oracle_trace_lines.argtypes = [_D, ctypes.c_int, P, ctypes.c_double, ctypes.c_double, _D, _D]
+    lib.oracle_cons_to_prim.argtypes = [_D, P, _D, ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_prim_to_cons.argtypes = [_D, ctypes.c_double, _D]
+    lib.oracle_exact_star.argtypes = [_D, _D, ctypes.c_double, _D]
+    lib.oracle_exact_sample.argtypes = [_D, _D, ctypes.c_double, _D, ctypes.c_int, _D]
+    if counting:
+        lib.oracle_tally_reset.argtypes = []
+        lib.oracle_tally_get.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        lib.oracle_tally_stages.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+    return lib
 
 
 def _ptr(a):

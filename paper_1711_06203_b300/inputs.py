@@ -119,6 +119,43 @@ def stratified(n, dim=3, gamma=5.0 / 3.0, g=1.0, H=0.1, perturb=0.0, rng=None):
     return conserved(rho, zero, zero, zero, p, gamma)
 
 
+def uniform_flow(rho, vel, p, dim, gamma):
+    """A density field carried by a uniform velocity `vel` at uniform pressure
+    `p` (w = 0 in 2-D)."""
+    z = np.zeros_like(rho)
+    w = vel[2] if dim == 3 else 0.0
+    return conserved(rho, vel[0] + z, vel[1] + z, w + z, p + z, gamma)
+
+
+def product_profile(n, dim, dx, vel, t=0.0, amp=0.3, gamma=1.4):
+    """rho = 2 + amp * prod_a (x_a - vel_a t + 1) over the active axes (bilinear
+    in 2-D, trilinear in 3-D), uniform velocity `vel` and p = 1, sampled at
+    zone centres (equal to the zone averages: the profile is linear in each
+    coordinate separately).  At t > 0 it is the exact solution translated by
+    vel * t."""
+    X = zone_centres(n, dim, dx)
+    r = 1.0
+    for a in range(dim):
+        r = r * (X[a] - vel[a] * t + 1.0)
+    return uniform_flow(2.0 + amp * r, vel, 1.0, dim, gamma)
+
+
+def translation_box(rng, n, dim, dx, dt, signs, gamma=1.4, sigma_rho=0.5):
+    """Random density rho ~ LogNormal(0, sigma_rho) on every zone (ghosts
+    included), carried at uniform pressure 1 by the uniform velocity whose
+    component a is signs[a] * dx[a] / dt: in one step of length dt the exact
+    solution moves every zone average by exactly one zone along each active
+    axis.  Returns (U, U_translated), the second the exact answer on the
+    interior."""
+    shape = grown_shape(n, dim)
+    rho = rng.lognormal(0.0, sigma_rho, shape)
+    vel = tuple(signs[a] * dx[a] / dt for a in range(3))
+    moved = rho
+    for a in range(dim):
+        moved = np.roll(moved, signs[a], axis=2 - a)
+    return uniform_flow(rho, vel, 1.0, dim, gamma), uniform_flow(moved, vel, 1.0, dim, gamma)
+
+
 LEVEL_SIDES = (16, 24, 32, 48, 64)
 
 

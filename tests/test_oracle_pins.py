@@ -16,7 +16,11 @@ wrong sign or index, a transposed operand) fails at least one of them:
   * the whole step: Sod vs the exact solution, Sedov self-similar scaling with
     xi0 from the similarity ODE, conservation on periodic boxes, uniform-state
     preservation, dimensional reduction, mirror symmetry, free fall under
-    constant gravity, hydrostatic balance of a stratified atmosphere.
+    constant gravity, hydrostatic balance of a stratified atmosphere;
+  * corner transport: a product profile advected obliquely and a random
+    density moved one zone per axis at unit Courant number, both exact
+    solutions, with planted mistakes in the transverse corrections that
+    each fail one of them.
 """
 import os
 
@@ -669,3 +673,106 @@ def test_flux_form_gravity_balances_potential_energy(einfeldt):
         errs[flux_form] = abs(change - boundary) / scale
     assert errs[True] <= 1e-14, errs
     assert errs[False] > 1e3 * max(errs[True], 1e-17), errs
+
+
+# ---------------------------------------------------------------- corner transport (CTU transverse terms)
+# Uniform velocity and pressure reduce the Euler equations to advection of the
+# density (a contact wave), whose exact solution is a translation.  Two exact
+# solutions of that problem fix every coefficient and every index of the
+# corner-transport corrections (Sec. 3.2, unsplit PPM):
+#   * a profile that is linear in each coordinate separately (bilinear in 2-D,
+#     trilinear in 3-D).  Averaging the exact x-flux over the step gives
+#     X [Y Z - (b Z + c Y)/2 + b c / 3] + (terms that do not depend on X and
+#     cancel in the x-difference), with b, c the transverse Courant lengths:
+#     the 1/2 of the final correction and, in 3-D, the 1/3 of the intermediate
+#     one composed with the final 1/2 (1/2 * 1/3 twice) are the only weights
+#     that reproduce it, so the translated zone averages come out to round-off;
+#   * unit Courant number along every axis: the exact step moves every zone
+#     average by one zone along each axis.  The upwind x-state of a 3-D CTU
+#     step at Courant number 1 is the weighted sum 1/3 (own zone) + 1/6 +
+#     1/6 (transverse neighbours) + 1/3 (the diagonal one), which is exactly
+#     the fraction of the face's swept volume in each zone; a wrong weight, a
+#     wrong transverse pair or the other zone's transverse faces breaks it for
+#     a random density.
+CORNER_N = {3: (12, 10, 8), 2: (12, 10, 1)}
+CORNER_VEL = (0.7, 0.4, -0.3)
+
+
+def _interior_rel_err(A, B, dim):
+    I = I3 if dim == 3 else I2
+    a, b = A[I].reshape(5, -1), B[I].reshape(5, -1)
+    den = np.abs(b).max(axis=1)
+    return float((np.abs(a - b).max(axis=1) / np.where(den > 0, den, 1.0)).max())
+
+
+def product_profile_error(dim):
+    """Max relative interior error of one CFL step of the product profile
+    against its exact translation."""
+    n, dx = CORNER_N[dim], (1 / 12, 1 / 12, 1 / 12)
+    U0 = inputs.product_profile(n, dim, dx, CORNER_VEL)
+    P = oracle.params(dim, n, dx=dx, bc=oracle.BC_PREFILLED, gamma=1.4)
+    d, rc = oracle.dt(U0, P)
+    U1, rc1 = oracle.step(U0, P, d)
+    if rc or rc1:
+        return float("inf")
+    return _interior_rel_err(U1, inputs.product_profile(n, dim, dx, CORNER_VEL, t=d), dim)
+
+
+def unit_courant_error(dim, signs):
+    """Max relative interior error of one unit-Courant step of a random density
+    against the exact one-zone translation."""
+    n, dx, dt = CORNER_N[dim], (1 / 12, 1 / 10, 1 / 8), 0.05
+    U0, want = inputs.translation_box(np.random.default_rng(17), n, dim, dx, dt, signs)
+    P = oracle.params(dim, n, dx=dx, bc=oracle.BC_PREFILLED, gamma=1.4)
+    U1, rc = oracle.step(U0, P, dt)
+    return float("inf") if rc else _interior_rel_err(U1, want, dim)
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_product_profile_is_advected_exactly(dim):
+    assert product_profile_error(dim) <= 1e-13
+
+
+@pytest.mark.parametrize("dim,signs", [(3, (1, 1, 1)), (3, (1, -1, 1)), (3, (-1, 1, -1)), (2, (1, 1, 1)),
+                                       (2, (-1, 1, 1))])
+def test_unit_courant_step_translates_by_one_zone(dim, signs):
+    assert unit_courant_error(dim, signs) <= 1e-13
+
+
+# each edit is a plausible slip in the corner-transport code; every one must
+# fail at least one of the two exact solutions above (checked in 3-D and 2-D)
+CORNER_MISTAKES = {
+    "intermediate coefficient 1/2 instead of 1/3":
+        [("real coef = dtdx[t] * THIRD;", "real coef = dtdx[t] * 0.5;")],
+    "intermediate correction dropped":
+        [("real coef = dtdx[t] * THIRD;", "real coef = dtdx[t] * 0.0;")],
+    "intermediate correction with the wrong sign":
+        [("real coef = dtdx[t] * THIRD;", "real coef = -dtdx[t] * THIRD;")],
+    "intermediate correction from the other zone's transverse faces":
+        [("F1[t].get(zl + g.str[t], a); F1[t].get(zl, b);", "F1[t].get(id + g.str[t], a); F1[t].get(id, b);")],
+    "final 3-D correction with F^{t|d} instead of F^{t1|t2}":
+        [("F2[t1][t2].get(z + g.str[t1], ah); F2[t1][t2].get(z, al);",
+          "F2[t1][d].get(z + g.str[t1], ah); F2[t1][d].get(z, al);"),
+         ("F2[t2][t1].get(z + g.str[t2], bh); F2[t2][t1].get(z, bl);",
+          "F2[t2][d].get(z + g.str[t2], bh); F2[t2][d].get(z, bl);")],
+    "final 3-D coefficient 1/3 instead of 1/2":
+        [("correct_state(q, *P, K, 0.5 * dtdx[t1], ah, al, 0.5 * dtdx[t2], bh, bl, s);",
+          "correct_state(q, *P, K, THIRD * dtdx[t1], ah, al, THIRD * dtdx[t2], bh, bl, s);")],
+    "final 2-D coefficient 1/3 instead of 1/2":
+        [("correct_state(q, *P, K, 0.5 * dtdx[t1], ah, al, 0.0, nullptr, nullptr, s);",
+          "correct_state(q, *P, K, THIRD * dtdx[t1], ah, al, 0.0, nullptr, nullptr, s);")],
+    "final 2-D correction dropped":
+        [("correct_state(q, *P, K, 0.5 * dtdx[t1], ah, al, 0.0, nullptr, nullptr, s);",
+          "correct_state(q, *P, K, 0.0 * dtdx[t1], ah, al, 0.0, nullptr, nullptr, s);")],
+    "final correction from the other zone's transverse faces":
+        [("long z = side ? id : zl;", "long z = side ? zl : id;")],
+}
+
+
+@pytest.mark.parametrize("name", list(CORNER_MISTAKES))
+def test_planted_corner_transport_mistakes_fail(name, tmp_path):
+    from oracle_variants import planted
+    dim = 2 if "2-D" in name else 3
+    with planted(tmp_path, CORNER_MISTAKES[name]):
+        errs = (product_profile_error(dim), unit_courant_error(dim, (1, -1, 1)))
+    assert max(errs) > 1e-9, (name, errs)
