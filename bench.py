@@ -8,7 +8,11 @@ pure-hydro Sedov problem of the paper's Castro scaling runs (Sec. 4, Fig. 3
 left; Fig. 4 left), at the size one box of such a run holds.  A step is one
 CTU-PPM advance of the whole box (primitive state, tracing, 12 Riemann solves
 per zone, update, CFL reduction) through the library's C ABI with the state
-resident in HBM; the next step uses the CFL step the library returns.
+resident in HBM; the next step uses the CFL step the library returns.  The
+timed run is the whole 200-step problem from the initial state (--steps);
+the warm-up steps run on a copy that is then reset.  Beside it: the 2-D Sod
+tube (64^2, 50 steps), the batched level, serving, the 512^3 stratified box
+and the other entry points' legs.
 
 --impl ours (default): the CUDA library.  --impl reference: the CPU oracle
 (test infrastructure, not the product) on the same workload, timed on the
@@ -228,21 +232,81 @@ def run_reference(args):
     from paper_1711_06203_b300 import inputs
     n = args.n
     U, _ = inputs.sedov(n)
-    # warm-up steps advance the state; timed steps are bounded so the run ends in minutes
-    _, _, _, U = cpu_oracle_rate(U, n, args.warmup, budget_s=60.0)
+    # warm-up steps from the initial state, then the timed run from the
+    # initial state again, bounded so that it ends in minutes: the oracle's
+    # cost per step barely depends on the state, so the first steps of the
+    # run stand for all of them
+    cpu_oracle_rate(U, n, args.warmup, budget_s=60.0)
     rate, done, t, _ = cpu_oracle_rate(U, n, args.steps, budget_s=150.0)
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": "3D PPM zone-updates/s", "value": rate, "unit": "zone-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"sedov3d_{n}^3", "n": n, "gamma": 1.4, "cfl": 0.5, "bc": "outflow"},
+        "steps_done": done,
+        "config": {"workload": f"sedov3d_{n}^3_{args.steps}steps", "n": n, "gamma": 1.4, "cfl": 0.5,
+                   "bc": "outflow", "steps_from_initial_state": args.steps},
         "cpu_baseline": {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{done} full {n}^3 oracle steps after {args.warmup} warm-up steps"},
+                         "sample": f"the first {done} of the {args.steps} {n}^3 oracle steps from the initial "
+                                   f"state, after {args.warmup} warm-up steps"},
         "e2e": {"value": rate, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_sod(args, dev, stream, steps=50):
+    """2-D Sod shock tube along x on one 64x64 box (4 ghost zones, outflow,
+    gamma 1.4, CFL 0.5): 50 steps from the initial state, each taking the CFL
+    step the library returns, timed with events around the whole run.  The
+    run is repeated: the first pass warms up, the second is reported."""
+    import torch
+
+    from paper_1711_06203_b300 import binding as hb
+    from paper_1711_06203_b300 import inputs
+
+    n = 64
+    U0 = inputs.sod(n, 2, 0)
+    ctx = hb.Context(dev.index)
+    p = hb.params(2, gamma=1.4, cfl=0.5)
+    a0 = torch.from_numpy(U0).to(dev)
+    b = torch.empty_like(a0)
+    box = lambda t: hb.box(t, (n, n, 1), (1.0 / n,) * 3, hb.BC_OUTFLOW)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        a = a0.clone()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        dt, t = ctx.hydro_dt(box(a), p, stream), 0.0
+        for _ in range(steps):
+            t += dt
+            dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    # the same run as a device-resident time loop (hydro_advance_box_steps:
+    # the CFL step stays on the device, two captured one-box graphs)
+    dt_dev = torch.zeros(2, dtype=torch.float64, device=dev)
+    t_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        a = a0.clone()
+        t_dev.zero_()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        dt_dev[0] = ctx.hydro_dt(box(a), p, stream)
+        ctx.hydro_advance_box_steps(box(a), box(b), p, steps, dt_dev, t_dev, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms_loop = e0.elapsed_time(e1) / steps
+    t_loop = t_dev.item()
+    ctx.close()
+    return {"workload": "sod2d_64^2_50steps: Sod along x, 64x64, outflow, gamma 1.4, CFL 0.5", "steps": steps,
+            "t_final": t, "ms_per_step": ms, "zone_updates_per_s": n * n / (ms * 1e-3),
+            "note": "hydro_advance_box per step: launch- and host-sync-bound (each step returns its CFL step "
+                    "to the host)",
+            "device_loop": {"ms_per_step": ms_loop, "zone_updates_per_s": n * n / (ms_loop * 1e-3),
+                            "t_final": t_loop, "call": "hydro_advance_box_steps"}}
 
 
 def bench_batch(args, dev, stream, cpu_sample=False):
@@ -410,37 +474,56 @@ def bench_large(args, dev, stream):
 
     n = 512
     torch.cuda.empty_cache()
-    a = stratified_device(n, dev)
-    b = torch.empty_like(a)
+    a0 = stratified_device(n, dev)
     bc = ((hb.BC_PERIODIC,) * 2, (hb.BC_PERIODIC,) * 2, (hb.BC_REFLECT,) * 2)
     p = hb.params(3, gamma=5.0 / 3.0, cfl=0.5, grav=(0.0, 0.0, -1.0))
-    ctx = hb.Context(dev.index)
 
     def box(t):
         return hb.box(t, (n, n, n), (1.0 / n,) * 3, bc)
 
-    dt = ctx.hydro_dt(box(a), p, stream)
-    for _ in range(3):
-        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
-        a, b = b, a
     steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
-        a, b = b, a
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / steps
-    ctx.close()
-    del a, b
+    runs = {}
+    # the default context (slab-by-slab step under the 16 GiB scratch
+    # limit), then the whole-box step (137 GB of scratch) for comparison
+    for name, limit in (("slabs", None), ("whole_box", 0)):
+        a, b = a0.clone(), torch.empty_like(a0)
+        ctx = hb.Context(dev.index)
+        if limit is not None:
+            ctx.hydro_ctx_set_scratch_limit(limit)
+        dt = ctx.hydro_dt(box(a), p, stream)
+        for _ in range(3):
+            dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+            a, b = b, a
+        torch.cuda.synchronize(dev)
+        used = torch.cuda.mem_get_info(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
+            a, b = b, a
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        ctx.close()
+        del a, b
+        torch.cuda.empty_cache()
+        free_after = torch.cuda.mem_get_info(dev)[0]
+        # device memory the context held: what closing it and dropping the
+        # two state buffers gave back, less the two states
+        state_bytes = a0.numel() * a0.element_size()
+        runs[name] = {"ms_per_step": ms, "zone_updates_per_s": n ** 3 / (ms * 1e-3),
+                      "scratch_gb": (free_after - used[0] - 2 * state_bytes) / 1e9}
+    del a0
     torch.cuda.empty_cache()
+    ms = runs["slabs"]["ms_per_step"]
     hbm = algorithmic_bytes_per_step(n) / (ms * 1e-3) / 1e9
     peak = measured_peaks().get("hbm_gbs", 6400.0)
     return {"workload": "512^3 stratified atmosphere, g = -1 in z, 1e-3 pressure perturbations, periodic x/y, "
                         "reflecting z", "steps_timed": steps, "ms_per_step": ms,
-            "zone_updates_per_s": n ** 3 / (ms * 1e-3), "hbm_algorithmic_gbs": hbm, "hbm_peak_gbs": peak,
+            "zone_updates_per_s": n ** 3 / (ms * 1e-3), "scratch_gb": runs["slabs"]["scratch_gb"],
+            "whole_box": runs["whole_box"],
+            "slab_over_whole_time": ms / runs["whole_box"]["ms_per_step"],
+            "hbm_algorithmic_gbs": hbm, "hbm_peak_gbs": peak,
             "hbm_frac": hbm / peak, "l2": "inputs far larger than L2 (5.6 GB per state)"}
 
 
@@ -717,7 +800,12 @@ def bench_serve(args, dev, zone_rate):
     """Serving stream: a seeded prefix of independent 3-D problems (Sod,
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
     process at 0.7 x the measured plain capacity (requests/s), served by the
-    continuous-batching server with state resident on the device."""
+    continuous-batching server with state resident on the device, under the
+    scheduling policy --serve-policy (default: response ratio, 10 ms
+    quantum).  Beside the latency percentiles: the slowdown of each request
+    (its latency over its own steps' cost alone on the GPU, at the server's
+    measured cost per zone), and the host time spent choosing sets and
+    enqueueing."""
     import numpy as np
     import torch
 
@@ -732,6 +820,8 @@ def bench_serve(args, dev, zone_rate):
     arrivals = inputs.poisson_arrivals(len(reqs), rate, seed=1711)
     torch.cuda.empty_cache()
     srv = hb.Server(dev.index, max_slots=64)
+    policy = hb.SERVE_ALL if args.serve_policy == "all" else hb.SERVE_RESPONSE_RATIO
+    srv.serve_set_policy(policy, args.serve_quantum_ms)
     t0 = time.perf_counter()
     ids = []
     for r, ta in zip(reqs, arrivals):
@@ -744,16 +834,24 @@ def bench_serve(args, dev, zone_rate):
     st = srv.serve_stats()
     srv.close()
     lat = np.array([r["latency_ms"] for r in res])
+    alone = np.array([q["steps"] * st["ms_per_unit"] * (q["n"] + 3) ** 3 for q in reqs])
+    slow = lat / alone
     work = sum(r["zone_updates"] for r in res)
     ok = sum(1 for r in res if r["status"] == 0)
     return {"workload": "prefix of a seeded stream of 3-D Sod/Sedov/two-state requests, sides {32..256}, "
                         "10-100 steps, Poisson arrivals at 0.7 x plain capacity",
+            "policy": args.serve_policy, "quantum_ms": args.serve_quantum_ms if policy else None,
             "requests": len(reqs), "completed_ok": ok, "arrival_rate_per_s": rate,
             "plain_capacity_requests_per_s": capacity, "mean_work_zone_updates": float(mean_work),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99)),
+            "alone_p50_ms": float(np.percentile(alone, 50)), "alone_p99_ms": float(np.percentile(alone, 99)),
             "mean_queue_ms": float(np.mean([r["queue_ms"] for r in res])),
             "zone_updates_per_s": work / wall, "busy_zone_updates_per_s": st["zone_updates"] / (st["busy_ms"] * 1e-3),
-            "iterations": st["iterations"], "wall_s": wall,
+            "iterations": st["iterations"], "box_steps": st["box_steps"],
+            "enqueue_ms_per_iteration": st["enqueue_ms"] / max(1, st["iterations"]),
+            "busy_ms_per_iteration": st["busy_ms"] / max(1, st["iterations"]), "wall_s": wall,
             "hbm_budget_gb": st["hbm_budget"] / 1e9, "scratch_pool_gb": st["hbm_scratch_pool"] / 1e9}
 
 
@@ -776,17 +874,21 @@ def run_ours(args):
     U0, ndep = inputs.sedov(n)
     ctx = hb.Context(local_rank)
     p = hb.params(3, gamma=1.4, cfl=0.5)
-    a = torch.from_numpy(U0).to(dev)
+    a0 = torch.from_numpy(U0).to(dev)  # the initial state, kept for the timed and e2e runs
+    a = a0.clone()
     b = torch.empty_like(a)
     stream = torch.cuda.current_stream(dev)
 
     def box(t):
         return hb.box(t, (n, n, n), dx, hb.BC_OUTFLOW)
 
+    # warm-up: W untimed steps on a copy of the initial state (library
+    # scratch, caches, clocks); the timed run then starts again from t = 0
     dt = ctx.hydro_dt(box(a), p, stream)
     for _ in range(args.warmup):
         dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
         a, b = b, a
+    a.copy_(a0)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     ctx.hydro_ctx_set_profiling(True)
@@ -801,9 +903,13 @@ def run_ours(args):
         sampler.wait_first()
     t_wall0 = time.time()
     wall0 = time.perf_counter()
+    t_sim = 0.0
     for k in range(args.steps):
         flush.zero_()  # evict L2 between timed steps (outside the events)
         ev[k][0].record(stream)
+        if k == 0:
+            dt = ctx.hydro_dt(box(a), p, stream)  # the run's first CFL step, from the initial state
+        t_sim += dt
         dt = ctx.hydro_advance_box(box(a), box(b), p, dt, want_dt_next=True, stream=stream)
         ev[k][1].record(stream)
         a, b = b, a
@@ -820,17 +926,24 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     zones = n ** 3
     value = whole_job_rate(zones, world, args.steps, total_ms)
+    # the same run's steps 6-25: the early blast, when most of the box is at rest
+    early = step_ms[5:25]
+    early_window = ({"steps": "6-25", "ms_per_step": sum(early) / len(early),
+                     "zone_updates_per_s": zones * len(early) / (sum(early) * 1e-3)} if len(early) == 20 else None)
 
-    # end to end through the public host-buffer call: every step copies the
-    # pinned host state in and the result out, inside the events
+    # end to end through the public host-buffer call: the same run from the
+    # initial state, every step copying the pinned host state in and the
+    # result out, inside the events
     h_in = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
     h_in.copy_(a)
     h_out = torch.empty_like(h_in, pin_memory=True)
-    e2e_steps = max(3, min(args.steps, 10))
     ctx.hydro_advance_box_host(box(h_in), box(h_out), p, dt, stream=stream)  # sizes the staging buffers
+    h_in.copy_(a0)
+    e2e_steps = args.steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
+    dt = ctx.hydro_dt(box(a0), p, stream)
     for _ in range(e2e_steps):
         dt = ctx.hydro_advance_box_host(box(h_in), box(h_out), p, dt, want_dt_next=True, stream=stream)
         h_in, h_out = h_out, h_in
@@ -840,6 +953,7 @@ def run_ours(args):
     # outflow faces derive their ghost zones, so only the interior rows of
     # each field's interior z-planes cross the host link, in both directions
     nbytes = 5 * n * n * (n + 8) * a.element_size()
+    sod = bench_sod(args, dev, stream) if world == 1 and not args.no_batch else None
 
     # roofline of the dominant stage (FP64 ALU bound: every stage is)
     units = units_per_step(n)
@@ -885,9 +999,12 @@ def run_ours(args):
         "ms_per_step_median": statistics.median(step_ms), "ms_per_step_range": [min(step_ms), max(step_ms)],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"sedov3d_{n}^3", "n": n, "gamma": 1.4, "cfl": 0.5, "bc": "outflow",
+        "config": {"workload": f"sedov3d_{n}^3_{args.steps}steps", "n": n, "gamma": 1.4, "cfl": 0.5,
+                   "bc": "outflow", "steps_from_initial_state": args.steps, "t_final": t_sim,
                    "deposit_zones": ndep, "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"replica x{world}"},
+        "early_window": early_window,
+        "sod2d": sod,
         "roofline": {"bound": "alu", "kernel": f"{dom} stage ({LAUNCHES_PER_STEP_3D[dom]} launches/step)",
                      "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                      "frac": achieved / FP64_PEAK_GFLOPS,
@@ -924,13 +1041,20 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200, help="timed steps from the initial state (the workload is 200)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=128, help="box side (the workload is 128)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-level leg")
-    ap.add_argument("--serve-requests", type=int, default=24, help="served request prefix (0 skips the leg)")
+    ap.add_argument("--serve-requests", type=int, default=200, help="served request prefix (0 skips the leg)")
+    ap.add_argument("--serve-policy", choices=("ratio", "all"), default="ratio",
+                    help="serving policy: response ratio within a quantum (default) or every request every iteration")
+    ap.add_argument("--serve-quantum-ms", type=float, default=10.0)
+    ap.add_argument("--serve-plain-rate", type=float, default=4.35e8,
+                    help="--serve-only: plain zone-updates/s that sets the arrival rate (0.7 x capacity)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving leg (at the plain rate measured by a short Sedov run) and print it")
     ap.add_argument("--no-large", action="store_true", help="skip the 512^3 large-box leg")
     ap.add_argument("--mol-only", action="store_true",
                     help="run only the method-of-lines leg at --n and print its JSON (for profiling)")
@@ -946,6 +1070,13 @@ def main():
         return run_reference(args)
     if args.batch_profile:
         return batch_profile(args)
+    if args.serve_only:
+        import torch
+
+        dev = torch.device("cuda", 0)
+        with torch.cuda.device(dev):
+            print(json.dumps(bench_serve(args, dev, args.serve_plain_rate)), flush=True)
+        return 0
     if args.mol_only or args.batch_only:
         import torch
 

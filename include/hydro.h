@@ -157,6 +157,26 @@ int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box
                         const hydro_params_t* params, const double* dt_dev, double* dt_next_dev, int* bad_box_host,
                         void* stream);
 
+/* Advance one box nsteps CTU-PPM steps with the time step kept on the device,
+ * with no host synchronisation between steps (paper Sec. 3: the time loop of a
+ * level; here it runs as replays of two captured step graphs, which removes
+ * the per-step host round trip that bounds small boxes).
+ *  - a, b: two device boxes of the same interior size (as for
+ *    hydro_advance_box); step k goes a -> b for even k, b -> a for odd k, so
+ *    the result is in b after an odd number of steps and in a after an even
+ *    one.  No face may be HYDRO_BC_PREFILLED (its ghosts would be stale after
+ *    the first step): HYDRO_EINVAL.
+ *  - dt_dev: device array of 2 doubles; dt_dev[0] holds the first step's dt
+ *    on entry (e.g. from hydro_dt).  Step k takes dt_dev[k % 2] and writes
+ *    the CFL step of its result to dt_dev[(k + 1) % 2], so after the call
+ *    dt_dev[nsteps % 2] is the next step's dt.
+ *  - t_dev: NULL, or a device double to which every step's dt is added.
+ *  - A non-physical state is recorded in the context (hydro_ctx_check).
+ *  - Asynchronous on `stream`; shares the batched step's plans and scratch
+ *    pool (do not overlap with hydro_advance_batch on the same context). */
+int hydro_advance_box_steps(hydro_ctx_t* ctx, const hydro_box_t* a, const hydro_box_t* b,
+                            const hydro_params_t* params, int nsteps, double* dt_dev, double* t_dev, void* stream);
+
 /* Fill every ghost zone of a level of boxes that tile a rectangular domain
  * (paper Sec. 3: the AMR library manages a level's grid data and ghost
  * exchange; Fig. 1: a level of uneven boxes).
@@ -298,12 +318,14 @@ int hydro_ctx_check(hydro_ctx_t* ctx);
 /* ---- serving: continuous batching of independent problems ----
  * A server owns a context, a stream and a scheduler thread.  Requests are
  * admitted in arrival order while their device footprint (two copies of the
- * grown state plus the step's scratch) fits the HBM budget and a slot is
- * free; every scheduler iteration then advances ALL admitted requests by one
- * CTU-PPM step in a single batched step (hydro_advance_batch's engine), each
- * with its own gamma and CFL time step, so requests that arrive while others
- * run join the next iteration.  Finished requests are retired and their memory
- * released.  All serve_* calls are thread-safe. */
+ * grown state, plus the step scratch the scheduling policy can need) fits the
+ * HBM budget and a slot is free.  Every scheduler iteration then advances a
+ * set of admitted requests by one CTU-PPM step in a single batched step
+ * (hydro_advance_batch's engine), each with its own gamma and CFL time step,
+ * so requests that arrive while others run join the next iteration.  Which
+ * requests step is the policy's choice (serve_set_policy).  Finished requests
+ * are retired and their memory released.  All serve_* calls are
+ * thread-safe. */
 enum { HYDRO_PROB_SOD = 0, HYDRO_PROB_SEDOV = 1, HYDRO_PROB_TWO_STATE = 2 };
 
 typedef struct {
@@ -332,9 +354,19 @@ typedef struct {
 typedef struct {
   int queued, active;
   long long admitted, completed, iterations, zone_updates;
-  double busy_ms;           /* time the scheduler spent in batched steps */
+  double busy_ms;           /* time the scheduler spent in batched steps (enqueue + device) */
   size_t hbm_budget, hbm_states, hbm_scratch_pool;
+  long long box_steps;      /* box steps taken (a batched iteration of k boxes counts k) */
+  double enqueue_ms;        /* host time choosing sets, building descriptors, tuning, enqueueing */
+  double ms_per_unit;       /* measured cost of one step per (n+3)^3 zones, ms */
 } hydro_serve_stats_t;
+
+/* Scheduling policies (serve_set_policy). */
+enum {
+  HYDRO_SERVE_ALL = 0,            /* every admitted request steps every iteration */
+  HYDRO_SERVE_RESPONSE_RATIO = 1  /* default: highest (waited + remaining work) / remaining work first,
+                                     within a per-iteration GPU-time quantum */
+};
 
 typedef struct serve serve_t;
 
@@ -350,6 +382,19 @@ int serve_submit(serve_t* s, const hydro_request_t* req, uint64_t* id);
 int serve_poll(serve_t* s, uint64_t id, hydro_result_t* res, int timeout_ms);
 /* Snapshot of the server's counters. */
 int serve_stats(serve_t* s, hydro_serve_stats_t* st);
+/* Choose the scheduling policy while the server is idle (nothing queued or
+ * active; else HYDRO_EAGAIN).  HYDRO_SERVE_RESPONSE_RATIO: each iteration
+ * steps the requests in decreasing order of (time since submission +
+ * remaining work) / remaining work, where remaining work = steps left x the
+ * measured cost of one step of that box size, adding requests while the
+ * iteration's estimated GPU time stays within quantum_ms (the first request
+ * always steps); only the stepped set needs step scratch, so the admission
+ * reserve is the largest box's scratch plus what a quantum can hold.
+ * HYDRO_SERVE_ALL: every admitted request steps every iteration (quantum_ms
+ * ignored) and the reserve is the scratch of every admitted request.  The
+ * default is HYDRO_SERVE_RESPONSE_RATIO with a 10 ms quantum.  Either way a
+ * request's result does not depend on the policy or on the other requests. */
+int serve_set_policy(serve_t* s, int policy, double quantum_ms);
 /* Stop the scheduler (the step in flight completes), release everything;
  * requests not yet polled are dropped.  NULL is a no-op. */
 void serve_destroy(serve_t* s);
@@ -369,12 +414,15 @@ void serve_destroy(serve_t* s);
  *    every GPU that loads this library until the process exits, and is
  *    shared by every call on that device: calls
  *    whose work overlaps on the GPU (different streams, or threads) race and
- *    must be serialised by the caller.  Each call clears the state it needs.
+ *    must be serialised by the caller.  Each step resets the scratch state
+ *    it needs; only the bad-state flag carries over (see below).
  *  - Runs on the calling thread's current device.  The first call on a device
  *    looks up the storage's device address (cudaGetSymbolAddress); make that
  *    first call outside any stream capture.
- *  - in, out, params, dt, dt_next_host, stream: as for hydro_advance_box
- *    (a bad state is reported only when dt_next_host is given). */
+ *  - in, out, params, dt, dt_next_host, stream: as for hydro_advance_box.
+ *    A bad state is reported only by a call that passes dt_next_host: the
+ *    device's bad-state flag stays set from the call that raised it until
+ *    such a call returns HYDRO_EBADSTATE, which clears it. */
 #define HYDRO_NOALLOC_MAX_ZONES 64000
 int hydro_advance_box_noalloc(const hydro_box_t* in, const hydro_box_t* out, const hydro_params_t* params,
                               double dt, double* dt_next_host, void* stream);
@@ -398,6 +446,36 @@ int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* cal
 
 /* Total number of CUDA kernels this context has enqueued (host counter). */
 long long hydro_ctx_launches(const hydro_ctx_t* ctx);
+
+/* Scratch limit of a context's single-box step (hydro_advance_box and
+ * hydro_advance_box_host).  The staged step keeps every intermediate of a box
+ * (123 fields of the grown box, 984 bytes per grown zone: 2.5 GB at 128^3,
+ * 137 GB at 512^3).  A 3-D box whose whole-box scratch exceeds `bytes` is
+ * stepped slab by slab along z instead, with scratch for one slab and its
+ * 4-plane halos (balanced slabs of as many planes as fit): the result is
+ * bitwise the same, at the cost of recomputing the few planes where slabs
+ * meet.  0: never slab.  Default 16 GiB.  Takes effect at the next step. */
+int hydro_ctx_set_scratch_limit(hydro_ctx_t* ctx, size_t bytes);
+
+/* ---- boundary fluxes of a box step (paper Sec. 3: a level's coarse-fine
+ * synchronisation corrects coarse zones with the fluxes of the fine level, so
+ * the fluxes through a box's outer faces are part of what a step produces;
+ * they are also the boundary term of its conservation balance) ----
+ * Enable (1) or disable (0) recording: while enabled, every hydro_advance_box
+ * and hydro_advance_box_host call on this context also keeps the final
+ * Riemann fluxes (the ones the update differences) through the 2*dim outer
+ * faces of its box, in context-owned device memory (one extra kernel).
+ * Disabling forgets what was recorded. */
+int hydro_ctx_record_face_fluxes(hydro_ctx_t* ctx, int enable);
+
+/* Copy the recorded fluxes through face `side` (0: the low face, face 0; 1:
+ * the high face, face n[d]) of axis d of the most recent recorded step into
+ * dst (device, caller-owned): 5 fields (mass, momentum x/y/z, energy flux per
+ * unit area and time), each n[t1] x n[t2] values with t1 < t2 the two other
+ * axes and t1 fastest (in 2-D t2 has extent 1).  Enqueued on `stream`, after
+ * the step in stream order.  HYDRO_EINVAL if nothing is recorded (recording
+ * off, or no step since it was enabled) or d is not an axis of that step. */
+int hydro_ctx_face_flux(hydro_ctx_t* ctx, int d, int side, double* dst, void* stream);
 
 /* Diagnostics (no counterpart in the paper): the kernels scale by 2 and by
  * 1/2 on the integer pipe instead of the FP64 multiplier; this runs those two

@@ -96,7 +96,11 @@ class hydro_serve_stats_t(ctypes.Structure):
         ("admitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("iterations", ctypes.c_longlong),
         ("zone_updates", ctypes.c_longlong), ("busy_ms", ctypes.c_double),
         ("hbm_budget", ctypes.c_size_t), ("hbm_states", ctypes.c_size_t), ("hbm_scratch_pool", ctypes.c_size_t),
+        ("box_steps", ctypes.c_longlong), ("enqueue_ms", ctypes.c_double), ("ms_per_unit", ctypes.c_double),
     ]
+
+
+SERVE_ALL, SERVE_RESPONSE_RATIO = 0, 1
 
 
 _LIBS = {}
@@ -142,12 +146,18 @@ def lib(variant="default"):
     L.serve_submit.argtypes = [vp, ctypes.POINTER(hydro_request_t), ctypes.POINTER(ctypes.c_uint64)]
     L.serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hydro_result_t), ctypes.c_int]
     L.serve_stats.argtypes = [vp, ctypes.POINTER(hydro_serve_stats_t)]
+    L.serve_set_policy.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.serve_destroy.argtypes = [vp]
     L.serve_destroy.restype = None
     L.hydro_ctx_set_profiling.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_stage_times.argtypes = [vp, D, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     L.hydro_ctx_launches.argtypes = [vp]
     L.hydro_ctx_launches.restype = ctypes.c_longlong
+    L.hydro_ctx_record_face_fluxes.argtypes = [vp, ctypes.c_int]
+    L.hydro_ctx_set_scratch_limit.argtypes = [vp, ctypes.c_size_t]
+    L.hydro_advance_box_steps.argtypes = [vp, ctypes.POINTER(hydro_box_t), ctypes.POINTER(hydro_box_t),
+                                          ctypes.POINTER(hydro_params_t), ctypes.c_int, vp, vp, vp]
+    L.hydro_ctx_face_flux.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
     _LIBS[variant] = L
     return L
 
@@ -403,6 +413,38 @@ class Context:
     def hydro_ctx_launches(self):
         return self.L.hydro_ctx_launches(self.h)
 
+    def hydro_advance_box_steps(self, a, b, p, nsteps, dt_dev, t_dev=None, stream=None):
+        """nsteps steps alternating a -> b -> a ..., dt kept on the device in
+        dt_dev (2 float64 on the device; dt_dev[0] = first dt); t_dev (1
+        float64 on the device, optional) accumulates the steps' dts."""
+        rc = self.L.hydro_advance_box_steps(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(p), int(nsteps),
+                                            ctypes.c_void_p(dt_dev.data_ptr()),
+                                            ctypes.c_void_p(t_dev.data_ptr()) if t_dev is not None else None,
+                                            _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_advance_box_steps")
+
+    def hydro_ctx_set_scratch_limit(self, nbytes):
+        """Step 3-D boxes whose whole-box scratch exceeds nbytes slab by slab (0: never)."""
+        rc = self.L.hydro_ctx_set_scratch_limit(self.h, int(nbytes))
+        if rc:
+            raise HydroError(rc, "hydro_ctx_set_scratch_limit")
+
+    def hydro_ctx_record_face_fluxes(self, enable=True):
+        rc = self.L.hydro_ctx_record_face_fluxes(self.h, 1 if enable else 0)
+        if rc:
+            raise HydroError(rc, "hydro_ctx_record_face_fluxes")
+
+    def hydro_ctx_face_flux(self, d, side, dst, stream=None):
+        """Copy the recorded final fluxes through face `side` of axis d of the
+        last recorded step into the device tensor dst (5 x n_t2 x n_t1 doubles)."""
+        import torch
+        assert dst.is_cuda and dst.dtype == torch.float64 and dst.is_contiguous()
+        rc = self.L.hydro_ctx_face_flux(self.h, int(d), int(side), ctypes.c_void_p(dst.data_ptr()),
+                                        _stream_handle(stream))
+        if rc:
+            raise HydroError(rc, "hydro_ctx_face_flux")
+
 
 class Server:
     """A serve_t: continuous batching of independent hydro problems on one device."""
@@ -443,6 +485,13 @@ class Server:
         out = {k: getattr(res, k) for k, _ in hydro_result_t._fields_}
         out["state"] = self._bufs.pop(rid, None)
         return out
+
+    def serve_set_policy(self, policy, quantum_ms=10.0):
+        """HYDRO_SERVE_ALL (0) or HYDRO_SERVE_RESPONSE_RATIO (1, the default) with
+        its per-iteration quantum; only while the server is idle."""
+        rc = self.L.serve_set_policy(self.h, int(policy), float(quantum_ms))
+        if rc:
+            raise HydroError(rc, "serve_set_policy")
 
     def serve_stats(self):
         st = hydro_serve_stats_t()

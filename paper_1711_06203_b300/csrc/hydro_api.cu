@@ -13,7 +13,6 @@
 using namespace hydro;
 
 namespace {
-
 // restores the calling thread's current device on scope exit
 struct DeviceGuard {
   int prev = -1;
@@ -167,6 +166,72 @@ int read_flags(hydro_ctx* ctx, cudaStream_t st, DevFlags* host) {
   return HYDRO_OK;
 }
 
+// zones of the transverse interior of a d-face plane
+long long face_area(const int n[3], int dim, int d) {
+  long long A = 1;
+  for (int t = 0; t < dim; ++t)
+    if (t != d) A *= n[t];
+  return A;
+}
+
+
+int ensure_faces(hydro_ctx* ctx, const int n[3], int dim) {
+  size_t need = 0;
+  for (int d = 0; d < dim; ++d) need += 2 * 5 * (size_t)face_area(n, dim, d) * sizeof(double);
+  ctx->faces_dim = 0;
+  if (need > ctx->faces_bytes) {
+    if (ctx->faces) cudaFree(ctx->faces);
+    ctx->faces = nullptr;
+    ctx->faces_bytes = 0;
+    if (cudaMalloc(&ctx->faces, need) != cudaSuccess) {
+      cudaGetLastError();
+      return HYDRO_ENOMEM;
+    }
+    ctx->faces_bytes = need;
+  }
+  return HYDRO_OK;
+}
+
+// interior planes per slab of a 3-D step whose whole-box scratch exceeds
+// the context's limit (balanced slabs of at most the planes the limit
+// holds), or 0 to step the box whole
+int slab_planes(const hydro_ctx* ctx, const ScratchGeom& sg, const int n[3], int dim) {
+  if (dim != 3 || ctx->scratch_limit == 0) return 0;
+  const size_t per_plane = (size_t)sg.sz * SCRATCH_FIELDS * sizeof(double);
+  if ((size_t)sg.sc * SCRATCH_FIELDS * sizeof(double) <= ctx->scratch_limit) return 0;
+  long long tmax = (long long)(ctx->scratch_limit / per_plane) - 2 * NG;
+  if (tmax < 1) tmax = 1;
+  const long long nslab = (n[2] + tmax - 1) / tmax;
+  return (int)((n[2] + nslab - 1) / nslab);
+}
+
+int ensure_slab_cursors(hydro_ctx* ctx, int count) {
+  if (count <= ctx->slab_cursor_cap) return HYDRO_OK;
+  if (ctx->slab_cursors) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return HYDRO_ECUDA;
+    cudaFree(ctx->slab_cursors);
+  }
+  ctx->slab_cursors = nullptr;
+  ctx->slab_cursor_cap = 0;
+  const int cap = std::max(count, 96);
+  if (cudaMalloc(&ctx->slab_cursors, cap * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return HYDRO_ENOMEM;
+  }
+  ctx->slab_cursor_cap = cap;
+  return HYDRO_OK;
+}
+
+int record_face_fluxes(hydro_ctx* ctx, const StepArgs& a, const int n[3], int dim, cudaStream_t st) {
+  int rc = ensure_faces(ctx, n, dim);
+  if (rc) return rc;
+  if (launch_record_faces(a, 0, dim == 3 ? n[2] : 1, ctx->faces, st) != cudaSuccess) return HYDRO_ECUDA;
+  ctx->launches += 1;
+  ctx->faces_dim = dim;
+  for (int t = 0; t < 3; ++t) ctx->faces_n[t] = n[t];
+  return HYDRO_OK;
+}
+
 // after a profiled step: wait for it and add its stage durations
 int collect_stage_times(hydro_ctx* ctx, cudaStream_t st) {
   if (cudaEventSynchronize(ctx->events[NSTAGES]) != cudaSuccess) return HYDRO_ECUDA;
@@ -292,6 +357,8 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
   for (auto& e : ctx->pipe_events)
     if (e) cudaEventDestroy(e);
   if (ctx->pipe_cursors) cudaFree(ctx->pipe_cursors);
+  if (ctx->faces) cudaFree(ctx->faces);
+  if (ctx->slab_cursors) cudaFree(ctx->slab_cursors);
   delete ctx;
 }
 
@@ -348,16 +415,44 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
   a.in = geom_of(in, dim);
   a.out = geom_of(out, dim);
   a.sg = scratch_geom(in->n, dim);
-  size_t bytes = (size_t)a.sg.sc * SCRATCH_FIELDS * sizeof(double);
-  int rc = ensure_scratch(ctx, bytes);
-  if (rc) return rc;
-  a.s = carve_scratch(ctx->scratch, a.sg.sc);
   a.K = step_const(params, in->dx, dt);
   for (int d = 0; d < 3; ++d) a.dx[d] = in->dx[d];
   a.cfl = params->cfl;
   a.flags = ctx->flags;
   a.events = ctx->profiling ? ctx->events : nullptr;
-  if (launch_step(a, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+  const int T = slab_planes(ctx, a.sg, in->n, dim);
+  int rc;
+  if (T > 0) {
+    // scratch larger than the context's limit: slab by slab along z
+    a.sg.sc = a.sg.sz * (T + 2 * NG);
+    const int nslab = (in->n[2] + T - 1) / T;
+    rc = ensure_scratch(ctx, (size_t)a.sg.sc * SCRATCH_FIELDS * sizeof(double));
+    if (rc) return rc;
+    rc = ensure_slab_cursors(ctx, 3 * nslab);
+    if (rc) return rc;
+    a.s = carve_scratch(ctx->scratch, a.sg.sc);
+    double* faces = nullptr;
+    if (ctx->record_faces) {
+      rc = ensure_faces(ctx, in->n, dim);
+      if (rc) return rc;
+      faces = ctx->faces;
+    }
+    if (launch_step_slabs(a, T, ctx->slab_cursors, faces, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+    if (faces) {
+      ctx->faces_dim = dim;
+      for (int t = 0; t < 3; ++t) ctx->faces_n[t] = in->n[t];
+    }
+  } else {
+    size_t bytes = (size_t)a.sg.sc * SCRATCH_FIELDS * sizeof(double);
+    rc = ensure_scratch(ctx, bytes);
+    if (rc) return rc;
+    a.s = carve_scratch(ctx->scratch, a.sg.sc);
+    if (launch_step(a, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+    if (ctx->record_faces) {
+      rc = record_face_fluxes(ctx, a, in->n, dim, st);
+      if (rc) return rc;
+    }
+  }
   if (ctx->profiling) {
     rc = collect_stage_times(ctx, st);
     if (rc) return rc;
@@ -426,7 +521,8 @@ int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_
     return true;
   };
   int rc;
-  if (dim == 3 && !prefilled && !ctx->profiling) {
+  const ScratchGeom whole = scratch_geom(in->n, dim);
+  if (dim == 3 && !prefilled && !ctx->profiling && slab_planes(ctx, whole, in->n, dim) == 0) {
     // 3-D with derived faces: copies overlap the kernels (launch_step_host_piped)
     rc = ensure_pipe(ctx);
     if (rc) return rc;
@@ -458,6 +554,10 @@ int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_
     }
     hp.cursors = ctx->pipe_cursors;
     if (launch_step_host_piped(a, hp, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+    if (ctx->record_faces) {
+      rc = record_face_fluxes(ctx, a, in->n, dim, st);
+      if (rc) return rc;
+    }
   } else {
     if (prefilled) {
       if (cudaMemcpyAsync(din.u, in->u, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HYDRO_ECUDA;
@@ -516,6 +616,34 @@ int hydro_ctx_stage_times(hydro_ctx_t* ctx, double* ms, int nmax, long long* cal
 }
 
 long long hydro_ctx_launches(const hydro_ctx_t* ctx) { return ctx ? ctx->launches : -1; }
+
+int hydro_ctx_set_scratch_limit(hydro_ctx_t* ctx, size_t bytes) {
+  if (!ctx) return HYDRO_EINVAL;
+  ctx->scratch_limit = bytes;
+  return HYDRO_OK;
+}
+
+int hydro_ctx_record_face_fluxes(hydro_ctx_t* ctx, int enable) {
+  if (!ctx) return HYDRO_EINVAL;
+  ctx->record_faces = enable ? 1 : 0;
+  ctx->faces_dim = 0;
+  return HYDRO_OK;
+}
+
+int hydro_ctx_face_flux(hydro_ctx_t* ctx, int d, int side, double* dst, void* stream) {
+  if (!ctx || !dst || side < 0 || side > 1 || ctx->faces_dim == 0 || d < 0 || d >= ctx->faces_dim)
+    return HYDRO_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return HYDRO_ECUDA;
+  long long off = 0;
+  for (int e = 0; e < d; ++e) off += 2 * 5 * face_area(ctx->faces_n, ctx->faces_dim, e);
+  const long long A = 5 * face_area(ctx->faces_n, ctx->faces_dim, d);
+  off += side * A;
+  if (cudaMemcpyAsync(dst, ctx->faces + off, (size_t)A * sizeof(double), cudaMemcpyDeviceToDevice,
+                      static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return HYDRO_ECUDA;
+  return HYDRO_OK;
+}
 
 int hydro_selftest_divsqrt(const double* x, const double* y, double* rcp, double* quo, double* sq, long long n,
                            void* stream) {

@@ -29,6 +29,16 @@ struct hydro_ctx {
   cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
   cudaEvent_t pipe_events[2 * hydro::PIPE_MAX_CHUNKS + 2] = {};
   unsigned long long* pipe_cursors = nullptr;
+  // final fluxes through the outer faces of the last recorded box step
+  int record_faces = 0;
+  double* faces = nullptr;        // 2 * dim face planes, 5 fields each, in (d, side) order
+  size_t faces_bytes = 0;
+  int faces_dim = 0;              // 0: nothing recorded
+  int faces_n[3] = {0, 0, 0};
+  // a 3-D box whose whole-box step scratch exceeds this is stepped slab by slab along z (0: never)
+  size_t scratch_limit = (size_t)16 << 30;
+  unsigned long long* slab_cursors = nullptr;  // work counters of the slab sweeps
+  int slab_cursor_cap = 0;
 };
 
 void hydro_batch_release(hydro_ctx* ctx);
@@ -37,10 +47,14 @@ void hydro_amr_release(hydro_ctx* ctx);
 size_t hydro_batch_pool_bytes(const hydro_ctx* ctx);
 namespace hydro { struct BatchBox; }
 // batched step with per-box params; *plan_boxes (nullable) receives the device
-// descriptors of the plan that ran (valid until the next batched call)
+// descriptors of the plan that ran (valid until the next batched call).
+// direct: enqueue the launches without capturing or caching a plan (for box
+// sets that change from call to call).  *enqueue_ms (nullable): host time
+// from entry until the step was enqueued (plan or descriptors, tuning, launch)
 int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
                     const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,
-                    int* bad_first_host, int* bad_all_host, cudaStream_t st, const hydro::BatchBox** plan_boxes);
+                    int* bad_first_host, int* bad_all_host, cudaStream_t st, const hydro::BatchBox** plan_boxes,
+                    bool direct = false, double* enqueue_ms = nullptr);
 
 namespace hydro {
 bool valid_params(const hydro_params_t* p);
@@ -53,4 +67,8 @@ Scratch carve_scratch(double* base, long long sc);
 int ensure_scratch(hydro_ctx* ctx, size_t bytes);
 int read_flags(hydro_ctx* ctx, cudaStream_t st, DevFlags* host);
 int collect_stage_times(hydro_ctx* ctx, cudaStream_t st);
+int record_face_fluxes(hydro_ctx* ctx, const StepArgs& a, const int n[3], int dim, cudaStream_t st);
+int ensure_faces(hydro_ctx* ctx, const int n[3], int dim);
+int slab_planes(const hydro_ctx* ctx, const ScratchGeom& sg, const int n[3], int dim);
+int ensure_slab_cursors(hydro_ctx* ctx, int count);
 }  // namespace hydro

@@ -166,6 +166,12 @@ struct hydro_batch_state {
   // autotuned number of segments per pencil, keyed by box extent along the sweep
   std::map<int, int> seg_parts;
   bool tune_loaded = false;
+  // direct (uncaptured) launches: descriptors, block tables and flags of the
+  // call in flight, rewritten by every call
+  BatchBox* d_direct_boxes = nullptr;
+  int* d_direct_maps = nullptr;
+  int* d_direct_bad = nullptr;
+  size_t direct_box_cap = 0, direct_map_cap = 0;
 };
 
 namespace {
@@ -200,6 +206,7 @@ void fill_ranges(BatchBox& B, int dim, hydro_batch_state* S) {
     sw.lo1 = rt.lo[t1]; sw.ext1 = rt.ext[t1];
     sw.lo2 = rt.lo[t2]; sw.ext2 = rt.ext[t2];
     sw.nd = n[d];
+    sw.lod = -1;
     sw.seg = (d < dim) ? segment_length(S, n[d]) : TRACE_SEG;
     sw.nseg = (n[d] + 2 + sw.seg - 1) / sw.seg;
     Range r = rt;
@@ -451,8 +458,157 @@ void hydro_batch_release(hydro_ctx* ctx) {
   for (Plan* p : S->plans) destroy_plan(p);
   if (S->scratch) cudaFree(S->scratch);
   if (S->capture) cudaStreamDestroy(S->capture);
+  if (S->d_direct_boxes) cudaFree(S->d_direct_boxes);
+  if (S->d_direct_maps) cudaFree(S->d_direct_maps);
+  if (S->d_direct_bad) cudaFree(S->d_direct_bad);
   delete S;
   ctx->batch = nullptr;
+}
+
+// Device descriptors of every box of a batched call: the scratch pool (one
+// block per box), per-box constants and stage ranges, sweep segments (tuned
+// per size class unless `tune` is off).  Waits for the work queued on `st`.
+static int build_boxes(hydro_ctx* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                       const hydro_params_t* params, int pstride, int dim, bool tune, cudaStream_t st,
+                       std::vector<BatchBox>& boxes) {
+  hydro_batch_state* S = ctx->batch;
+  // the tuner and the pool below write scratch from another stream: let the
+  // work already queued on `st` (which may still read scratch) finish first
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
+  // scratch pool: one scratch block per box
+  std::vector<ScratchGeom> sgs(nbox);
+  size_t total = 0;
+  for (int b = 0; b < nbox; ++b) {
+    sgs[b] = scratch_geom(in[b].n, dim);
+    total += (size_t)sgs[b].sc * SCRATCH_FIELDS;
+  }
+  int rc = ensure_batch_scratch(ctx, total * sizeof(double));
+  if (rc) return rc;
+  boxes.resize(nbox);
+  size_t off = 0;
+  for (int b = 0; b < nbox; ++b) {
+    BatchBox& B = boxes[b];
+    std::memset(&B, 0, sizeof B);
+    B.in = geom_of(&in[b], dim);
+    B.out = geom_of(&out[b], dim);
+    B.sg = sgs[b];
+    B.s = carve_scratch(S->scratch + off, sgs[b].sc);
+    off += (size_t)sgs[b].sc * SCRATCH_FIELDS;
+    const hydro_params_t* pb = &params[(size_t)b * pstride];
+    B.K = step_const(pb, in[b].dx, 1.0);  // dt fields are set on the device every call
+    for (int a = 0; a < 3; ++a) B.dx[a] = in[b].dx[a];
+    B.cfl = pb->cfl;
+  }
+  for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
+  if (tune) {
+    // a throw-away plan holding only the primitive stage, for the tuner's input
+    Plan tmp;
+    std::vector<LaunchSpec> L = {{L_PRIM, 0, 0, 0, 0, 0}};
+    std::vector<int> maps;
+    build_maps(boxes, L, maps);
+    tmp.launches = L;
+    if (cudaMalloc(&tmp.d_boxes, nbox * sizeof(BatchBox)) != cudaSuccess ||
+        cudaMalloc(&tmp.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      if (tmp.d_boxes) cudaFree(tmp.d_boxes);
+      return HYDRO_ENOMEM;
+    }
+    cudaMemcpyAsync(tmp.d_boxes, boxes.data(), nbox * sizeof(BatchBox), cudaMemcpyHostToDevice, S->capture);
+    cudaMemcpyAsync(tmp.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, S->capture);
+    rc = autotune(ctx, boxes, &tmp, dim);
+    cudaStreamSynchronize(S->capture);
+    cudaFree(tmp.d_boxes);
+    cudaFree(tmp.d_maps);
+    if (rc) return rc;
+    for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
+  } else {
+    for (int b = 0; b < nbox; ++b)
+      for (int d = 0; d < 3; ++d) {
+        boxes[b].tr[d].seg = TRACE_SEG;
+        boxes[b].tr[d].nseg = (boxes[b].in.n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
+      }
+  }
+  return HYDRO_OK;
+}
+
+// per-box bad-state flags of the call just enqueued (waits for it) when asked for
+static int read_bad(const int* d_bad, int nbox, int* bad_first_host, int* bad_all_host, cudaStream_t st) {
+  if (!bad_first_host && !bad_all_host) return HYDRO_OK;
+  std::vector<int> tmp;
+  int* bad = bad_all_host;
+  if (!bad) {
+    tmp.resize(nbox);
+    bad = tmp.data();
+  }
+  if (cudaMemcpyAsync(bad, d_bad, nbox * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return HYDRO_ECUDA;
+  int first = -1;
+  for (int b = 0; b < nbox; ++b)
+    if (bad[b]) { first = b; break; }
+  if (bad_first_host) *bad_first_host = first;
+  return first >= 0 ? HYDRO_EBADSTATE : HYDRO_OK;
+}
+
+// The same launch sequence enqueued directly, without a graph or a cached
+// plan: for callers whose set of boxes changes from call to call (a server
+// stepping a different subset of its requests every iteration), where a
+// capture per set would cost more than the launches it saves.  Descriptors
+// and block tables go to device buffers reused by every direct call, so the
+// caller must not overlap two direct calls on one context.
+static int run_direct(hydro_ctx* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
+                      const hydro_params_t* params, int pstride, int dim, bool tune, const double* dt_dev,
+                      double* dt_next_dev, int* bad_first_host, int* bad_all_host, cudaStream_t st,
+                      const hydro::BatchBox** plan_boxes, std::chrono::steady_clock::time_point t_entry,
+                      double* enqueue_ms) {
+  hydro_batch_state* S = ctx->batch;
+  std::vector<BatchBox> boxes;
+  int rc = build_boxes(ctx, in, out, nbox, params, pstride, dim, tune, st, boxes);
+  if (rc) return rc;
+  Plan p;  // launch list and block tables only; the buffers belong to S
+  p.nbox = nbox;
+  p.dim = dim;
+  p.einfeldt = (params[0].flags & HYDRO_FLAG_EINFELDT) != 0;
+  p.launches = launch_list(dim);
+  std::vector<int> maps;
+  build_maps(boxes, p.launches, maps);
+  if ((size_t)nbox > S->direct_box_cap || maps.size() > S->direct_map_cap) {
+    if (S->d_direct_boxes) cudaFree(S->d_direct_boxes);
+    if (S->d_direct_maps) cudaFree(S->d_direct_maps);
+    if (S->d_direct_bad) cudaFree(S->d_direct_bad);
+    S->d_direct_boxes = nullptr;
+    S->d_direct_maps = nullptr;
+    S->d_direct_bad = nullptr;
+    S->direct_box_cap = S->direct_map_cap = 0;
+    const size_t nb = std::max<size_t>(2 * (size_t)nbox, 64), nm = std::max<size_t>(2 * maps.size(), 1 << 16);
+    if (cudaMalloc(&S->d_direct_boxes, nb * sizeof(BatchBox)) != cudaSuccess ||
+        cudaMalloc(&S->d_direct_maps, nm * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&S->d_direct_bad, nb * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return HYDRO_ENOMEM;
+    }
+    S->direct_box_cap = nb;
+    S->direct_map_cap = nm;
+  }
+  // pageable sources: each copy has left the host vector when the call returns
+  if (cudaMemcpyAsync(S->d_direct_boxes, boxes.data(), nbox * sizeof(BatchBox), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(S->d_direct_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return HYDRO_ECUDA;
+  p.d_boxes = S->d_direct_boxes;
+  p.d_maps = S->d_direct_maps;
+  p.d_bad = S->d_direct_bad;
+  const unsigned gb = (unsigned)((nbox + 127) / 128);
+  kb_prepare<<<gb, 128, 0, st>>>(p.d_boxes, nbox, dt_dev);
+  for (auto& l : p.launches) enqueue_launch(&p, l, st);
+  kb_finalize<<<gb, 128, 0, st>>>(p.d_boxes, nbox, dt_next_dev, p.d_bad, ctx->flags);
+  if (cudaGetLastError() != cudaSuccess) return HYDRO_ECUDA;
+  if (enqueue_ms)
+    *enqueue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_entry).count();
+  ctx->launches += (long long)p.launches.size() + 2;
+  if (plan_boxes) *plan_boxes = S->d_direct_boxes;
+  return read_bad(S->d_direct_bad, nbox, bad_first_host, bad_all_host, st);
 }
 
 // Batched step with per-box parameters (params[b * pstride]); all boxes
@@ -460,7 +616,9 @@ void hydro_batch_release(hydro_ctx* ctx) {
 // box's bad-state flag, bad_first_host the first bad box index.
 int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
                     const hydro_params_t* params, int pstride, const double* dt_dev, double* dt_next_dev,
-                    int* bad_first_host, int* bad_all_host, cudaStream_t st, const hydro::BatchBox** plan_boxes) {
+                    int* bad_first_host, int* bad_all_host, cudaStream_t st, const hydro::BatchBox** plan_boxes,
+                    bool direct, double* enqueue_ms) {
+  const auto t_entry = std::chrono::steady_clock::now();
   if (!ctx || !in || !out || nbox < 1 || !dt_dev || !params) return HYDRO_EINVAL;
   const int dim = params[0].dim;
   for (int b = 0; b < nbox; ++b) {
@@ -509,67 +667,16 @@ int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* 
   key = fnv(key, &dt_next_dev, sizeof dt_next_dev);
   const bool tune = !(params0->flags & HYDRO_FLAG_NO_AUTOTUNE);
   key = fnv(key, &tune, sizeof tune);
+  if (direct) return run_direct(ctx, in, out, nbox, params, pstride, dim, tune, dt_dev, dt_next_dev,
+                                bad_first_host, bad_all_host, st, plan_boxes, t_entry, enqueue_ms);
   Plan* plan = nullptr;
   for (Plan* p : S->plans)
     if (p->key == key) plan = p;
 
   if (!plan) {
-    // the tuner and the pool below write scratch from another stream: let the
-    // work already queued on `st` (which may still read scratch) finish first
-    if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
-    // scratch pool: one scratch block per box
-    std::vector<ScratchGeom> sgs(nbox);
-    size_t total = 0;
-    for (int b = 0; b < nbox; ++b) {
-      sgs[b] = scratch_geom(in[b].n, dim);
-      total += (size_t)sgs[b].sc * SCRATCH_FIELDS;
-    }
-    int rc = ensure_batch_scratch(ctx, total * sizeof(double));
+    std::vector<BatchBox> boxes;
+    int rc = build_boxes(ctx, in, out, nbox, params, pstride, dim, tune, st, boxes);
     if (rc) return rc;
-    std::vector<BatchBox> boxes(nbox);
-    size_t off = 0;
-    for (int b = 0; b < nbox; ++b) {
-      BatchBox& B = boxes[b];
-      std::memset(&B, 0, sizeof B);
-      B.in = geom_of(&in[b], dim);
-      B.out = geom_of(&out[b], dim);
-      B.sg = sgs[b];
-      B.s = carve_scratch(S->scratch + off, sgs[b].sc);
-      off += (size_t)sgs[b].sc * SCRATCH_FIELDS;
-      const hydro_params_t* pb = &params[(size_t)b * pstride];
-      B.K = step_const(pb, in[b].dx, 1.0);  // dt fields are set on the device every call
-      for (int a = 0; a < 3; ++a) B.dx[a] = in[b].dx[a];
-      B.cfl = pb->cfl;
-    }
-    for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
-    if (tune) {
-      // a throw-away plan holding only the primitive stage, for the tuner's input
-      Plan tmp;
-      std::vector<LaunchSpec> L = {{L_PRIM, 0, 0, 0, 0, 0}};
-      std::vector<int> maps;
-      build_maps(boxes, L, maps);
-      tmp.launches = L;
-      if (cudaMalloc(&tmp.d_boxes, nbox * sizeof(BatchBox)) != cudaSuccess ||
-          cudaMalloc(&tmp.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        if (tmp.d_boxes) cudaFree(tmp.d_boxes);
-        return HYDRO_ENOMEM;
-      }
-      cudaMemcpyAsync(tmp.d_boxes, boxes.data(), nbox * sizeof(BatchBox), cudaMemcpyHostToDevice, S->capture);
-      cudaMemcpyAsync(tmp.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, S->capture);
-      rc = autotune(ctx, boxes, &tmp, dim);
-      cudaStreamSynchronize(S->capture);
-      cudaFree(tmp.d_boxes);
-      cudaFree(tmp.d_maps);
-      if (rc) return rc;
-      for (int b = 0; b < nbox; ++b) fill_ranges(boxes[b], dim, S);
-    } else {
-      for (int b = 0; b < nbox; ++b)
-        for (int d = 0; d < 3; ++d) {
-          boxes[b].tr[d].seg = TRACE_SEG;
-          boxes[b].tr[d].nseg = (boxes[b].in.n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
-        }
-    }
     plan = new (std::nothrow) Plan();
     if (!plan) return HYDRO_ENOMEM;
     plan->key = key;
@@ -624,31 +731,43 @@ int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* 
   plan->last_use = ++S->clock;
   if (plan_boxes) *plan_boxes = plan->d_boxes;
   if (cudaGraphLaunch(plan->exec, st) != cudaSuccess) return HYDRO_ECUDA;
+  if (enqueue_ms)
+    *enqueue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_entry).count();
   ctx->launches += (long long)plan->launches.size() + 2;
-  if (bad_first_host || bad_all_host) {
-    std::vector<int> tmp;
-    int* bad = bad_all_host;
-    if (!bad) {
-      tmp.resize(nbox);
-      bad = tmp.data();
-    }
-    if (cudaMemcpyAsync(bad, plan->d_bad, nbox * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return HYDRO_ECUDA;
-    int first = -1;
-    for (int b = 0; b < nbox; ++b)
-      if (bad[b]) { first = b; break; }
-    if (bad_first_host) *bad_first_host = first;
-    if (first >= 0) return HYDRO_EBADSTATE;
-  }
-  return HYDRO_OK;
+  return read_bad(plan->d_bad, nbox, bad_first_host, bad_all_host, st);
 }
 
 extern "C" int hydro_advance_batch(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* out, int nbox,
                                    const hydro_params_t* params, const double* dt_dev, double* dt_next_dev,
                                    int* bad_box_host, void* stream) {
   return hydro_batch_run(ctx, in, out, nbox, params, 0, dt_dev, dt_next_dev, bad_box_host, nullptr,
-                         static_cast<cudaStream_t>(stream), nullptr);
+                         static_cast<cudaStream_t>(stream), nullptr, false);
+}
+
+static __global__ void kb_accumulate(double* __restrict__ t, const double* __restrict__ dt) { *t += *dt; }
+
+extern "C" int hydro_advance_box_steps(hydro_ctx_t* ctx, const hydro_box_t* a, const hydro_box_t* b,
+                                       const hydro_params_t* params, int nsteps, double* dt_dev, double* t_dev,
+                                       void* stream) {
+  if (!ctx || !a || !b || !params || !dt_dev || nsteps < 0 || !valid_params(params)) return HYDRO_EINVAL;
+  for (int ax = 0; ax < params->dim; ++ax)
+    for (int side = 0; side < 2; ++side)
+      if (a->bc[ax][side] == HYDRO_BC_PREFILLED || b->bc[ax][side] == HYDRO_BC_PREFILLED) return HYDRO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < nsteps; ++k) {
+    const hydro_box_t* in = (k % 2) ? b : a;
+    const hydro_box_t* out = (k % 2) ? a : b;
+    double* dt_in = dt_dev + (k % 2);
+    double* dt_out = dt_dev + ((k + 1) % 2);
+    int rc = hydro_batch_run(ctx, in, out, 1, params, 0, dt_in, dt_out, nullptr, nullptr, st, nullptr);
+    if (rc) return rc;
+    if (t_dev) {
+      kb_accumulate<<<1, 1, 0, st>>>(t_dev, dt_in);
+      if (cudaGetLastError() != cudaSuccess) return HYDRO_ECUDA;
+      ctx->launches += 1;
+    }
+  }
+  return HYDRO_OK;
 }
 
 extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax) {

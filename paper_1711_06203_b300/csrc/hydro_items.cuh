@@ -183,7 +183,7 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
   long long r = t / R.ext1;
   c3[T2] = R.lo2 + (int)(r % R.ext2);
   const int seg = (int)(r / R.ext2);
-  const int i0 = -1 + seg * R.seg;
+  const int i0 = R.lod + seg * R.seg;
   const int i1 = min(i0 + R.seg, R.nd + 1);
   c3[D] = i0;
   const long long sc = sg.sc;

@@ -36,12 +36,19 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 double* g_dev_scratch[MAX_DEVICES] = {};  // device address of g_noalloc_scratch per device
 
-// once per device, with that device current: fetch the array's device address
+// once per device, with that device current: fetch the array's device
+// address and clear its flag block (the bad-state flag then stays set from
+// the call that raised it until a call with dt_next_host reports it)
 int noalloc_setup(int device, double** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_dev_scratch[device]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HYDRO_ECUDA;
+    }
+    if (cudaMemset(static_cast<double*>(p) + NOALLOC_DOUBLES, 0, sizeof(DevFlags)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
       cudaGetLastError();
       return HYDRO_ECUDA;
     }
@@ -92,9 +99,10 @@ extern "C" int hydro_advance_box_noalloc(const hydro_box_t* in, const hydro_box_
   a.cfl = params->cfl;
   a.flags = reinterpret_cast<DevFlags*>(base + NOALLOC_DOUBLES);
   a.events = nullptr;
-  // the flag block keeps the previous call's contents: the sticky bad-state
-  // flag must start each call at zero (the speed maxima are reset by the step)
-  if (cudaMemsetAsync(a.flags, 0, sizeof(DevFlags), st) != cudaSuccess) return HYDRO_ECUDA;
+  // the flag block keeps the previous call's contents: the step itself resets
+  // the speed maxima and sweep cursors; the bad-state flag is sticky, so a
+  // bad state of a call without dt_next_host is reported by the next call
+  // that passes one, which clears it
   if (launch_step(a, st, nullptr) != cudaSuccess) return HYDRO_ECUDA;
   if (dt_next_host) {
     DevFlags h;
@@ -102,7 +110,12 @@ extern "C" int hydro_advance_box_noalloc(const hydro_box_t* in, const hydro_box_
       return HYDRO_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HYDRO_ECUDA;
     *dt_next_host = h.dt_next;
-    if (h.bad) return HYDRO_EBADSTATE;
+    if (h.bad) {
+      if (cudaMemsetAsync(&a.flags->bad, 0, sizeof(int), st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return HYDRO_ECUDA;
+      return HYDRO_EBADSTATE;
+    }
   }
   return HYDRO_OK;
 }

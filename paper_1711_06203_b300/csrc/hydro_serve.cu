@@ -3,15 +3,27 @@
 // Requests (a Sod, Sedov or two-state Riemann problem on a cubic FP64 box,
 // advanced a given number of CTU-PPM steps) arrive at any time.  A scheduler
 // thread admits them in arrival order as long as their device footprint fits
-// the HBM budget and a slot is free, builds their initial state on the device,
-// and then advances ALL active requests together: every iteration is one
-// batched CTU-PPM step (hydro_batch_run) over every active box, each with its
-// own gamma and CFL time step.  Requests that finish are retired (state copied
-// to the caller's host buffer if one was given) and their memory is released,
-// so new arrivals join the running batch at the next iteration.  The paper's
-// analogue is the box iterator feeding a level's boxes to the GPU kernel
-// (Sec. 4); serving many small problems concurrently is this library's own
-// use of it.
+// the HBM budget and a slot is free and builds their initial state on the
+// device.  Every iteration is then one batched CTU-PPM step (hydro_batch_run,
+// launched directly: the stepped set changes from iteration to iteration)
+// over a set of active boxes, each with its own gamma and CFL time step:
+//   - HYDRO_SERVE_ALL: every active request steps every iteration (the GPU is
+//     shared evenly per step, so a small request advances only as fast as
+//     the largest box in the mix);
+//   - HYDRO_SERVE_RESPONSE_RATIO (default): the requests with the highest
+//     response ratio (time since submission + remaining work, over remaining
+//     work; work = steps left x the measured cost of a step of that size)
+//     step, added in that order while the iteration's estimated GPU time stays
+//     within a quantum (the first one always steps).  Short requests get
+//     through quickly, and a long one's ratio grows while it waits, so it is
+//     not starved.  Only the stepped set needs step scratch, so the scratch
+//     pool is bounded by the quantum and the largest box, and more requests'
+//     states fit the budget.
+// Requests that finish are retired (state copied to the caller's host buffer
+// if one was given) and their memory is released, so new arrivals join at the
+// next iteration.  The paper's analogue is the box iterator feeding a level's
+// boxes to the GPU kernel (Sec. 4); serving many small problems concurrently
+// is this library's own use of it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,6 +91,15 @@ struct Req {
 
 size_t grown_zones(int n) { return (size_t)(n + 2 * NG) * (n + 2 * NG) * (n + 2 * NG); }
 
+// relative cost of one step of an n^3 box: the tracing and solver stages run
+// over (n + 2)^3 to (n + 3)^3 zones
+double step_units(int n) { return (double)(n + 3) * (n + 3) * (n + 3); }
+
+// the fastest rate a step can reach, ms per unit (0.5 ns per zone: four
+// times the measured single-box rate), used to bound the scratch a quantum
+// can need before the rate is measured
+constexpr double MIN_MS_PER_UNIT = 5e-7;
+
 hydro_box_t box_of(double* u, int n) {
   hydro_box_t b;
   std::memset(&b, 0, sizeof b);
@@ -131,12 +152,23 @@ struct serve {
   std::thread loop;
   double* dt_dev = nullptr;
   double* dt_next_dev = nullptr;
+  // scheduling
+  int policy = HYDRO_SERVE_RESPONSE_RATIO;
+  double quantum_ms = 10.0;
+  double ms_per_unit = 2.1e-6;  // measured cost of a step per step_units (running average)
   // statistics
-  long long iterations = 0, zone_updates = 0, admitted = 0, completed = 0;
-  double busy_ms = 0.0;
+  long long iterations = 0, zone_updates = 0, admitted = 0, completed = 0, box_steps = 0;
+  double busy_ms = 0.0, enqueue_ms = 0.0;
   size_t pool_cached = 0;  // scratch pool size, refreshed by the scheduler thread
 
   size_t pool_bytes() const { return hydro_batch_pool_bytes(ctx); }
+  // scratch the pool may need with the active set plus one more request
+  size_t pool_need(size_t scratch_sum, size_t scratch_max) const {
+    if (policy == HYDRO_SERVE_ALL) return std::max(pool_bytes(), scratch_sum);
+    const double units = quantum_ms / MIN_MS_PER_UNIT;
+    const size_t quantum_scratch = (size_t)(units * SCRATCH_FIELDS * sizeof(double));
+    return std::max(pool_bytes(), std::min(scratch_sum, scratch_max + quantum_scratch));
+  }
   void retire(Req* r, int status);
   void run();
 };
@@ -178,15 +210,19 @@ void serve::run() {
       cv_work.wait(lock, [&] { return stop || !pending.empty() || !active.empty(); });
       if (stop) break;
       // admission in arrival order while the footprint fits the budget
-      size_t scratch_sum = 0;
-      for (Req* r : active) scratch_sum += r->scratch_bytes;
+      size_t scratch_sum = 0, scratch_max = 0;
+      for (Req* r : active) {
+        scratch_sum += r->scratch_bytes;
+        scratch_max = std::max(scratch_max, r->scratch_bytes);
+      }
       while (!pending.empty() && (int)(active.size() + fresh.size()) < max_slots) {
         Req* r = pending.front();
-        size_t scratch_need = std::max(pool_bytes(), scratch_sum + r->scratch_bytes);
+        size_t scratch_need = pool_need(scratch_sum + r->scratch_bytes, std::max(scratch_max, r->scratch_bytes));
         if (states_used + r->state_bytes + scratch_need > budget) break;
         pending.pop_front();
         states_used += r->state_bytes;
         scratch_sum += r->scratch_bytes;
+        scratch_max = std::max(scratch_max, r->scratch_bytes);
         r->admitted = Clock::now();
         admitted += 1;
         fresh.push_back(r);
@@ -237,38 +273,69 @@ void serve::run() {
     }
     if (active.empty()) continue;
 
-    // one batched step over every active request
+    // the set that steps this iteration
     const auto t0 = Clock::now();
-    const int na = (int)active.size();
+    std::vector<Req*> step_set;
+    if (policy == HYDRO_SERVE_ALL) {
+      step_set = active;
+    } else {
+      std::vector<std::pair<double, Req*>> order;
+      for (Req* r : active) {
+        const double work = (r->req.steps - r->steps_done) * ms_per_unit * step_units(r->req.n);
+        order.push_back({(ms_between(r->submitted, t0) + work) / work, r});
+      }
+      std::stable_sort(order.begin(), order.end(),
+                       [](const std::pair<double, Req*>& a, const std::pair<double, Req*>& b) { return a.first > b.first; });
+      size_t scratch_sum = 0, scratch_max = 0;
+      for (Req* r : active) {
+        scratch_sum += r->scratch_bytes;
+        scratch_max = std::max(scratch_max, r->scratch_bytes);
+      }
+      const size_t scratch_cap = pool_need(scratch_sum, scratch_max);
+      double est = 0.0;
+      size_t scratch = 0;
+      for (auto& o : order) {
+        Req* r = o.second;
+        const double c = ms_per_unit * step_units(r->req.n);
+        if (!step_set.empty() && (est + c > quantum_ms || scratch + r->scratch_bytes > scratch_cap)) continue;
+        step_set.push_back(r);
+        est += c;
+        scratch += r->scratch_bytes;
+      }
+    }
+    const int na = (int)step_set.size();
     bin.resize(na);
     bout.resize(na);
     prm.resize(na);
     dts.resize(na);
     dtn.resize(na);
     bad.assign(na, 0);
+    double units = 0.0;
     for (int i = 0; i < na; ++i) {
-      Req* r = active[i];
+      Req* r = step_set[i];
       bin[i] = box_of(r->buf[r->cur], r->req.n);
       bout[i] = box_of(r->buf[r->cur ^ 1], r->req.n);
       prm[i] = params_of(r->req);
       dts[i] = r->dt;
+      units += step_units(r->req.n);
     }
     int rc = HYDRO_OK;
+    const double select_ms = ms_between(t0, Clock::now());
+    double enq_ms = 0.0;
     if (cudaMemcpyAsync(dt_dev, dts.data(), na * sizeof(double), cudaMemcpyHostToDevice, stream) != cudaSuccess)
       rc = HYDRO_ECUDA;
     if (rc == HYDRO_OK)
       rc = hydro_batch_run(ctx, bin.data(), bout.data(), na, prm.data(), 1, dt_dev, dt_next_dev, nullptr,
-                           bad.data(), stream, nullptr);
+                           bad.data(), stream, nullptr, true, &enq_ms);
     if (rc == HYDRO_OK || rc == HYDRO_EBADSTATE) {
       if (cudaMemcpyAsync(dtn.data(), dt_next_dev, na * sizeof(double), cudaMemcpyDeviceToHost, stream) !=
               cudaSuccess ||
           cudaStreamSynchronize(stream) != cudaSuccess)
         rc = HYDRO_ECUDA;
     }
-    std::vector<Req*> still;
     std::vector<std::pair<Req*, int>> finished;
     for (int i = 0; i < na; ++i) {
-      Req* r = active[i];
+      Req* r = step_set[i];
       if (rc != HYDRO_OK && rc != HYDRO_EBADSTATE) {
         finished.push_back({r, rc});
         continue;
@@ -282,15 +349,24 @@ void serve::run() {
       r->steps_done += 1;
       r->dt = dtn[i];
       if (r->steps_done >= r->req.steps) finished.push_back({r, HYDRO_OK});
-      else still.push_back(r);
     }
+    const auto t1 = Clock::now();
     {
       std::lock_guard<std::mutex> lock(mu);
       iterations += 1;
+      box_steps += na;
       for (int i = 0; i < na; ++i)
-        if (!bad[i]) zone_updates += (long long)active[i]->req.n * active[i]->req.n * active[i]->req.n;
-      busy_ms += ms_between(t0, Clock::now());
+        if (!bad[i]) zone_updates += (long long)step_set[i]->req.n * step_set[i]->req.n * step_set[i]->req.n;
+      const double ms = ms_between(t0, t1);
+      busy_ms += ms;
+      enqueue_ms += select_ms + enq_ms;
+      if (rc == HYDRO_OK && units > 0.0) ms_per_unit = 0.8 * ms_per_unit + 0.2 * (ms / units);
       pool_cached = pool_bytes();
+      std::vector<Req*> still;
+      for (Req* r : active)
+        if (std::find_if(finished.begin(), finished.end(),
+                         [r](const std::pair<Req*, int>& f) { return f.first == r; }) == finished.end())
+          still.push_back(r);
       active.swap(still);
     }
     for (auto& f : finished) retire(f.first, f.second);
@@ -385,6 +461,17 @@ int serve_poll(serve_t* s, uint64_t id, hydro_result_t* res, int timeout_ms) {
   return HYDRO_OK;
 }
 
+int serve_set_policy(serve_t* s, int policy, double quantum_ms) {
+  if (!s || (policy != HYDRO_SERVE_ALL && policy != HYDRO_SERVE_RESPONSE_RATIO)) return HYDRO_EINVAL;
+  if (policy == HYDRO_SERVE_RESPONSE_RATIO && !(quantum_ms > 0.0 && quantum_ms <= 60000.0)) return HYDRO_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  // busy while anything is queued, being admitted or running
+  if (!s->pending.empty() || s->admitted != s->completed) return HYDRO_EAGAIN;
+  s->policy = policy;
+  if (policy == HYDRO_SERVE_RESPONSE_RATIO) s->quantum_ms = quantum_ms;
+  return HYDRO_OK;
+}
+
 int serve_stats(serve_t* s, hydro_serve_stats_t* st) {
   if (!s || !st) return HYDRO_EINVAL;
   std::lock_guard<std::mutex> lock(s->mu);
@@ -398,6 +485,9 @@ int serve_stats(serve_t* s, hydro_serve_stats_t* st) {
   st->hbm_budget = s->budget;
   st->hbm_states = s->states_used;
   st->hbm_scratch_pool = s->pool_cached;
+  st->box_steps = s->box_steps;
+  st->enqueue_ms = s->enqueue_ms;
+  st->ms_per_unit = s->ms_per_unit;
   return HYDRO_OK;
 }
 

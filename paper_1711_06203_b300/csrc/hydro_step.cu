@@ -141,6 +141,40 @@ __global__ void k_zero_cursors(unsigned long long* c, int n) {
 
 inline unsigned blocks_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
+// copy the final fluxes on the outer faces (face 0 and face n_d along every
+// active d, transverse interior) into dst, plane after plane in (d, side)
+// order, each plane 5 fields of (t1 fastest, t2) with t1 < t2 the transverse
+// axes; x- and y-faces only on the planes [zlo, zhi), z-faces only when
+// those planes include the first (face 0) or the last (face n_z) one
+__global__ void k_record_faces(Scratch s, ScratchGeom sg, int n0, int n1, int n2, int dim, int zlo, int zhi,
+                               double* __restrict__ dst) {
+  const int n[3] = {n0, n1, n2};
+  long long off = 0;
+  for (int d = 0; d < dim; ++d) {
+    const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+    const int e1 = n[t1], e2 = (t2 < dim) ? n[t2] : 1;
+    const long long A = (long long)e1 * e2;
+    for (int side = 0; side < 2; ++side) {
+      // rows of t2 to copy: for x- and y-faces (t2 = z) the planes given
+      int r0 = 0, r1 = e2;
+      if (dim == 3 && t2 == 2) { r0 = zlo; r1 = zhi; }
+      if (d == 2 && !(side ? zhi == n2 : zlo == 0)) r1 = r0;  // z-face outside these planes
+      const long long cnt = (long long)(r1 - r0) * e1;
+      for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 5 * cnt;
+           q += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(q / cnt);
+        const long long r = q - c * cnt;
+        int z[3] = {0, 0, 0};
+        z[d] = side ? n[d] : 0;
+        z[t1] = (int)(r % e1);
+        z[t2] = r0 + (int)(r / e1);
+        dst[off + c * A + (long long)z[t2] * e1 + z[t1]] = s.F3[d][c * sg.sc + sg.id(z[0], z[1], z[2])];
+      }
+      off += 5 * A;
+    }
+  }
+}
+
 // tracing sweep along d over pencils whose transverse coordinates are
 // [-1, n] on the first transverse axis and [lo2, lo2 + ext2) on the second
 void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long long* cur, cudaStream_t st) {
@@ -150,6 +184,7 @@ void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long lon
   sw.lo1 = -1; sw.ext1 = n[t1] + 2;
   sw.lo2 = lo2; sw.ext2 = ext2;
   sw.nd = n[d];
+  sw.lod = -1;
   sw.seg = TRACE_SEG;
   sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
   const unsigned need = blocks_for(sw.count());
@@ -159,22 +194,31 @@ void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long lon
   if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
 }
 
-// first fluxes through d-faces [0, n_d] x the transverse zones of rt (the
-// tracing range: zones [-1, n] on active axes, or a slab of z-planes) of the
-// directions d in dirs (bit d), one launch
-int launch_flux1_all(const StepArgs& a, const Range& rt, unsigned dirs, cudaStream_t st) {
-  const int* n = a.in.n;
+// first fluxes of the directions d in dirs (bit d) over the face ranges r[d], one launch
+int launch_flux1_ranges(const StepArgs& a, const Range r[3], unsigned dirs, cudaStream_t st) {
   DirSets S;
   S.first[0] = 0;
   for (int d = 0; d < 3; ++d) {
-    S.r[d] = rt;
-    S.r[d].lo[d] = 0;
-    S.r[d].ext[d] = n[d] + 1;
+    S.r[d] = r[d];
     S.first[d + 1] = S.first[d] + (((dirs >> d) & 1u) ? blocks_for(S.r[d].count()) : 0u);
   }
   if (a.K.einfeldt) k_flux1<true><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   else k_flux1<false><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   return 1;
+}
+
+// first fluxes through d-faces [0, n_d] x the transverse zones of rt (the
+// tracing range: zones [-1, n] on active axes, or a slab of z-planes) of the
+// directions d in dirs (bit d), one launch
+int launch_flux1_all(const StepArgs& a, const Range& rt, unsigned dirs, cudaStream_t st) {
+  const int* n = a.in.n;
+  Range r[3];
+  for (int d = 0; d < 3; ++d) {
+    r[d] = rt;
+    r[d].lo[d] = 0;
+    r[d].ext[d] = n[d] + 1;
+  }
+  return launch_flux1_ranges(a, r, dirs, st);
 }
 
 // final fluxes through d-faces [0, n_d] of every active direction d, over
@@ -201,9 +245,14 @@ int launch_flux3_all(const StepArgs& a, int dim, int zlo, int zext, cudaStream_t
   return 1;
 }
 
-// 3-D intermediate fluxes F^{d|t}: d-faces [0, n_d] x t in [0, n_t) x third axis [-1, n]
-int launch_flux2_all(const StepArgs& a, cudaStream_t st) {
+// 3-D intermediate fluxes F^{d|t}: d-faces [0, n_d] x t in [0, n_t) x third
+// axis [-1, n], restricted along z to the interior planes [zlo, zlo + zext)
+// of a slab (the ranges grow by the faces and zones the slab's final fluxes
+// read: F^{x|y}, F^{y|x} on planes [zlo - 1, zlo + zext], F^{z|x}, F^{z|y} on
+// z-faces [zlo, zlo + zext], F^{x|z}, F^{y|z} on the slab's planes)
+int launch_flux2_all(const StepArgs& a, cudaStream_t st, int zlo = 0, int zext = -1) {
   const int* n = a.in.n;
+  if (zext < 0) zext = n[2];
   Flux2Sets S;
   S.first[0] = 0;
   int c = 0;
@@ -215,6 +264,10 @@ int launch_flux2_all(const StepArgs& a, cudaStream_t st) {
       r.lo[d] = 0; r.ext[d] = n[d] + 1;
       r.lo[t] = 0; r.ext[t] = n[t];
       r.lo[o] = -1; r.ext[o] = n[o] + 2;
+      // the z extent: faces, zones or the widened range of the slab
+      if (d == 2) { r.lo[2] = zlo; r.ext[2] = zext + 1; }
+      else if (t == 2) { r.lo[2] = zlo; r.ext[2] = zext; }
+      else { r.lo[2] = zlo - 1; r.ext[2] = zext + 2; }
       S.first[c + 1] = S.first[c] + blocks_for(r.count());
       ++c;
     }
@@ -260,6 +313,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
     sw.lo1 = rt.lo[t1]; sw.ext1 = rt.ext[t1];
     sw.lo2 = rt.lo[t2]; sw.ext2 = rt.ext[t2];
     sw.nd = n[d];
+    sw.lod = -1;
     sw.seg = TRACE_SEG;
     sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
     const unsigned need = blocks_for(sw.count());
@@ -287,6 +341,96 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
   k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], dim, a.cfl);
   nl += 2;
   mark(NSTAGES);
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+Scratch shift_scratch(const Scratch& s, long long shift) {
+  Scratch w = s;
+  w.Q -= shift;
+  for (int d = 0; d < 3; ++d) {
+    w.TM[d] -= shift;
+    w.TP[d] -= shift;
+    w.F1[d] -= shift;
+    w.F3[d] -= shift;
+    for (int t = 0; t < 3; ++t)
+      if (w.F2[d][t]) w.F2[d][t] -= shift;
+  }
+  return w;
+}
+
+cudaError_t launch_record_faces(const StepArgs& a, int zlo, int zhi, double* faces, cudaStream_t st) {
+  const int dim = a.K.dim;
+  k_record_faces<<<148, 256, 0, st>>>(a.s, a.sg, a.in.n[0], a.in.n[1], dim == 3 ? a.in.n[2] : 1, dim, zlo, zhi,
+                                      faces);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_slabs(const StepArgs& a, int T, unsigned long long* cursors, double* faces,
+                              cudaStream_t st, long long* launches) {
+  const int* n = a.in.n;
+  const int nslab = (n[2] + T - 1) / T;
+  long long nl = 0;
+  auto mark = [&](int stage) {
+    if (a.events) cudaEventRecord(a.events[stage], st);
+  };
+  // a slabbed step is timed as a whole: its duration is reported as the
+  // primitive-state stage, the other stages as zero
+  mark(ST_PRIM);
+  k_reset_step<<<1, 32, 0, st>>>(a.flags);
+  k_zero_cursors<<<1, 256, 0, st>>>(cursors, 3 * nslab);
+  nl += 2;
+  for (int k = 0; k < nslab; ++k) {
+    const int z0 = k * T, ze = std::min(T, n[2] - z0);
+    StepArgs w = a;
+    w.s = shift_scratch(a.s, (long long)z0 * a.sg.sz);
+    const Scratch& s = w.s;
+    // primitive state on planes [z0 - 4, z0 + ze + 4) of the grown box
+    Range rp;
+    for (int ax = 0; ax < 2; ++ax) { rp.lo[ax] = -NG; rp.ext[ax] = n[ax] + 2 * NG; }
+    rp.lo[2] = z0 - NG; rp.ext[2] = ze + 2 * NG;
+    k_prim<<<blocks_for(rp.count()), BLOCK, 0, st>>>(a.in, a.sg, s.Q, a.K, rp, a.flags);
+    // traced states on zones [-1, n] in x and y and planes [z0 - 1, z0 + ze]
+    launch_trace(0, w, z0 - 1, ze + 2, cursors + 3 * k, st);
+    launch_trace(1, w, z0 - 1, ze + 2, cursors + 3 * k + 1, st);
+    {
+      SweepRange sw;
+      sw.lo1 = -1; sw.ext1 = n[0] + 2;
+      sw.lo2 = -1; sw.ext2 = n[1] + 2;
+      sw.lod = z0 - 1;
+      sw.nd = z0 + ze;
+      sw.seg = TRACE_SEG;
+      sw.nseg = (ze + 2 + TRACE_SEG - 1) / TRACE_SEG;
+      const unsigned need = blocks_for(sw.count());
+      k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(
+          a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cursors + 3 * k + 2);
+    }
+    // first fluxes: x- and y-faces on planes [z0 - 1, z0 + ze], z-faces [z0, z0 + ze]
+    Range r1[3];
+    for (int d = 0; d < 3; ++d) {
+      for (int ax = 0; ax < 2; ++ax) { r1[d].lo[ax] = -1; r1[d].ext[ax] = n[ax] + 2; }
+      r1[d].lo[2] = z0 - 1; r1[d].ext[2] = ze + 2;
+      if (d < 2) { r1[d].lo[d] = 0; r1[d].ext[d] = n[d] + 1; }
+    }
+    r1[2].lo[2] = z0; r1[2].ext[2] = ze + 1;
+    nl += 4 + launch_flux1_ranges(w, r1, 7u, st);
+    nl += launch_flux2_all(w, st, z0, ze);
+    nl += launch_flux3_all(w, 3, z0, ze, st);
+    Range ru;
+    ru.lo[0] = 0; ru.ext[0] = n[0];
+    ru.lo[1] = 0; ru.ext[1] = n[1];
+    ru.lo[2] = z0; ru.ext[2] = ze;
+    k_update<<<blocks_for(ru.count()), BLOCK, 0, st>>>(a.in, a.out, a.sg, s.F3[0], s.F3[1], s.F3[2], a.K, ru,
+                                                       a.flags);
+    nl += 1;
+    if (faces) {
+      if (launch_record_faces(w, z0, z0 + ze, faces, st) != cudaSuccess) return cudaGetLastError();
+      nl += 1;
+    }
+  }
+  k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], 3, a.cfl);
+  nl += 1;
+  for (int stg = ST_TRACE; stg <= NSTAGES; ++stg) mark(stg);
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

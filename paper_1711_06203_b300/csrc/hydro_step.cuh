@@ -48,12 +48,14 @@ struct Range {
   long long count() const { return (long long)ext[0] * ext[1] * ext[2]; }
 };
 
-// pencil segments of the tracing sweep: zones [-1, n_d] along d cut into
-// segments of TRACE_SEG, for every transverse position in [-1, n]
+// pencil segments of the tracing sweep: zones [lod, nd] along d (lod = -1:
+// the whole range [-1, n_d]) cut into segments of TRACE_SEG, for every
+// transverse position in the given ranges
 constexpr int TRACE_SEG = 16;
 struct SweepRange {
   int lo1, ext1, lo2, ext2;  // transverse axes T1 (thread-fastest) and T2
-  int nd, nseg, seg;         // zones along d, segments per pencil, zones per segment
+  int nd, nseg, seg;         // last zone along d, segments per pencil, zones per segment
+  int lod;                   // first zone along d
   __host__ __device__ long long count() const { return (long long)ext1 * ext2 * nseg; }
 };
 
@@ -99,6 +101,25 @@ struct StepArgs {
 // enqueue one step (all kernels) on `stream`; adds the number of kernels
 // launched to *launches
 cudaError_t launch_step(const StepArgs& a, cudaStream_t stream, long long* launches);
+
+// The same step of a 3-D box computed slab by slab along z, T interior planes
+// at a time, with scratch for T + 8 planes only (a.sg, a.s: that window,
+// unshifted).  Each slab computes every intermediate its planes need from
+// the input box itself (the ghost mapping is the whole box's), so planes
+// next to a slab boundary are computed by both slabs with the same values:
+// the result is bitwise that of launch_step.  `cursors`: 3 * ceil(n_z / T)
+// device work counters, zeroed by the step.  `faces` (nullable): record the
+// outer-face fluxes slab by slab into this buffer (layout of
+// hydro_ctx_face_flux).
+cudaError_t launch_step_slabs(const StepArgs& a, int T, unsigned long long* cursors, double* faces,
+                              cudaStream_t stream, long long* launches);
+// scratch pointers that index a window of planes starting at plane z0 with
+// the whole box's zone coordinates (every pointer moves down by z0 * sz)
+Scratch shift_scratch(const Scratch& s, long long shift);
+// copy the final fluxes on the outer faces into `faces` (layout of
+// hydro_ctx_face_flux): d-faces along x and y over the planes [zlo, zhi),
+// the z-faces at 0 and n_z when the planes include the first or last one
+cudaError_t launch_record_faces(const StepArgs& a, int zlo, int zhi, double* faces, cudaStream_t stream);
 
 // A 3-D step whose input arrives from, and whose output returns to, host
 // memory, with the copies overlapping the kernels: the interior z-planes

@@ -7,7 +7,9 @@ whole domain with the same boundary kinds.
   * K steps of fill + batched step + level dt reduction (all on the device)
     equal K steps of the single box: bitwise for the contraction-free build,
     to the parity tolerance for the product build (whose batched and
-    single-box kernels may fuse multiply-adds differently).
+    single-box kernels may fuse multiply-adds differently);
+  * two level steps equal two steps of the CPU oracle on the single box over
+    the domain: bitwise (contraction-free build), within 1e-10 (product).
 """
 import numpy as np
 import pytest
@@ -137,3 +139,46 @@ def test_fill_boundary_rejects_bad_tilings():
     with pytest.raises(hb.HydroError):  # periodic on one face only
         ctx.hydro_fill_boundary([d], [(0, 0, 0)], 3, (16, 16, 16), ((PER, O), (O, O), (O, O)))
     ctx.close()
+
+
+@pytest.mark.parametrize("variant,dim", [("exact", 3), ("default", 3), ("default", 2)])
+def test_level_two_steps_against_oracle(variant, dim):
+    """Two level steps (device ghost fill, batched step, level dt reduction)
+    against the CPU oracle's single box over the whole domain, each side
+    taking its own CFL steps: bitwise for the contraction-free build, within
+    1e-10 for the product build."""
+    domain, lo, sizes, U, bc, dx = _setup(dim)
+    P = oracle.params(dim, domain[:dim], dx=dx, bc=bc, gamma=5 / 3, cfl=0.5)
+    ref, _, odts = oracle.run(U, P, 2)
+    p = hb.params(dim, gamma=5 / 3, cfl=0.5)
+    ctx = hb.Context(0, variant)
+    a = [torch.from_numpy(B).cuda() for B in _split(U, lo, sizes, dim)]
+    b = [torch.full_like(x, float("nan")) for x in a]
+    da = [hb.box(t, s, dx, hb.BC_PREFILLED) for t, s in zip(a, sizes)]
+    db = [hb.box(t, s, dx, hb.BC_PREFILLED) for t, s in zip(b, sizes)]
+    big = torch.from_numpy(U).cuda()
+    dt_dev = torch.full((len(sizes),), ctx.hydro_dt(hb.box(big, domain, dx, bc), p), dtype=torch.float64,
+                        device="cuda")
+    dt_next = torch.empty_like(dt_dev)
+    level_dts = []
+    for _ in range(2):
+        ctx.hydro_fill_boundary(da, lo, dim, domain[:dim], bc[:dim])
+        level_dts.append(dt_dev[0].item())
+        ctx.hydro_advance_batch(da, db, p, dt_dev, dt_next)
+        ctx.hydro_level_min_dt(dt_next, dt_dev)
+        da, db = db, da
+        a, b = b, a
+    torch.cuda.synchronize()
+    ctx.close()
+    if variant == "exact":
+        assert level_dts == odts
+    else:
+        assert np.allclose(level_dts, odts, rtol=1e-13, atol=0)
+    for t, c, s in zip(a, lo, sizes):
+        got = t.cpu().numpy()
+        got = got[:, 4:-4, 4:-4, 4:-4] if dim == 3 else got[:, 0, 4:-4, 4:-4]
+        want = _region(ref, c, s, dim)
+        if variant == "exact":
+            assert np.array_equal(got, want)
+        else:
+            assert np.all(rel_linf(got, want) <= 1e-10)

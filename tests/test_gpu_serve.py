@@ -1,7 +1,8 @@
 """Continuous-batching server: results are the same alone and in a mix of
-concurrently running requests (bitwise: the batched step's arithmetic for a
-box does not depend on the other boxes), match the CPU oracle, and the
-request life cycle (admission, polling, budget refusal) behaves."""
+concurrently running requests, under both scheduling policies (bitwise: the
+batched step's arithmetic for a box does not depend on the other boxes or on
+which of them step with it), match the CPU oracle, and the request life cycle
+(admission, polling, budget refusal, policy changes) behaves."""
 import time
 
 import numpy as np
@@ -51,7 +52,8 @@ def test_served_results_match_oracle():
         assert r["zone_updates"] == q["steps"] * q["n"] ** 3
 
 
-def test_alone_equals_in_the_mix():
+@pytest.mark.parametrize("policy", [hb.SERVE_RESPONSE_RATIO, hb.SERVE_ALL])
+def test_alone_equals_in_the_mix(policy):
     # each request alone in its own server
     alone = []
     for q in REQS:
@@ -61,6 +63,7 @@ def test_alone_equals_in_the_mix():
         srv.close()
     # in a mix: a long request starts first, the others arrive while it runs
     srv = hb.Server(0, max_slots=8)
+    srv.serve_set_policy(policy, 10.0)
     long_id = srv.serve_submit(kind=hb.PROB_SEDOV, n=32, steps=60)
     t0 = time.time()
     while srv.serve_stats()["active"] == 0 and time.time() - t0 < 30:
@@ -79,8 +82,36 @@ def test_alone_equals_in_the_mix():
         assert np.array_equal(a["state"][I3], m["state"][I3])
     assert stats["completed"] == len(REQS) + 1 and stats["admitted"] == len(REQS) + 1
     assert stats["zone_updates"] == 60 * 32 ** 3 + sum(q["steps"] * q["n"] ** 3 for q in REQS)
+    assert stats["box_steps"] == 60 + sum(q["steps"] for q in REQS)
     # the requests overlapped the long one: fewer iterations than the sum of all steps
     assert 60 <= stats["iterations"] < 60 + sum(q["steps"] for q in REQS)
+
+
+def test_response_ratio_quantum_and_policy_changes():
+    """With a quantum smaller than one step of any box, every iteration steps
+    exactly one request; the policy can change only while the server is idle."""
+    srv = hb.Server(0, max_slots=8)
+    with pytest.raises(hb.HydroError) as e:
+        srv.serve_set_policy(7, 1.0)
+    assert e.value.status == hb.HYDRO_EINVAL
+    with pytest.raises(hb.HydroError) as e:
+        srv.serve_set_policy(hb.SERVE_RESPONSE_RATIO, 0.0)
+    assert e.value.status == hb.HYDRO_EINVAL
+    srv.serve_set_policy(hb.SERVE_RESPONSE_RATIO, 1e-6)
+    long_id = srv.serve_submit(kind=hb.PROB_SEDOV, n=32, steps=200)
+    with pytest.raises(hb.HydroError) as e:  # busy
+        srv.serve_set_policy(hb.SERVE_ALL)
+    assert e.value.status == hb.HYDRO_EAGAIN
+    ids = [srv.serve_submit(**q) for q in REQS]
+    res = [srv.serve_poll(i, timeout_ms=120000) for i in ids + [long_id]]
+    st = srv.serve_stats()
+    assert all(r["status"] == hb.HYDRO_OK for r in res)
+    assert st["iterations"] == st["box_steps"] == 200 + sum(q["steps"] for q in REQS)
+    # the short requests were not held behind the long one: each finished
+    # before it
+    assert max(r["latency_ms"] for r in res[:-1]) < res[-1]["latency_ms"]
+    srv.serve_set_policy(hb.SERVE_ALL)
+    srv.close()
 
 
 def test_poll_and_budget_semantics():
