@@ -484,6 +484,14 @@ int hydro_ctx_face_flux(hydro_ctx_t* ctx, int d, int side, double* dst, void* st
  * IEEE 2.0*x and 0.5*x. */
 int hydro_selftest_scale2(const double* x, double* twice, double* half, long long n, void* stream);
 
+/* Diagnostics (no counterpart in the paper): the device's FP64 issue rate,
+ * the denominator of the step's FP64 roofline.  Launches nblocks blocks of
+ * 256 threads, each thread running 8 independent chains of `iters` FP64
+ * multiply-adds (nblocks * 256 * 8 * iters FMAs, 2 flops each), and writes
+ * one double per thread to out (device, nblocks * 256 doubles); time it with
+ * events on `stream`. */
+int hydro_selftest_fp64_rate(double* out, int nblocks, int iters, void* stream);
+
 /* Diagnostics (no counterpart in the paper): the kernels' reciprocal,
  * quotient and square root -- IEEE in the contraction-free build, Newton
  * refinements of the hardware's approximations in the product build -- over

@@ -155,6 +155,7 @@ def lib(variant="default"):
     L.hydro_ctx_launches.restype = ctypes.c_longlong
     L.hydro_ctx_record_face_fluxes.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_set_scratch_limit.argtypes = [vp, ctypes.c_size_t]
+    L.hydro_selftest_fp64_rate.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.hydro_advance_box_steps.argtypes = [vp, ctypes.POINTER(hydro_box_t), ctypes.POINTER(hydro_box_t),
                                           ctypes.POINTER(hydro_params_t), ctypes.c_int, vp, vp, vp]
     L.hydro_ctx_face_flux.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -216,6 +217,28 @@ def hydro_selftest_scale2(x, variant="default", stream=None):
     if rc:
         raise HydroError(rc, "hydro_selftest_scale2")
     return t, h
+
+
+def hydro_selftest_fp64_rate(nblocks=148 * 8, iters=4096, variant="default", stream=None, reps=3):
+    """Measured FP64 rate of the device in GFLOP/s (2 flops per multiply-add),
+    best of `reps` timed launches after one warm-up launch."""
+    import torch
+    out = torch.empty(nblocks * 256, dtype=torch.float64, device="cuda")
+    st = stream or torch.cuda.current_stream()
+    best = None
+    for rep in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc = lib(variant).hydro_selftest_fp64_rate(ctypes.c_void_p(out.data_ptr()), int(nblocks), int(iters),
+                                                   _stream_handle(st))
+        e1.record(st)
+        if rc:
+            raise HydroError(rc, "hydro_selftest_fp64_rate")
+        e1.synchronize()
+        if rep:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    return 2.0 * nblocks * 256 * 8 * iters / (best * 1e-3) / 1e9
 
 
 def hydro_selftest_divsqrt(x, y, variant="default", stream=None):

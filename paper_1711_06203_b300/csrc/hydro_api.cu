@@ -205,23 +205,6 @@ int slab_planes(const hydro_ctx* ctx, const ScratchGeom& sg, const int n[3], int
   return (int)((n[2] + nslab - 1) / nslab);
 }
 
-int ensure_slab_cursors(hydro_ctx* ctx, int count) {
-  if (count <= ctx->slab_cursor_cap) return HYDRO_OK;
-  if (ctx->slab_cursors) {
-    if (cudaDeviceSynchronize() != cudaSuccess) return HYDRO_ECUDA;
-    cudaFree(ctx->slab_cursors);
-  }
-  ctx->slab_cursors = nullptr;
-  ctx->slab_cursor_cap = 0;
-  const int cap = std::max(count, 96);
-  if (cudaMalloc(&ctx->slab_cursors, cap * sizeof(unsigned long long)) != cudaSuccess) {
-    cudaGetLastError();
-    return HYDRO_ENOMEM;
-  }
-  ctx->slab_cursor_cap = cap;
-  return HYDRO_OK;
-}
-
 int record_face_fluxes(hydro_ctx* ctx, const StepArgs& a, const int n[3], int dim, cudaStream_t st) {
   int rc = ensure_faces(ctx, n, dim);
   if (rc) return rc;
@@ -264,6 +247,20 @@ __global__ void k_selftest_divsqrt(const double* __restrict__ x, const double* _
   quo[i] = ddiv(y[i], x[i]);
   sq[i] = dsqrt(x[i]);
 }
+// FP64 issue rate: eight independent multiply-add chains per thread
+__global__ void k_selftest_fp64_rate(double* __restrict__ out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 __global__ void k_selftest_intpipe(const double* __restrict__ x, const double* __restrict__ y,
                                    double* __restrict__ prod, double* __restrict__ sum, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,13 +271,12 @@ __global__ void k_selftest_intpipe(const double* __restrict__ x, const double* _
 // z-chunks of the overlapped host-buffer step
 constexpr int PIPE_CHUNKS = 4;
 
-// copy streams, events and sweep cursors of the overlapped host-buffer step
+// copy streams and events of the overlapped host-buffer step
 int ensure_pipe(hydro_ctx* ctx) {
-  if (ctx->pipe_cursors) return HYDRO_OK;
+  if (ctx->pipe_ready) return HYDRO_OK;
   bool ok = cudaStreamCreateWithFlags(&ctx->pipe_h2d, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&ctx->pipe_d2h, cudaStreamNonBlocking) == cudaSuccess;
   for (auto& e : ctx->pipe_events) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
-  ok = ok && cudaMalloc(&ctx->pipe_cursors, (2 * PIPE_MAX_CHUNKS + 5) * sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     if (ctx->pipe_h2d) cudaStreamDestroy(ctx->pipe_h2d);
@@ -289,11 +285,10 @@ int ensure_pipe(hydro_ctx* ctx) {
       if (e) cudaEventDestroy(e);
       e = nullptr;
     }
-    if (ctx->pipe_cursors) cudaFree(ctx->pipe_cursors);
     ctx->pipe_h2d = ctx->pipe_d2h = nullptr;
-    ctx->pipe_cursors = nullptr;
     return HYDRO_ENOMEM;
   }
+  ctx->pipe_ready = true;
   return HYDRO_OK;
 }
 
@@ -356,9 +351,7 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
   if (ctx->pipe_d2h) cudaStreamDestroy(ctx->pipe_d2h);
   for (auto& e : ctx->pipe_events)
     if (e) cudaEventDestroy(e);
-  if (ctx->pipe_cursors) cudaFree(ctx->pipe_cursors);
   if (ctx->faces) cudaFree(ctx->faces);
-  if (ctx->slab_cursors) cudaFree(ctx->slab_cursors);
   delete ctx;
 }
 
@@ -425,10 +418,7 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
   if (T > 0) {
     // scratch larger than the context's limit: slab by slab along z
     a.sg.sc = a.sg.sz * (T + 2 * NG);
-    const int nslab = (in->n[2] + T - 1) / T;
     rc = ensure_scratch(ctx, (size_t)a.sg.sc * SCRATCH_FIELDS * sizeof(double));
-    if (rc) return rc;
-    rc = ensure_slab_cursors(ctx, 3 * nslab);
     if (rc) return rc;
     a.s = carve_scratch(ctx->scratch, a.sg.sc);
     double* faces = nullptr;
@@ -437,7 +427,7 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
       if (rc) return rc;
       faces = ctx->faces;
     }
-    if (launch_step_slabs(a, T, ctx->slab_cursors, faces, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
+    if (launch_step_slabs(a, T, faces, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
     if (faces) {
       ctx->faces_dim = dim;
       for (int t = 0; t < 3; ++t) ctx->faces_n[t] = in->n[t];
@@ -552,7 +542,6 @@ int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_
       hp.h2d_done[k] = ctx->pipe_events[2 + k];
       hp.upd_done[k] = ctx->pipe_events[2 + PIPE_MAX_CHUNKS + k];
     }
-    hp.cursors = ctx->pipe_cursors;
     if (launch_step_host_piped(a, hp, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
     if (ctx->record_faces) {
       rc = record_face_fluxes(ctx, a, in->n, dim, st);
@@ -658,6 +647,13 @@ int hydro_selftest_intpipe(const double* x, const double* y, double* prod, doubl
   if (!x || !y || !prod || !sum || n < 0) return HYDRO_EINVAL;
   if (n == 0) return HYDRO_OK;
   k_selftest_intpipe<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, prod, sum, n);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+int hydro_selftest_fp64_rate(double* out, int nblocks, int iters, void* stream) {
+  if (!out || nblocks < 1 || iters < 1) return HYDRO_EINVAL;
+  k_selftest_fp64_rate<<<(unsigned)nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(out, iters, 0.999999,
+                                                                                        1e-6);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 

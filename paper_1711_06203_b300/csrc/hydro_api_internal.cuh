@@ -25,10 +25,10 @@ struct hydro_ctx {
   long long stage_calls = 0;
   double* host_stage = nullptr;   // device in/out boxes of hydro_advance_box_host (grown on demand)
   size_t host_stage_bytes = 0;
-  // copy streams, events and sweep cursors of the overlapped host-buffer step (made on first use)
+  // copy streams and events of the overlapped host-buffer step (made on first use)
   cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
   cudaEvent_t pipe_events[2 * hydro::PIPE_MAX_CHUNKS + 2] = {};
-  unsigned long long* pipe_cursors = nullptr;
+  bool pipe_ready = false;
   // final fluxes through the outer faces of the last recorded box step
   int record_faces = 0;
   double* faces = nullptr;        // 2 * dim face planes, 5 fields each, in (d, side) order
@@ -37,8 +37,6 @@ struct hydro_ctx {
   int faces_n[3] = {0, 0, 0};
   // a 3-D box whose whole-box step scratch exceeds this is stepped slab by slab along z (0: never)
   size_t scratch_limit = (size_t)16 << 30;
-  unsigned long long* slab_cursors = nullptr;  // work counters of the slab sweeps
-  int slab_cursor_cap = 0;
 };
 
 void hydro_batch_release(hydro_ctx* ctx);
@@ -70,5 +68,4 @@ int collect_stage_times(hydro_ctx* ctx, cudaStream_t st);
 int record_face_fluxes(hydro_ctx* ctx, const StepArgs& a, const int n[3], int dim, cudaStream_t st);
 int ensure_faces(hydro_ctx* ctx, const int n[3], int dim);
 int slab_planes(const hydro_ctx* ctx, const ScratchGeom& sg, const int n[3], int dim);
-int ensure_slab_cursors(hydro_ctx* ctx, int count);
 }  // namespace hydro

@@ -281,6 +281,164 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
   }
 }
 
+// ---- stages 2-3 along x with the lanes of a warp along the pencil.  A warp
+// takes ROW_ZONES consecutive zones [t0, t0 + ROW_ZONES) of one x-pencil
+// (t0 = lod + ROW_ZONES * tile); lane l holds zone t0 - 1 + l, so lanes 0 and
+// 31 only supply the slope, the flattening coefficient and the interface value
+// their neighbours need.  Every quantity of a zone is the tracing sweep's, by
+// the same expressions: the slope and the flattening coefficient of each zone
+// once, the interface value at its high face once, the neighbours' values
+// through shuffles.  The loads of a warp are consecutive doubles (the
+// sequential sweep along x reads with lanes along y, a cache line per lane).
+constexpr int ROW_ZONES = 30;
+__device__ __forceinline__ double shfl_up1(double x) { return __shfl_up_sync(0xffffffffu, x, 1); }
+__device__ __forceinline__ double shfl_dn1(double x) { return __shfl_down_sync(0xffffffffu, x, 1); }
+
+// w: the warp's work item (tile fastest, then T1, then T2); all 32 lanes call
+__device__ __forceinline__ void trace_row_x_item(ScratchGeom sg, const double* __restrict__ Q,
+                                                 double* __restrict__ TM, double* __restrict__ TP, StepConst K,
+                                                 SweepRange R, long long w) {
+  const int ntile = (R.nd - R.lod + ROW_ZONES) / ROW_ZONES;  // zones [lod, nd]
+  const long long r = w / ntile;
+  if (r >= (long long)R.ext1 * R.ext2) return;  // uniform over the warp
+  const int lane = threadIdx.x & 31;
+  const int tile = (int)(w - r * ntile);
+  const int j = R.lo1 + (int)(r % R.ext1), k = R.lo2 + (int)(r / R.ext1);
+  const int t0 = R.lod + tile * ROW_ZONES;
+  const int i = t0 - 1 + lane;
+  const long long sc = sg.sc;
+  const long long id = sg.id(i, j, k);
+  const double* __restrict__ qv[5] = {Q + QRHO * sc, Q + QU * sc, Q + QV * sc, Q + QW * sc, Q + QP * sc};
+  // zones up to nd + 1 supply slopes and flattening; their stencil stays in the grown box
+  const bool live = i <= R.nd + 1;
+  double am1[5], a0[5], ap1[5], pm2 = 0.0, pp2 = 0.0;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    am1[v] = live ? qv[v][id - 1] : 0.0;
+    a0[v] = live ? qv[v][id] : 0.0;
+    ap1[v] = live ? qv[v][id + 1] : 0.0;
+  }
+  if (live && K.flatten) {
+    pm2 = qv[4][id - 2];
+    pp2 = qv[4][id + 2];
+  }
+  // this zone's slope and flattening coefficient
+  double sl[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) sl[v] = mc_slope_d(a0[v] - am1[v], ap1[v] - a0[v], am1[v], ap1[v]);
+  const double ct0 = K.flatten ? flat_tilde(pm2, am1[4], ap1[4], pp2, am1[1], ap1[1], K.small_pres) : 1.0;
+  // the interface value at the high face, from the next zone's slope
+  double fp[5], fm[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fp[v] = face_value(a0[v], ap1[v], sl[v], shfl_dn1(sl[v]));
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fm[v] = shfl_up1(fp[v]);
+  const double ctm = shfl_up1(ct0), ctp = shfl_dn1(ct0);
+  if (lane == 0 || lane > ROW_ZONES || i > R.nd) return;
+  double chi = 1.0;
+  if (K.flatten) chi = dless(ap1[4], am1[4]) ? dmin(ct0, ctp) : dmin(ct0, ctm);
+  double am[5], ap[5], dap[5], a6[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) ppm_limit(a0[v], fm[v], fp[v], chi, am[v], ap[v], a6[v], &dap[v]);
+  trace_zone<0>(am, ap, dap, a6, a0, Q[QC * sc + id], Q[QRC * sc + id], Q[QCR * sc + id], Q[QIC2 * sc + id], K, TM,
+                TP, sc, id);
+}
+
+// ---- stages 2-3 along y or z in tiles: a block of TILE_W warps takes 32
+// pencils (consecutive positions of the flattened transverse range, x
+// fastest, so the loads of a warp are consecutive doubles) and TILE_ZONES
+// zones [t0, t0 + TILE_ZONES) along D.  Three phases, each spread over the
+// warps and separated by barriers: the slope and flattening coefficient of
+// every zone of [t0 - 1, t0 + TILE_ZONES], the interface value at the high
+// face of every zone of [t0 - 1, t0 + TILE_ZONES), then the limiter and the
+// tracing of the tile's zones, exchanging the zones' values through shared
+// memory.  Every quantity is formed once per zone (plus the two halo zones
+// per tile) by the sweep's expressions, so the traced states are the
+// sweep's bit for bit; a thread holds one zone's values instead of a
+// sweep's sliding windows, so more warps fit an SM.
+constexpr int TILE_ZONES = 12, TILE_W = 4;
+struct TileSmem {
+  double sl[5][TILE_ZONES + 2][32];  // slopes, rows t0 - 1 .. t0 + TILE_ZONES
+  double ct[TILE_ZONES + 2][32];     // flattening coefficients, same rows
+  double fp[5][TILE_ZONES + 1][32];  // interface value at the high face, rows t0 - 1 .. t0 + TILE_ZONES - 1
+};
+
+// blk: the block's work item (column group fastest, then the tile along D)
+template <int D>
+__device__ __forceinline__ void trace_tile_item(ScratchGeom sg, const double* __restrict__ Q,
+                                                double* __restrict__ TM, double* __restrict__ TP, StepConst K,
+                                                SweepRange R, long long blk, TileSmem& sm) {
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  const long long ncol = (long long)R.ext1 * R.ext2;
+  const long long ngroup = (ncol + 31) / 32;
+  const int tile = (int)(blk / ngroup);
+  const long long col = (blk - tile * ngroup) * 32 + (threadIdx.x & 31);
+  const int warp = threadIdx.x >> 5;
+  const bool cvalid = col < ncol;
+  int c3[3];
+  c3[T1] = R.lo1 + (int)(cvalid ? col % R.ext1 : 0);
+  c3[T2] = R.lo2 + (int)(cvalid ? col / R.ext1 : 0);
+  const int t0 = R.lod + tile * TILE_ZONES;
+  c3[D] = t0;
+  const long long sc = sg.sc;
+  const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
+  const long long id0 = sg.id(c3[0], c3[1], c3[2]);  // zone t0 of this pencil
+  const double* __restrict__ qv[5] = {Q + QRHO * sc, Q + (QU + D) * sc, Q + (QU + T1) * sc, Q + (QU + T2) * sc,
+                                      Q + QP * sc};
+  // phase A: rows r = 0 .. TILE_ZONES + 1 hold zones t0 - 1 + r (live up to nd + 1)
+  for (int r = warp; r < TILE_ZONES + 2; r += TILE_W) {
+    const int i = t0 - 1 + r;
+    if (cvalid && i <= R.nd + 1) {
+      const long long id = id0 + (long long)(r - 1) * st;
+      double am1[5], a0[5], ap1[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        am1[v] = qv[v][id - st];
+        a0[v] = qv[v][id];
+        ap1[v] = qv[v][id + st];
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.sl[v][r][threadIdx.x & 31] = mc_slope_d(a0[v] - am1[v], ap1[v] - a0[v], am1[v], ap1[v]);
+      sm.ct[r][threadIdx.x & 31] =
+          K.flatten ? flat_tilde(qv[4][id - 2 * st], am1[4], ap1[4], qv[4][id + 2 * st], am1[1], ap1[1], K.small_pres)
+                    : 1.0;
+    }
+  }
+  __syncthreads();
+  // phase B: the interface value at the high face of zones t0 - 1 + r, r = 0 .. TILE_ZONES
+  for (int r = warp; r < TILE_ZONES + 1; r += TILE_W) {
+    const int i = t0 - 1 + r;
+    if (cvalid && i <= R.nd) {
+      const long long id = id0 + (long long)(r - 1) * st;
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        sm.fp[v][r][threadIdx.x & 31] =
+            face_value(qv[v][id], qv[v][id + st], sm.sl[v][r][threadIdx.x & 31], sm.sl[v][r + 1][threadIdx.x & 31]);
+    }
+  }
+  __syncthreads();
+  // phase C: limiter and tracing of zones t0 + r, r = 0 .. TILE_ZONES - 1
+  for (int r = warp; r < TILE_ZONES; r += TILE_W) {
+    const int i = t0 + r;
+    if (!cvalid || i > R.nd) continue;
+    const int l = threadIdx.x & 31;
+    const long long id = id0 + (long long)r * st;
+    double a0[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) a0[v] = qv[v][id];
+    double chi = 1.0;
+    if (K.flatten) {
+      const double ct0 = sm.ct[r + 1][l];
+      chi = dless(qv[4][id + st], qv[4][id - st]) ? dmin(ct0, sm.ct[r + 2][l]) : dmin(ct0, sm.ct[r][l]);
+    }
+    double am[5], ap[5], dap[5], a6[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ppm_limit(a0[v], sm.fp[v][r][l], sm.fp[v][r + 1][l], chi, am[v], ap[v], a6[v], &dap[v]);
+    trace_zone<D>(am, ap, dap, a6, a0, Q[QC * sc + id], Q[QRC * sc + id], Q[QCR * sc + id], Q[QIC2 * sc + id], K, TM,
+                  TP, sc, id);
+  }
+}
+
 __device__ __forceinline__ void load5(const double* __restrict__ A, long long sc, long long id, double v[5]) {
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = A[c * sc + id];
@@ -377,22 +535,6 @@ __device__ __forceinline__ void flux3_item(ScratchGeom sg, const double* __restr
   correct(TM, id, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
   hllc_flux<EINF>(sL, sR, D, K, F);
   store5(F3, sg.sc, id, F);
-}
-
-// Warp-granular dynamic scheduling: each warp takes the next 32 work items
-// from a cursor until the item space [0, total) is exhausted.  Used by the
-// tracing sweep, whose items (pencil segments) are few and long, so a static
-// grid would leave a partly filled last wave.
-template <typename F>
-__device__ __forceinline__ void for_dynamic_items(unsigned long long* cursor, long long total, F&& body) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(cursor, 32ull);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if ((long long)base >= total) return;
-    body((long long)base + lane);
-  }
 }
 
 // block-wide max of three non-negative doubles, then one atomicMax per value

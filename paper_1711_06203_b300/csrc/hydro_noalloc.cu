@@ -100,7 +100,7 @@ extern "C" int hydro_advance_box_noalloc(const hydro_box_t* in, const hydro_box_
   a.flags = reinterpret_cast<DevFlags*>(base + NOALLOC_DOUBLES);
   a.events = nullptr;
   // the flag block keeps the previous call's contents: the step itself resets
-  // the speed maxima and sweep cursors; the bad-state flag is sticky, so a
+  // the speed maxima; the bad-state flag is sticky, so a
   // bad state of a call without dt_next_host is reported by the next call
   // that passes one, which clears it
   if (launch_step(a, st, nullptr) != cudaSuccess) return HYDRO_ECUDA;

@@ -12,27 +12,22 @@ __global__ void __launch_bounds__(BLOCK) k_prim(BoxGeom in, ScratchGeom sg, doub
   prim_item(in, sg, Q, K, R, flags, (long long)blockIdx.x * BLOCK + threadIdx.x);
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLOCK) k_trace(ScratchGeom sg, const double* __restrict__ Q,
-                                                 double* __restrict__ TM, double* __restrict__ TP, StepConst K,
-                                                 SweepRange R, unsigned long long* cursor) {
-  for_dynamic_items(cursor, R.count(), [&](long long t) { trace_item<D>(sg, Q, TM, TP, K, R, t); });
+// the x tracing with the lanes of a warp along x (one warp per row segment)
+__global__ void __launch_bounds__(BLOCK) k_trace_row_x(ScratchGeom sg, const double* __restrict__ Q,
+                                                       double* __restrict__ TM, double* __restrict__ TP, StepConst K,
+                                                       SweepRange R) {
+  trace_row_x_item(sg, Q, TM, TP, K, R, ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5);
 }
 
-// blocks of k_trace<D> that fit on the device at once (queried once per process and device)
+// the y and z tracing in tiles of 32 pencils x TILE_ZONES zones (five blocks
+// per SM: 96 registers, a few bytes of spills, were 2 % faster on the Sedov
+// box and 0.4 % on random data than 114 registers at four)
 template <int D>
-int trace_resident_blocks() {
-  static int cached[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 1;
-  if (!cached[dev]) {
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<D>, BLOCK, 0);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = std::max(1, per_sm * sms);
-  }
-  return cached[dev];
+__global__ void __launch_bounds__(TILE_W * 32, 5) k_trace_tile(ScratchGeom sg, const double* __restrict__ Q,
+                                                            double* __restrict__ TM, double* __restrict__ TP,
+                                                            StepConst K, SweepRange R) {
+  __shared__ TileSmem sm;
+  trace_tile_item<D>(sg, Q, TM, TP, K, R, blockIdx.x, sm);
 }
 
 // Face sets of one direction each (first or final fluxes) in one launch:
@@ -129,17 +124,28 @@ __global__ void k_reset_speed(DevFlags* flags) {
 }
 
 __global__ void k_reset_step(DevFlags* flags) {
-  if (threadIdx.x < 3) {
-    flags->maxspeed[threadIdx.x] = 0ull;
-    flags->work[threadIdx.x] = 0ull;
-  }
-}
-
-__global__ void k_zero_cursors(unsigned long long* c, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) c[i] = 0ull;
+  if (threadIdx.x < 3) flags->maxspeed[threadIdx.x] = 0ull;
 }
 
 inline unsigned blocks_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
+
+// the y or z tracing over the pencils and zones of sw, in tiles of 32 pencils x TILE_ZONES zones
+template <int D>
+void launch_trace_tile(const ScratchGeom& sg, const Scratch& s, const StepConst& K, const SweepRange& sw,
+                       cudaStream_t st) {
+  const long long ngroup = ((long long)sw.ext1 * sw.ext2 + 31) / 32;
+  const long long ntile = (sw.nd - sw.lod + TILE_ZONES) / TILE_ZONES;
+  k_trace_tile<D><<<(unsigned)(ngroup * ntile), TILE_W * 32, 0, st>>>(sg, s.Q, s.TM[D], s.TP[D], K, sw);
+}
+
+// the x tracing over the pencils and zones of sw: one warp per row segment of ROW_ZONES zones
+void launch_trace_row_x(const ScratchGeom& sg, const Scratch& s, const StepConst& K, const SweepRange& sw,
+                        cudaStream_t st) {
+  const long long ntile = (sw.nd - sw.lod + ROW_ZONES) / ROW_ZONES;
+  const long long warps = ntile * sw.ext1 * sw.ext2;
+  k_trace_row_x<<<(unsigned)((warps + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], K,
+                                                                                       sw);
+}
 
 // copy the final fluxes on the outer faces (face 0 and face n_d along every
 // active d, transverse interior) into dst, plane after plane in (d, side)
@@ -175,23 +181,26 @@ __global__ void k_record_faces(Scratch s, ScratchGeom sg, int n0, int n1, int n2
   }
 }
 
-// tracing sweep along d over pencils whose transverse coordinates are
-// [-1, n] on the first transverse axis and [lo2, lo2 + ext2) on the second
-void launch_trace(int d, const StepArgs& a, int lo2, int ext2, unsigned long long* cur, cudaStream_t st) {
+// the tracing along d over zones [lod, nd] of the pencils whose transverse
+// coordinates are [-1, n] on the first transverse axis and [lo2, lo2 + ext2)
+// on the second
+void launch_trace_range(int d, const StepArgs& a, int lo2, int ext2, int lod, int nd, cudaStream_t st) {
   const int* n = a.in.n;
   const int t1 = (d == 0) ? 1 : 0;
   SweepRange sw;
   sw.lo1 = -1; sw.ext1 = n[t1] + 2;
   sw.lo2 = lo2; sw.ext2 = ext2;
-  sw.nd = n[d];
-  sw.lod = -1;
+  sw.lod = lod;
+  sw.nd = nd;
   sw.seg = TRACE_SEG;
-  sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
-  const unsigned need = blocks_for(sw.count());
-  const Scratch& s = a.s;
-  if (d == 0) k_trace<0><<<std::min<unsigned>(need, trace_resident_blocks<0>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[0], s.TP[0], a.K, sw, cur);
-  if (d == 1) k_trace<1><<<std::min<unsigned>(need, trace_resident_blocks<1>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[1], s.TP[1], a.K, sw, cur);
-  if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
+  sw.nseg = (nd - lod + TRACE_SEG) / TRACE_SEG;
+  if (d == 0) launch_trace_row_x(a.sg, a.s, a.K, sw, st);
+  if (d == 1) launch_trace_tile<1>(a.sg, a.s, a.K, sw, st);
+  if (d == 2) launch_trace_tile<2>(a.sg, a.s, a.K, sw, st);
+}
+// ... over every zone [-1, n] along d
+void launch_trace(int d, const StepArgs& a, int lo2, int ext2, cudaStream_t st) {
+  launch_trace_range(d, a, lo2, ext2, -1, a.in.n[d], st);
 }
 
 // first fluxes of the directions d in dirs (bit d) over the face ranges r[d], one launch
@@ -308,19 +317,8 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, long long* launches)
     rt.ext[ax] = act ? n[ax] + 2 : 1;
   }
   for (int d = 0; d < dim; ++d) {
-    int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-    SweepRange sw;
-    sw.lo1 = rt.lo[t1]; sw.ext1 = rt.ext[t1];
-    sw.lo2 = rt.lo[t2]; sw.ext2 = rt.ext[t2];
-    sw.nd = n[d];
-    sw.lod = -1;
-    sw.seg = TRACE_SEG;
-    sw.nseg = (n[d] + 2 + TRACE_SEG - 1) / TRACE_SEG;
-    const unsigned need = blocks_for(sw.count());
-    unsigned long long* cur = &a.flags->work[d];
-    if (d == 0) k_trace<0><<<std::min<unsigned>(need, trace_resident_blocks<0>()), BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], a.K, sw, cur);
-    if (d == 1) k_trace<1><<<std::min<unsigned>(need, trace_resident_blocks<1>()), BLOCK, 0, st>>>(sg, s.Q, s.TM[1], s.TP[1], a.K, sw, cur);
-    if (d == 2) k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cur);
+    const int t2 = (d == 2) ? 1 : 2;
+    launch_trace(d, a, rt.lo[t2], rt.ext[t2], st);
   }
   nl += dim;
   mark(ST_FLUX1);
@@ -366,8 +364,7 @@ cudaError_t launch_record_faces(const StepArgs& a, int zlo, int zhi, double* fac
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_slabs(const StepArgs& a, int T, unsigned long long* cursors, double* faces,
-                              cudaStream_t st, long long* launches) {
+cudaError_t launch_step_slabs(const StepArgs& a, int T, double* faces, cudaStream_t st, long long* launches) {
   const int* n = a.in.n;
   const int nslab = (n[2] + T - 1) / T;
   long long nl = 0;
@@ -378,8 +375,7 @@ cudaError_t launch_step_slabs(const StepArgs& a, int T, unsigned long long* curs
   // primitive-state stage, the other stages as zero
   mark(ST_PRIM);
   k_reset_step<<<1, 32, 0, st>>>(a.flags);
-  k_zero_cursors<<<1, 256, 0, st>>>(cursors, 3 * nslab);
-  nl += 2;
+  nl += 1;
   for (int k = 0; k < nslab; ++k) {
     const int z0 = k * T, ze = std::min(T, n[2] - z0);
     StepArgs w = a;
@@ -391,20 +387,9 @@ cudaError_t launch_step_slabs(const StepArgs& a, int T, unsigned long long* curs
     rp.lo[2] = z0 - NG; rp.ext[2] = ze + 2 * NG;
     k_prim<<<blocks_for(rp.count()), BLOCK, 0, st>>>(a.in, a.sg, s.Q, a.K, rp, a.flags);
     // traced states on zones [-1, n] in x and y and planes [z0 - 1, z0 + ze]
-    launch_trace(0, w, z0 - 1, ze + 2, cursors + 3 * k, st);
-    launch_trace(1, w, z0 - 1, ze + 2, cursors + 3 * k + 1, st);
-    {
-      SweepRange sw;
-      sw.lo1 = -1; sw.ext1 = n[0] + 2;
-      sw.lo2 = -1; sw.ext2 = n[1] + 2;
-      sw.lod = z0 - 1;
-      sw.nd = z0 + ze;
-      sw.seg = TRACE_SEG;
-      sw.nseg = (ze + 2 + TRACE_SEG - 1) / TRACE_SEG;
-      const unsigned need = blocks_for(sw.count());
-      k_trace<2><<<std::min<unsigned>(need, trace_resident_blocks<2>()), BLOCK, 0, st>>>(
-          a.sg, s.Q, s.TM[2], s.TP[2], a.K, sw, cursors + 3 * k + 2);
-    }
+    launch_trace(0, w, z0 - 1, ze + 2, st);
+    launch_trace(1, w, z0 - 1, ze + 2, st);
+    launch_trace_range(2, w, -1, n[1] + 2, z0 - 1, z0 + ze, st);
     // first fluxes: x- and y-faces on planes [z0 - 1, z0 + ze], z-faces [z0, z0 + ze]
     Range r1[3];
     for (int d = 0; d < 3; ++d) {
@@ -460,8 +445,7 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     if (cudaEventRecord(p.h2d_done[k], p.h2d) != cudaSuccess) return cudaGetLastError();
   }
   k_reset_step<<<1, 32, 0, st>>>(a.flags);
-  k_zero_cursors<<<1, 64, 0, st>>>(p.cursors, 2 * PIPE_MAX_CHUNKS + 5);
-  nl += 2;
+  nl += 1;
   auto prim = [&](int zlo, int zext) {
     Range r;
     r.lo[0] = -NG; r.ext[0] = n[0] + 2 * NG;
@@ -488,7 +472,6 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
   const int bclo = a.in.bc[2][0], bchi = a.in.bc[2][1];  // 0 outflow, 1 reflect, 2 periodic
   const bool low_early = bclo == 0 || (bclo == 1 && zc(1) >= NG);
   const bool high_early = bchi == 0 || (bchi == 1 && zc(C - 1) <= n[2] - NG);
-  unsigned long long* cg = p.cursors + 2 * PIPE_MAX_CHUNKS;
   for (int k = 0; k < C; ++k) {
     if (cudaStreamWaitEvent(st, p.h2d_done[k], 0) != cudaSuccess) return cudaGetLastError();
     int z0 = zc(k), ze = zc(k + 1) - zc(k);
@@ -502,24 +485,24 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
       prim(n[2], NG);
       ze += 1;
     }
-    launch_trace(0, a, z0, ze, p.cursors + 2 * k, st);
-    launch_trace(1, a, z0, ze, p.cursors + 2 * k + 1, st);
+    launch_trace(0, a, z0, ze, st);
+    launch_trace(1, a, z0, ze, st);
     nl += 2 + flux1_xy(z0, ze);
   }
   if (!low_early) {
     prim(-NG, NG);
-    launch_trace(0, a, -1, 1, cg, st);
-    launch_trace(1, a, -1, 1, cg + 1, st);
+    launch_trace(0, a, -1, 1, st);
+    launch_trace(1, a, -1, 1, st);
     nl += 2 + flux1_xy(-1, 1);
   }
   if (!high_early) {
     prim(n[2], NG);
-    launch_trace(0, a, n[2], 1, cg + 2, st);
-    launch_trace(1, a, n[2], 1, cg + 3, st);
+    launch_trace(0, a, n[2], 1, st);
+    launch_trace(1, a, n[2], 1, st);
     nl += 2 + flux1_xy(n[2], 1);
   }
   // the z sweep
-  launch_trace(2, a, -1, n[1] + 2, cg + 4, st);
+  launch_trace(2, a, -1, n[1] + 2, st);
   nl += 1;
   // first z fluxes on z-faces [0, n_z] x transverse [-1, n], intermediate fluxes F^{d|t}
   {

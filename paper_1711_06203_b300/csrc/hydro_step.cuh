@@ -81,7 +81,6 @@ struct DevFlags {
   int bad;                         // sticky non-physical-state flag
   int pad;
   double dt_next;                  // cfl * min_d dx_d / maxspeed_d
-  unsigned long long work[3];      // work cursors of the three tracing sweeps
 };
 
 // stages of a step, timed separately when a context profiles
@@ -107,12 +106,10 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t stream, long long* launc
 // unshifted).  Each slab computes every intermediate its planes need from
 // the input box itself (the ghost mapping is the whole box's), so planes
 // next to a slab boundary are computed by both slabs with the same values:
-// the result is bitwise that of launch_step.  `cursors`: 3 * ceil(n_z / T)
-// device work counters, zeroed by the step.  `faces` (nullable): record the
+// the result is bitwise that of launch_step.  `faces` (nullable): record the
 // outer-face fluxes slab by slab into this buffer (layout of
 // hydro_ctx_face_flux).
-cudaError_t launch_step_slabs(const StepArgs& a, int T, unsigned long long* cursors, double* faces,
-                              cudaStream_t stream, long long* launches);
+cudaError_t launch_step_slabs(const StepArgs& a, int T, double* faces, cudaStream_t stream, long long* launches);
 // scratch pointers that index a window of planes starting at plane z0 with
 // the whole box's zone coordinates (every pointer moves down by z0 * sz)
 Scratch shift_scratch(const Scratch& s, long long shift);
@@ -138,7 +135,6 @@ struct HostPipe {
   cudaStream_t h2d, d2h;         // copy streams
   cudaEvent_t start, d2h_done;
   cudaEvent_t h2d_done[PIPE_MAX_CHUNKS], upd_done[PIPE_MAX_CHUNKS];
-  unsigned long long* cursors;   // 2 * PIPE_MAX_CHUNKS + 5 device work cursors of the tracing sweeps
 };
 cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t stream, long long* launches);
 // enqueue a CFL estimate of the interior of a box into flags->dt_next
