@@ -6,8 +6,10 @@
 // that box's work items with the same device bodies as the single-box path.
 // The launch sequence of a given set of boxes (a plan) is captured once in a
 // CUDA graph and replayed; per-box time steps are read from device memory at
-// run time, so one graph serves every step.  The pencil-segment length of
-// the tracing sweep is autotuned per box-size class.
+// run time, so one graph serves every step.  The tracing kernel along each
+// axis -- a pencil sweep with a given segment length, or the warp-row (x) and
+// shared-memory tile (y, z) kernels of the single-box step -- is autotuned
+// per box extent.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,6 +64,27 @@ __global__ void __launch_bounds__(BLOCK) kb_trace(const BatchBox* __restrict__ b
   trace_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], item_of(box_first, b));
 }
 
+// the x tracing by warp rows (one warp per ROW_ZONES zones of a pencil)
+__global__ void __launch_bounds__(BLOCK) kb_trace_row_x(const BatchBox* __restrict__ boxes,
+                                                        const int* __restrict__ blk_box,
+                                                        const int* __restrict__ box_first) {
+  const int b = blk_box[blockIdx.x];
+  const BatchBox& B = boxes[b];
+  trace_row_x_item(B.sg, B.s.Q, B.s.TM[0], B.s.TP[0], B.K, B.tr[0], item_of(box_first, b) >> 5);
+}
+
+// the y or z tracing by tiles of 32 pencils x TILE_ZONES zones (one block per tile)
+template <int D>
+__global__ void __launch_bounds__(BLOCK, 5) kb_trace_tile(const BatchBox* __restrict__ boxes,
+                                                          const int* __restrict__ blk_box,
+                                                          const int* __restrict__ box_first) {
+  static_assert(TILE_W * 32 == BLOCK, "a tile is one block");
+  __shared__ TileSmem sm;
+  const int b = blk_box[blockIdx.x];
+  const BatchBox& B = boxes[b];
+  trace_tile_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], blockIdx.x - box_first[b], sm);
+}
+
 template <int D, bool EINF>
 __global__ void __launch_bounds__(BLOCK) kb_flux1(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first) {
@@ -113,7 +136,9 @@ __global__ void kb_finalize(BatchBox* boxes, int nbox, double* __restrict__ dt_n
 }
 
 // ---- host side: plans
-enum LaunchKind { L_PRIM, L_TRACE, L_FLUX1, L_FLUX2, L_FLUX3, L_UPDATE };
+// L_TRACE: the pencil sweep of the boxes whose tmode[d] is 0; L_TRACE_T: the
+// warp rows / tiles of the boxes whose tmode[d] is 1
+enum LaunchKind { L_PRIM, L_TRACE, L_TRACE_T, L_FLUX1, L_FLUX2, L_FLUX3, L_UPDATE };
 
 struct LaunchSpec {
   LaunchKind kind;
@@ -177,13 +202,21 @@ struct hydro_batch_state {
 namespace {
 
 constexpr int MAX_PLANS = 8;
-const int SEG_PARTS[] = {1, 2, 3, 4};
+// tuner candidates per extent: the sweep with 1-4 segments per pencil, or
+// (0) the warp-row / tile kernels
+const int SEG_PARTS[] = {1, 2, 3, 4, 0};
 
 int segment_length(hydro_batch_state* S, int nd) {
   auto it = S->seg_parts.find(nd);
   int parts = (it == S->seg_parts.end()) ? -1 : it->second;
   if (parts <= 0) return TRACE_SEG;
   return (nd + 2 + parts - 1) / parts;
+}
+
+// the tracing kernel of an extent: 1 the warp rows / tiles, 0 the sweep (also untuned extents)
+int trace_mode(hydro_batch_state* S, int nd) {
+  auto it = S->seg_parts.find(nd);
+  return (it != S->seg_parts.end() && it->second == 0) ? 1 : 0;
 }
 
 // per-box ranges of every stage (same ranges as the single-box launch sequence)
@@ -209,6 +242,7 @@ void fill_ranges(BatchBox& B, int dim, hydro_batch_state* S) {
     sw.lod = -1;
     sw.seg = (d < dim) ? segment_length(S, n[d]) : TRACE_SEG;
     sw.nseg = (n[d] + 2 + sw.seg - 1) / sw.seg;
+    B.tmode[d] = (d < dim) ? trace_mode(S, n[d]) : 0;
     Range r = rt;
     r.lo[d] = 0;
     r.ext[d] = n[d] + 1;
@@ -230,10 +264,22 @@ void fill_ranges(BatchBox& B, int dim, hydro_batch_state* S) {
   for (int ax = 0; ax < 3; ++ax) { B.ru.lo[ax] = 0; B.ru.ext[ax] = (ax < dim) ? n[ax] : 1; }
 }
 
+// threads (blocks x BLOCK) of the warp-row / tile tracing of a box along d
+long long tile_items(const BatchBox& B, int d) {
+  const SweepRange& R = B.tr[d];
+  if (d == 0) {
+    const long long warps = (long long)((R.nd - R.lod + ROW_ZONES) / ROW_ZONES) * R.ext1 * R.ext2;
+    return (warps + BLOCK / 32 - 1) / (BLOCK / 32) * BLOCK;
+  }
+  const long long ngroup = ((long long)R.ext1 * R.ext2 + 31) / 32;
+  return ngroup * ((R.nd - R.lod + TILE_ZONES) / TILE_ZONES) * BLOCK;
+}
+
 long long items_of(const BatchBox& B, LaunchKind k, int d, int t) {
   switch (k) {
     case L_PRIM: return B.rp.count();
-    case L_TRACE: return B.tr[d].count();
+    case L_TRACE: return B.tmode[d] ? 0 : B.tr[d].count();
+    case L_TRACE_T: return B.tmode[d] ? tile_items(B, d) : 0;
     case L_FLUX1: return B.r1[d].count();
     case L_FLUX2: return B.r2[d][t].count();
     case L_FLUX3: return B.r3[d].count();
@@ -272,12 +318,18 @@ void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
   const int* bf = p->d_maps + L.first_off;
   BatchBox* B = p->d_boxes;
   const unsigned g = (unsigned)L.nblocks;
+  if (g == 0) return;  // no box of the set takes this kernel
   switch (L.kind) {
     case L_PRIM: kb_prim<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
     case L_TRACE:
       if (L.d == 0) kb_trace<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
       if (L.d == 1) kb_trace<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
       if (L.d == 2) kb_trace<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      break;
+    case L_TRACE_T:
+      if (L.d == 0) kb_trace_row_x<<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 1) kb_trace_tile<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 2) kb_trace_tile<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
       break;
     case L_FLUX1:
       if (p->einfeldt) launch_flux1<true>(L.d, g, B, bb, bf, st);
@@ -295,11 +347,21 @@ void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
   }
 }
 
+// kernels a launch list enqueues (launches without blocks are skipped)
+long long kernels_of(const std::vector<LaunchSpec>& L) {
+  long long k = 0;
+  for (auto& l : L) k += l.nblocks > 0;
+  return k;
+}
+
 // the stage launches of a step, in order
 std::vector<LaunchSpec> launch_list(int dim) {
   std::vector<LaunchSpec> v;
   v.push_back({L_PRIM, 0, 0, 0, 0, 0});
-  for (int d = 0; d < dim; ++d) v.push_back({L_TRACE, d, 0, 0, 0, 0});
+  for (int d = 0; d < dim; ++d) {
+    v.push_back({L_TRACE, d, 0, 0, 0, 0});
+    v.push_back({L_TRACE_T, d, 0, 0, 0, 0});
+  }
   for (int d = 0; d < dim; ++d) v.push_back({L_FLUX1, d, 0, 0, 0, 0});
   if (dim == 3)
     for (int d = 0; d < 3; ++d)
@@ -361,7 +423,7 @@ void load_tuning(hydro_batch_state* S) {
   if (!f) return;
   int nd, parts;
   while (std::fscanf(f, "%d %d", &nd, &parts) == 2)
-    if (nd > 0 && parts >= 1 && parts <= 8) S->seg_parts[nd] = parts;
+    if (nd > 0 && parts >= 0 && parts <= 8) S->seg_parts[nd] = parts;
   std::fclose(f);
 }
 
@@ -374,9 +436,10 @@ void save_tuning(const hydro_batch_state* S) {
   std::fclose(f);
 }
 
-// Time the x-sweep of the tracing stage over the boxes of each untuned size
-// class for every candidate segment count, keep the fastest.  Runs the
-// primitive stage first so the sweep reads real data; writes scratch only.
+// Time the tracing stage over the boxes of each untuned size class for every
+// candidate (the sweep with 1-4 segments per pencil, the warp-row / tile
+// kernels) on the axes of that extent, keep the fastest.  Runs the primitive
+// stage first so the tracing reads real data; writes scratch only.
 int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
   hydro_batch_state* S = ctx->batch;
   std::map<int, std::vector<int>> cls;
@@ -397,19 +460,24 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
     int best = 1;
     for (int parts : SEG_PARTS) {
       if (parts > 1 && (nd + 2 + parts - 1) / parts < 4) continue;
-      // a one-launch sub-batch: the x-sweep (or the first axis of that extent) of the class boxes
+      // a sub-batch of the class boxes with this candidate on their axes of this extent
       std::vector<BatchBox> sub;
       for (int b : kv.second) {
         BatchBox B = boxes[b];
         for (int d = 0; d < dim; ++d) {
           if (B.in.n[d] != nd) continue;
+          B.tmode[d] = parts == 0 ? 1 : 0;
+          if (parts == 0) continue;
           B.tr[d].seg = (nd + 2 + parts - 1) / parts;
           B.tr[d].nseg = (nd + 2 + B.tr[d].seg - 1) / B.tr[d].seg;
         }
         sub.push_back(B);
       }
       std::vector<LaunchSpec> L;
-      for (int d = 0; d < dim; ++d) L.push_back({L_TRACE, d, 0, 0, 0, 0});
+      for (int d = 0; d < dim; ++d) {
+        L.push_back({L_TRACE, d, 0, 0, 0, 0});
+        L.push_back({L_TRACE_T, d, 0, 0, 0, 0});
+      }
       std::vector<int> maps;
       build_maps(sub, L, maps);
       Plan p;
@@ -423,7 +491,7 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
       cudaMemcpyAsync(p.d_boxes, sub.data(), sub.size() * sizeof(BatchBox), cudaMemcpyHostToDevice, st);
       cudaMemcpyAsync(p.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, st);
       p.launches = L;
-      // only the sweeps along axes of this extent matter; time all dims of the sub-batch
+      // only the tracing along axes of this extent changes; time all dims of the sub-batch
       for (int rep = 0; rep < 4; ++rep) {
         if (rep == 1) cudaEventRecord(e0, st);
         for (auto& l : p.launches) enqueue_launch(&p, l, st);
@@ -606,7 +674,7 @@ static int run_direct(hydro_ctx* ctx, const hydro_box_t* in, const hydro_box_t* 
   if (cudaGetLastError() != cudaSuccess) return HYDRO_ECUDA;
   if (enqueue_ms)
     *enqueue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_entry).count();
-  ctx->launches += (long long)p.launches.size() + 2;
+  ctx->launches += kernels_of(p.launches) + 2;
   if (plan_boxes) *plan_boxes = S->d_direct_boxes;
   return read_bad(S->d_direct_bad, nbox, bad_first_host, bad_all_host, st);
 }
@@ -733,7 +801,7 @@ int hydro_batch_run(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t* 
   if (cudaGraphLaunch(plan->exec, st) != cudaSuccess) return HYDRO_ECUDA;
   if (enqueue_ms)
     *enqueue_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_entry).count();
-  ctx->launches += (long long)plan->launches.size() + 2;
+  ctx->launches += kernels_of(plan->launches) + 2;
   return read_bad(plan->d_bad, nbox, bad_first_host, bad_all_host, st);
 }
 
@@ -777,7 +845,7 @@ extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, i
   for (auto& kv : ctx->batch->seg_parts) {
     if (k < nmax) {
       extent[k] = kv.first;
-      segment[k] = (kv.first + 2 + kv.second - 1) / kv.second;
+      segment[k] = kv.second ? (kv.first + 2 + kv.second - 1) / kv.second : 0;
     }
     ++k;
   }

@@ -15,6 +15,7 @@ struct BatchBox {
   double cfl;
   Range rp, ru;
   SweepRange tr[3];
+  int tmode[3];  // tracing along d: 0 the pencil sweep (tr[d].seg zones per segment), 1 warp rows (x) / tiles (y, z)
   Range r1[3], r2[3][3], r3[3];
   DevFlags flags;
 };

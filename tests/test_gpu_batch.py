@@ -1,7 +1,7 @@
 """Batched level step (hydro_advance_batch) against the per-box step and the
 oracle.  The batched kernels run the same per-item device code as the
-single-box kernels; the results do not depend on the sweep segmentation the
-autotuner picks.  With multiply-add contraction on, the compiler may fuse
+single-box kernels; the results do not depend on the tracing kernel (sweep
+segmentation, or warp rows and tiles) the autotuner picks.  With multiply-add contraction on, the compiler may fuse
 differently in the batched kernels, so batch and per-box agree to the parity
 tolerance (observed: 1 ulp); the contraction-free build is bitwise equal to
 the oracle either way."""
@@ -105,6 +105,35 @@ def test_exact_batch_is_bitwise_equal_to_oracle():
         P = oracle.params(3, s, dx=(1 / s[0], 1 / s[1], 1 / s[2]), bc=oracle.BC_PREFILLED, gamma=5 / 3)
         ref, _ = oracle.step(U, P, d)
         assert np.array_equal(_interior(g, 3), _interior(ref, 3))
+
+
+@pytest.mark.parametrize("mode", ["tiles", "sweeps", "mixed"])
+def test_exact_batch_with_each_tracing_kernel(mode, tmp_path, monkeypatch):
+    """The tracing kernel chosen per extent (the sweep with a given segment
+    length, or the warp-row / tile kernels), forced through the tuning cache
+    file: every choice gives the oracle's result bit for bit, in 3-D and 2-D."""
+    sizes3 = SIZES3
+    sizes2 = [(40, 24, 1), (16, 64, 1), (32, 32, 1)]
+    extents = sorted({e for s in sizes3 + sizes2 for e in s if e > 1})
+    pick = {"tiles": lambda e: 0, "sweeps": lambda e: 2, "mixed": lambda e: 0 if e % 16 else 3}[mode]
+    cache = tmp_path / "tune.txt"
+    cache.write_text("".join(f"{e} {pick(e)}\n" for e in extents))
+    monkeypatch.setenv("HYDRO_TUNE_CACHE", str(cache))
+    for dim, sizes in ((3, sizes3), (2, sizes2)):
+        Us = _level(21 + dim, sizes, dim)
+        dts = [1e-3 * (1 + 0.1 * k) for k in range(len(sizes))]
+        ctx = hb.Context(0, "exact")
+        got, _ = _run_batch(ctx, Us, sizes, dim, dts, hb.params(dim, gamma=5 / 3))
+        tuning = ctx.hydro_batch_tuning()
+        ctx.close()
+        for e in extents:
+            want = 0 if pick(e) == 0 else (e + 2 + pick(e) - 1) // pick(e)
+            assert tuning[e] == want
+        for g, U, s, d in zip(got, Us, sizes, dts):
+            P = oracle.params(dim, s[:dim], dx=(1 / s[0], 1 / s[1], 1 / s[2] if dim == 3 else 1.0),
+                              bc=oracle.BC_PREFILLED, gamma=5 / 3)
+            ref, _ = oracle.step(U, P, d)
+            assert np.array_equal(_interior(g, dim), _interior(ref, dim)), (mode, dim, s)
 
 
 def test_graph_replay_uses_new_dt_and_ping_pong_plans():
