@@ -487,6 +487,13 @@ int hydro_ctx_face_flux(hydro_ctx_t* ctx, int d, int side, double* dst, void* st
  * IEEE 2.0*x and 0.5*x. */
 int hydro_selftest_scale2(const double* x, double* twice, double* half, long long n, void* stream);
 
+/* Diagnostics (no counterpart in the paper): the product build forms the
+ * sound speed and 1/rho of a first-solve face state from one refined
+ * reciprocal square root; this runs that helper over x[0..n) (device) into
+ * out[] (device), asynchronously on `stream`, so a test can bound its error
+ * against 1/sqrt(x).  The contraction-free build returns IEEE 1.0/sqrt(x). */
+int hydro_selftest_rsqrt(const double* x, double* out, long long n, void* stream);
+
 /* Diagnostics (no counterpart in the paper): the device's FP64 issue rate,
  * the denominator of the step's FP64 roofline.  Launches nblocks blocks of
  * 256 threads, each thread running 8 independent chains of `iters` FP64

@@ -156,6 +156,7 @@ def lib(variant="default"):
     L.hydro_ctx_record_face_fluxes.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_set_scratch_limit.argtypes = [vp, ctypes.c_size_t]
     L.hydro_selftest_fp64_rate.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    L.hydro_selftest_rsqrt.argtypes = [vp, vp, ctypes.c_longlong, vp]
     L.hydro_advance_box_steps.argtypes = [vp, ctypes.POINTER(hydro_box_t), ctypes.POINTER(hydro_box_t),
                                           ctypes.POINTER(hydro_params_t), ctypes.c_int, vp, vp, vp]
     L.hydro_ctx_face_flux.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -217,6 +218,18 @@ def hydro_selftest_scale2(x, variant="default", stream=None):
     if rc:
         raise HydroError(rc, "hydro_selftest_scale2")
     return t, h
+
+
+def hydro_selftest_rsqrt(x, variant="default", stream=None):
+    """Run the kernels' refined reciprocal square root over a CUDA float64 tensor."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    rc = lib(variant).hydro_selftest_rsqrt(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+                                           _stream_handle(stream))
+    if rc:
+        raise HydroError(rc, "hydro_selftest_rsqrt")
+    return out
 
 
 def hydro_selftest_fp64_rate(nblocks=148 * 8, iters=4096, variant="default", stream=None, reps=3):

@@ -247,6 +247,15 @@ __global__ void k_selftest_divsqrt(const double* __restrict__ x, const double* _
   quo[i] = ddiv(y[i], x[i]);
   sq[i] = dsqrt(x[i]);
 }
+__global__ void k_selftest_rsqrt(const double* __restrict__ x, double* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#ifdef HYDRO_IEEE_DIV_SQRT
+  out[i] = 1.0 / sqrt(x[i]);
+#else
+  out[i] = newton_range(x[i]) ? rsqrt_newton(x[i]) : 1.0 / sqrt(x[i]);
+#endif
+}
 // FP64 issue rate: eight independent multiply-add chains per thread
 __global__ void k_selftest_fp64_rate(double* __restrict__ out, int iters, double a, double b) {
   double x[8];
@@ -647,6 +656,13 @@ int hydro_selftest_intpipe(const double* x, const double* y, double* prod, doubl
   if (!x || !y || !prod || !sum || n < 0) return HYDRO_EINVAL;
   if (n == 0) return HYDRO_OK;
   k_selftest_intpipe<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, prod, sum, n);
+  return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+int hydro_selftest_rsqrt(const double* x, double* out, long long n, void* stream) {
+  if (!x || !out || n < 0) return HYDRO_EINVAL;
+  if (n == 0) return HYDRO_OK;
+  k_selftest_rsqrt<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n);
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 

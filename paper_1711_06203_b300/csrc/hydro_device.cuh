@@ -253,6 +253,15 @@ __device__ __forceinline__ double ddiv(double a, double b) {
   const double r = rcp_newton(ab);
   return mul_i(a, __longlong_as_double(dbits(r) | sign_bits(b)));
 }
+// 1/sqrt(x) for x in the refined range: from the hardware estimate y with
+// e = 1 - x y^2, 1/sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3e^2/8 + ...),
+// the binomial series kept to second order (error 5e^3/16)
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-mul_i(x, y), y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
+}
 __device__ __forceinline__ double dsqrt(double x) {
   if (__builtin_expect(!newton_range(x), 0)) return sqrt(x);
   double y;
@@ -311,6 +320,11 @@ __device__ __forceinline__ void cons_to_prim_flag(const double U[5], const StepC
 // face state for the Riemann solver: rho, u, v, w, p, rho*E, 1/rho
 enum { S_RHO = 0, S_P = 4, S_E = 5, S_INV = 6, NS = 7 };
 
+// sound speed sqrt(gamma p / rho) of a face state
+__device__ __forceinline__ double sound_of(const double s[NS], const StepConst& K) {
+  return dsqrt(mul_i(mul_i(K.gamma, s[S_P]), s[S_INV]));
+}
+
 __device__ __forceinline__ double energy_of(const double q[5], const StepConst& K) {
   return q[4] * K.gm1inv + mul_i(dhalf(q[0]), (mul_i(q[1], q[1]) + q[2] * q[2]) + q[3] * q[3]);
 }
@@ -320,6 +334,29 @@ __device__ __forceinline__ void state_from_prim(const double q[5], const StepCon
   for (int c = 0; c < 5; ++c) s[c] = q[c];
   s[S_E] = energy_of(q, K);
   s[S_INV] = drcp(q[0]);
+}
+
+// the same with the state's sound speed: in the product build 1/rho and
+// sqrt(gamma p / rho) both come from one refined y = 1/sqrt(gamma p rho),
+// as c = (gamma p) y and 1/rho = c y, instead of a reciprocal and a square root
+__device__ __forceinline__ void state_from_prim_c(const double q[5], const StepConst& K, double s[NS], double* c) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) s[v] = q[v];
+  s[S_E] = energy_of(q, K);
+#ifndef HYDRO_IEEE_DIV_SQRT
+  // (the three products after gamma p run on the FP64 pipe: the first-solve
+  // kernel's integer pipes are the busier ones, measured 7 % faster so)
+  const double gp = mul_i(K.gamma, q[4]);
+  const double x = gp * q[0];
+  if (__builtin_expect(newton_range(x), 1)) {
+    const double y = rsqrt_newton(x);
+    *c = gp * y;
+    s[S_INV] = *c * y;
+    return;
+  }
+#endif
+  s[S_INV] = drcp(q[0]);
+  *c = sound_of(s, K);
 }
 
 __device__ __forceinline__ void state_from_cons(const double U[5], const StepConst& K, double s[NS]) {
@@ -435,13 +472,12 @@ __device__ __forceinline__ double integ_minus(double am, double ap, double dap, 
 // K.einfeldt, so a Davis kernel carries none of the Einfeldt code and its
 // registers (compiled together they raised every solver kernel's
 // allocation from 64 to 76-96 registers).
+// HLLC flux of two face states whose sound speeds cl, cr are given
 template <bool EINF>
-__device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[NS], int d, const StepConst& K,
-                                          double F[5]) {
+__device__ __forceinline__ bool hllc_flux_c(const double sL[NS], const double sR[NS], double cl, double cr, int d,
+                                            const StepConst& K, double F[5]) {
   double rl = sL[S_RHO], pl = sL[S_P], ul = sL[1 + d];
   double rr = sR[S_RHO], pr = sR[S_P], ur = sR[1 + d];
-  double cl = dsqrt(mul_i(mul_i(K.gamma, pl), sL[S_INV]));
-  double cr = dsqrt(mul_i(mul_i(K.gamma, pr), sR[S_INV]));
   double sl, sr;
   if (!EINF) {  // Davis
     sl = dmin(ul - cl, ur - cr);
@@ -461,8 +497,16 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
     sr = dmax(ur + cr, utn + ct);
   }
   double ml = mul_i(rl, sl - ul), mr = mul_i(rr, sr - ur);
-  double sstar = ddiv((pr - pl) + ml * ul - mr * ur, ml - mr);
-  int region = ge0(sl) ? 0 : ge0(sstar) ? 1 : gt0(sr) ? 2 : 3;
+  const double num = (pr - pl) + ml * ul - mr * ur, den = ml - mr;
+#ifdef HYDRO_IEEE_DIV_SQRT
+  const double sstar = ddiv(num, den);
+  const bool sstar_ge0 = ge0(sstar);
+#else
+  // the sign of S* = num/den without forming the quotient: a zero numerator
+  // gives +-0 (>= 0), otherwise the quotient is >= 0 when the signs agree
+  const bool sstar_ge0 = !ine(dbits(num) << 1, 0) || !ilt(dbits(num) ^ dbits(den), 0);
+#endif
+  int region = ge0(sl) ? 0 : sstar_ge0 ? 1 : gt0(sr) ? 2 : 3;
   bool left = region <= 1;
   // the chosen side's state, component by component (selecting a pointer to
   // one of the two arrays would force both into local memory)
@@ -483,7 +527,16 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   // star state, with f = rho (S_K - u)/(S_K - S*), p* = p + rho (S_K - u)(S* - u)
   // and (rho E)* = f E/rho + (S* - u)(f S* + p/(S_K - S*))
   double sk = left ? sl : sr, mk = left ? ml : mr;
+#ifdef HYDRO_IEEE_DIV_SQRT
   double r = drcp(sk - sstar);
+#else
+  // S* = num/den and r = 1/(S_K - S*) = den/q with q = S_K den - num, both
+  // from one reciprocal g = 1/(den q): 1/den = g q, 1/q = g den
+  const double q = fma(sk, den, -num);
+  const double g = drcp(mul_i(den, q));
+  const double sstar = mul_i(num, mul_i(g, q));
+  const double r = mul_i(den, mul_i(g, den));
+#endif
   double f = mul_i(mk, r);
   double du = sstar - un;
   double mstar = mul_i(f, sstar);
@@ -494,6 +547,12 @@ __device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[N
   for (int k = 0; k < 3; ++k) F[1 + k] = (k == d) ? mstar * sstar + pstar : mul_i(mstar, s[1 + k]);
   F[4] = mul_i(sstar, Estar + pstar);
   return left;
+}
+
+template <bool EINF>
+__device__ __forceinline__ bool hllc_flux(const double sL[NS], const double sR[NS], int d, const StepConst& K,
+                                          double F[5]) {
+  return hllc_flux_c<EINF>(sL, sR, sound_of(sL, K), sound_of(sR, K), d, K, F);
 }
 
 }  // namespace hydro

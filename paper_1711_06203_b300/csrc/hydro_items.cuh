@@ -443,15 +443,16 @@ __device__ __forceinline__ void load5(const double* __restrict__ A, long long sc
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = A[c * sc + id];
 }
-// face state of a traced state for its (only) first Riemann solve; the
-// conserved form (rho*u, rho*v, rho*w, rho*E) is stored beside the primitive
-// fields, since the transverse corrections update it three more times
+// face state (and its sound speed *cs) of a traced state for its (only)
+// first Riemann solve; the conserved form (rho*u, rho*v, rho*w, rho*E) is
+// stored beside the primitive fields, since the transverse corrections update
+// it three more times
 __device__ __forceinline__ void traced_state(double* __restrict__ T, long long sc, long long id,
-                                             const StepConst& K, double s[NS]) {
+                                             const StepConst& K, double s[NS], double* cs) {
   double q[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) q[c] = T[c * sc + id];
-  state_from_prim(q, K, s);
+  for (int v = 0; v < 5; ++v) q[v] = T[v * sc + id];
+  state_from_prim_c(q, K, s, cs);
 #pragma unroll
   for (int c = 1; c < 4; ++c) T[(TS_MOM + c - 1) * sc + id] = mul_i(q[0], q[c]);
   T[TS_E * sc + id] = s[S_E];
@@ -470,10 +471,10 @@ __device__ __forceinline__ void flux1_item(ScratchGeom sg, double* __restrict__ 
   if (!range_zone(R, t, i, j, k)) return;
   const long long st = (D == 0) ? 1 : (D == 1) ? sg.sy : sg.sz;
   const long long id = sg.id(i, j, k);
-  double sL[NS], sR[NS], F[5];
-  traced_state(TP, sg.sc, id - st, K, sL);
-  traced_state(TM, sg.sc, id, K, sR);
-  hllc_flux<EINF>(sL, sR, D, K, F);
+  double sL[NS], sR[NS], F[5], cl, cr;
+  traced_state(TP, sg.sc, id - st, K, sL, &cl);
+  traced_state(TM, sg.sc, id, K, sR, &cr);
+  hllc_flux_c<EINF>(sL, sR, cl, cr, D, K, F);
   store5(F1, sg.sc, id, F);
 }
 

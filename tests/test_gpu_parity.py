@@ -360,6 +360,21 @@ def test_reciprocal_quotient_sqrt_error_bounds():
             assert _ulps(g[fin], w[fin]).max() <= bound, (variant, _ulps(g[fin], w[fin]).max())
 
 
+def test_reciprocal_square_root_error_bound():
+    """The product build's refined 1/sqrt(x) (the first solves' sound speed
+    and 1/rho come from it) stays within 2 ulp of the correctly rounded value
+    over 1e-280..1e280; outside the refined range and in the contraction-free
+    build it is IEEE 1.0/sqrt(x)."""
+    rng = np.random.default_rng(8)
+    x = np.concatenate([10.0 ** rng.uniform(-280, 280, 400000), rng.uniform(0.5, 2.0, 100000),
+                        [1.0, 4.0, 0.25, 2.0, 1e-310, 1.7976931348623157e308]])
+    want = (1.0 / np.sqrt(x.astype(np.longdouble))).astype(np.float64)
+    for variant, bound in (("exact", 1), ("default", 2)):
+        got = hb.hydro_selftest_rsqrt(torch.from_numpy(x).cuda(), variant).cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert _ulps(got, want).max() <= bound, (variant, _ulps(got, want).max())
+
+
 def test_host_buffer_step_matches_device_step():
     """hydro_advance_box_host on pageable and pinned host buffers gives the
     device path's result bit for bit: 3-D boxes with derived faces (interior
