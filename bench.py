@@ -406,7 +406,8 @@ def bench_batch(args, dev, stream, cpu_sample=False):
             "per_box_graph_zone_updates_per_s": zones / (ms_graph * 1e-3) if ms_graph else None,
             "speedup_vs_per_box_graph": ms_graph / ms_batch if ms_graph else None, "per_box_graph_error": graph_error,
             "per_box_launches_per_step": launches_plain, "plan_build_ms": plan_ms,
-            "sweep_segment_by_extent": {str(k): v for k, v in sorted(tuning.items())},
+            "tracing_by_axis_extent": {f"{'xyz'[a]}{e}": (f"sweep {v}" if v else "rows/tiles")
+                                       for (a, e), v in sorted(tuning.items())},
             "l2": "working set 3.7 GB of state + scratch, larger than L2", "cpu_oracle": cpu,
             "gpu_over_cpu_oracle": (zones / (ms_batch * 1e-3)) / cpu["zone_updates_per_s"] if cpu else None}
 

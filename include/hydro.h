@@ -146,8 +146,9 @@ int hydro_advance_box(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_box_t
  *    state is recorded in the context (hydro_ctx_check).
  *  - The first call for a given set of descriptors, params and dt arrays
  *    builds a plan: per-box work tables, scratch for all boxes in one
- *    context-owned pool, the tracing kernel per box extent (a pencil sweep
- *    with 1-4 segments per pencil, or the warp-row / tile kernels; timed on
+ *    context-owned pool, the tracing kernel per axis and box extent (a
+ *    pencil sweep with 1-4 segments per pencil, or the warp-row / tile
+ *    kernels; timed on
  *    the boxes unless HYDRO_FLAG_NO_AUTOTUNE, which takes 16-zone sweep
  *    segments; remembered in the context, and in the file named by the
  *    environment variable HYDRO_TUNE_CACHE if set) and a CUDA graph of the
@@ -203,11 +204,11 @@ int hydro_fill_boundary(hydro_ctx_t* ctx, const hydro_box_t* boxes, const int* l
  * enqueued on `stream`. */
 int hydro_level_min_dt(const double* dt_next_dev, double* dt_dev, int nbox, void* stream);
 
-/* The autotuned tracing kernels of a context: up to nmax pairs (box extent
- * along the tracing axis, zones per pencil segment of the sweep, or 0 for the
+/* The autotuned tracing kernels of a context: up to nmax triples (axis, box
+ * extent along it, zones per pencil segment of the sweep or 0 for the
  * warp-row (x) / shared-memory tile (y, z) kernels) into the host arrays
- * extent/segment.  Returns the number of tuned extents. */
-int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax);
+ * axis/extent/segment.  Returns the number of tuned (axis, extent) classes. */
+int hydro_batch_tuning(hydro_ctx_t* ctx, int* axis, int* extent, int* segment, int nmax);
 
 /* hydro_advance_box on host buffers: in->u and out->u point to host memory
  * (pinned or pageable) holding grown boxes in the natural layout (stride[0]

@@ -133,7 +133,8 @@ def lib(variant="default"):
     L.hydro_advance_box_host.argtypes = [vp, B, B, P, ctypes.c_double, D, vp]
     L.hydro_advance_box_retry.argtypes = [vp, B, B, P, ctypes.c_double, ctypes.c_int, D, D, vp]
     L.hydro_advance_batch.argtypes = [vp, B, B, ctypes.c_int, P, vp, vp, ctypes.POINTER(ctypes.c_int), vp]
-    L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.hydro_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     IP = ctypes.POINTER(ctypes.c_int)
     L.hydro_fill_boundary.argtypes = [vp, B, IP, ctypes.c_int, ctypes.c_int, IP, IP, vp]
     L.hydro_level_min_dt.argtypes = [vp, vp, ctypes.c_int, vp]
@@ -426,10 +427,12 @@ class Context:
             raise HydroError(rc, "hydro_level_min_dt")
 
     def hydro_batch_tuning(self):
-        ext = (ctypes.c_int * 64)()
-        seg = (ctypes.c_int * 64)()
-        k = self.L.hydro_batch_tuning(self.h, ext, seg, 64)
-        return {ext[i]: seg[i] for i in range(min(k, 64))}
+        """{(axis, extent): zones per sweep segment, or 0 for the warp rows / tiles}"""
+        ax = (ctypes.c_int * 192)()
+        ext = (ctypes.c_int * 192)()
+        seg = (ctypes.c_int * 192)()
+        k = self.L.hydro_batch_tuning(self.h, ax, ext, seg, 192)
+        return {(ax[i], ext[i]): seg[i] for i in range(min(k, 192))}
 
     STAGES = ("prim", "trace", "flux1", "flux2", "flux3", "update")
 

@@ -37,6 +37,23 @@ __device__ __forceinline__ long long item_of(const int* box_first, int b) {
   return (long long)(blockIdx.x - box_first[b]) * BLOCK + threadIdx.x;
 }
 
+// the box of this block: from the per-block table when the plan has one
+// (captured plans), else by binary search over the boxes' first blocks
+// (direct launches, which then upload nbox ints per launch instead of one
+// per block; a box with no blocks in this launch shares its first block
+// with the next one, and the search takes the last such box)
+__device__ __forceinline__ int box_of_block(const int* __restrict__ blk_box, const int* __restrict__ box_first,
+                                            int nbox) {
+  if (blk_box) return blk_box[blockIdx.x];
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (box_first[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void kb_prepare(BatchBox* boxes, int nbox, const double* __restrict__ dt_dev) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbox) return;
@@ -50,16 +67,16 @@ __global__ void kb_prepare(BatchBox* boxes, int nbox, const double* __restrict__
 }
 
 __global__ void __launch_bounds__(BLOCK) kb_prim(BatchBox* boxes, const int* __restrict__ blk_box,
-                                                 const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+                                                 const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   BatchBox& B = boxes[b];
   prim_item(B.in, B.sg, B.s.Q, B.K, B.rp, &B.flags, item_of(box_first, b));
 }
 
 template <int D>
 __global__ void __launch_bounds__(BLOCK) kb_trace(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
-                                                  const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+                                                  const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];
   trace_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], item_of(box_first, b));
 }
@@ -67,8 +84,8 @@ __global__ void __launch_bounds__(BLOCK) kb_trace(const BatchBox* __restrict__ b
 // the x tracing by warp rows (one warp per ROW_ZONES zones of a pencil)
 __global__ void __launch_bounds__(BLOCK) kb_trace_row_x(const BatchBox* __restrict__ boxes,
                                                         const int* __restrict__ blk_box,
-                                                        const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+                                                        const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];
   trace_row_x_item(B.sg, B.s.Q, B.s.TM[0], B.s.TP[0], B.K, B.tr[0], item_of(box_first, b) >> 5);
 }
@@ -77,26 +94,26 @@ __global__ void __launch_bounds__(BLOCK) kb_trace_row_x(const BatchBox* __restri
 template <int D>
 __global__ void __launch_bounds__(BLOCK, 5) kb_trace_tile(const BatchBox* __restrict__ boxes,
                                                           const int* __restrict__ blk_box,
-                                                          const int* __restrict__ box_first) {
+                                                          const int* __restrict__ box_first, int nbox) {
   static_assert(TILE_W * 32 == BLOCK, "a tile is one block");
   __shared__ TileSmem sm;
-  const int b = blk_box[blockIdx.x];
+  const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];
   trace_tile_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], blockIdx.x - box_first[b], sm);
 }
 
 template <int D, bool EINF>
 __global__ void __launch_bounds__(BLOCK) kb_flux1(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
-                                                  const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+                                                  const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];  // the traced-state arrays are written through B.s pointers
   flux1_item<D, EINF>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[D], B.K, B.r1[D], item_of(box_first, b));
 }
 
 template <int D, int T, bool EINF>
 __global__ void __launch_bounds__(BLOCK) kb_flux2(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
-                                                  const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+                                                  const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];
   flux2_item<D, T, EINF>(B.sg, B.s.TP[D], B.s.TM[D], B.s.F1[T], B.s.F2[D][T], B.K, B.r2[D][T], item_of(box_first, b));
 }
@@ -105,8 +122,8 @@ __global__ void __launch_bounds__(BLOCK) kb_flux2(const BatchBox* __restrict__ b
 // otherwise takes 94 and loses a third of its resident warps)
 template <int D, bool THREE, bool EINF>
 __global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK)) kb_flux3(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
-                                                  const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+                                                  const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];
   constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
   const double* fa = THREE ? B.s.F2[T1][T2] : B.s.F1[T1];
@@ -116,8 +133,8 @@ __global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK)) kb_flux3(const Ba
 
 // (held to 64 registers: 100 unbounded; a bound of 6 blocks per SM was no faster)
 __global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK))
-    kb_update(BatchBox* boxes, const int* __restrict__ blk_box, const int* __restrict__ box_first) {
-  const int b = blk_box[blockIdx.x];
+    kb_update(BatchBox* boxes, const int* __restrict__ blk_box, const int* __restrict__ box_first, int nbox) {
+  const int b = box_of_block(blk_box, box_first, nbox);
   BatchBox& B = boxes[b];
   update_item(B.in, B.out, B.sg, B.s.F3[0], B.s.F3[1], B.K.dim == 3 ? B.s.F3[2] : B.s.F3[0], B.K, B.ru, &B.flags,
               item_of(box_first, b));
@@ -151,6 +168,7 @@ struct LaunchSpec {
 struct Plan {
   uint64_t key = 0;
   int nbox = 0, dim = 0;
+  bool tables = true;     // per-block box tables in d_maps (else kernels search box_first)
   bool einfeldt = false;  // Einfeldt outer wave speeds (every box shares the flags)
   BatchBox* d_boxes = nullptr;
   int* d_maps = nullptr;
@@ -188,7 +206,8 @@ struct hydro_batch_state {
   size_t scratch_bytes = 0;
   cudaStream_t capture = nullptr;
   uint64_t clock = 0;
-  // autotuned number of segments per pencil, keyed by box extent along the sweep
+  // autotuned tracing kernel per axis and box extent along it (key: tune_key):
+  // segments per pencil of the sweep, or 0 for the warp rows / tiles
   std::map<int, int> seg_parts;
   bool tune_loaded = false;
   // direct (uncaptured) launches: descriptors, block tables and flags of the
@@ -206,16 +225,18 @@ constexpr int MAX_PLANS = 8;
 // (0) the warp-row / tile kernels
 const int SEG_PARTS[] = {1, 2, 3, 4, 0};
 
-int segment_length(hydro_batch_state* S, int nd) {
-  auto it = S->seg_parts.find(nd);
+int tune_key(int d, int nd) { return d * 65536 + nd; }
+
+int segment_length(hydro_batch_state* S, int d, int nd) {
+  auto it = S->seg_parts.find(tune_key(d, nd));
   int parts = (it == S->seg_parts.end()) ? -1 : it->second;
   if (parts <= 0) return TRACE_SEG;
   return (nd + 2 + parts - 1) / parts;
 }
 
 // the tracing kernel of an extent: 1 the warp rows / tiles, 0 the sweep (also untuned extents)
-int trace_mode(hydro_batch_state* S, int nd) {
-  auto it = S->seg_parts.find(nd);
+int trace_mode(hydro_batch_state* S, int d, int nd) {
+  auto it = S->seg_parts.find(tune_key(d, nd));
   return (it != S->seg_parts.end() && it->second == 0) ? 1 : 0;
 }
 
@@ -240,9 +261,9 @@ void fill_ranges(BatchBox& B, int dim, hydro_batch_state* S) {
     sw.lo2 = rt.lo[t2]; sw.ext2 = rt.ext[t2];
     sw.nd = n[d];
     sw.lod = -1;
-    sw.seg = (d < dim) ? segment_length(S, n[d]) : TRACE_SEG;
+    sw.seg = (d < dim) ? segment_length(S, d, n[d]) : TRACE_SEG;
     sw.nseg = (n[d] + 2 + sw.seg - 1) / sw.seg;
-    B.tmode[d] = (d < dim) ? trace_mode(S, n[d]) : 0;
+    B.tmode[d] = (d < dim) ? trace_mode(S, d, n[d]) : 0;
     Range r = rt;
     r.lo[d] = 0;
     r.ext[d] = n[d] + 1;
@@ -289,61 +310,64 @@ long long items_of(const BatchBox& B, LaunchKind k, int d, int t) {
 
 // solver launches, per wave-speed choice (EINF: Einfeldt, else Davis)
 template <bool EINF>
-void launch_flux1(int d, unsigned g, const BatchBox* B, const int* bb, const int* bf, cudaStream_t st) {
-  if (d == 0) kb_flux1<0, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
-  if (d == 1) kb_flux1<1, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
-  if (d == 2) kb_flux1<2, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+void launch_flux1(int d, unsigned g, const BatchBox* B, const int* bb, const int* bf, int nb, cudaStream_t st) {
+  if (d == 0) kb_flux1<0, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+  if (d == 1) kb_flux1<1, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+  if (d == 2) kb_flux1<2, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
 }
 template <bool EINF>
-void launch_flux2(int d, int t, unsigned g, const BatchBox* B, const int* bb, const int* bf, cudaStream_t st) {
+void launch_flux2(int d, int t, unsigned g, const BatchBox* B, const int* bb, const int* bf, int nb,
+                  cudaStream_t st) {
 #define F2(DD, TT) \
-  if (d == DD && t == TT) kb_flux2<DD, TT, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+  if (d == DD && t == TT) kb_flux2<DD, TT, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
   F2(0, 1) F2(0, 2) F2(1, 0) F2(1, 2) F2(2, 0) F2(2, 1)
 #undef F2
 }
 template <bool EINF>
-void launch_flux3(int d, int dim, unsigned g, const BatchBox* B, const int* bb, const int* bf, cudaStream_t st) {
+void launch_flux3(int d, int dim, unsigned g, const BatchBox* B, const int* bb, const int* bf, int nb,
+                  cudaStream_t st) {
   if (dim == 3) {
-    if (d == 0) kb_flux3<0, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
-    if (d == 1) kb_flux3<1, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
-    if (d == 2) kb_flux3<2, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+    if (d == 0) kb_flux3<0, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+    if (d == 1) kb_flux3<1, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+    if (d == 2) kb_flux3<2, true, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
   } else {
-    if (d == 0) kb_flux3<0, false, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
-    if (d == 1) kb_flux3<1, false, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf);
+    if (d == 0) kb_flux3<0, false, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+    if (d == 1) kb_flux3<1, false, EINF><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
   }
 }
 
 void enqueue_launch(const Plan* p, const LaunchSpec& L, cudaStream_t st) {
-  const int* bb = p->d_maps + L.map_off;
+  const int* bb = p->tables ? p->d_maps + L.map_off : nullptr;
   const int* bf = p->d_maps + L.first_off;
+  const int nb = p->nbox;
   BatchBox* B = p->d_boxes;
   const unsigned g = (unsigned)L.nblocks;
   if (g == 0) return;  // no box of the set takes this kernel
   switch (L.kind) {
-    case L_PRIM: kb_prim<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
+    case L_PRIM: kb_prim<<<g, BLOCK, 0, st>>>(B, bb, bf, nb); break;
     case L_TRACE:
-      if (L.d == 0) kb_trace<0><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 1) kb_trace<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 2) kb_trace<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 0) kb_trace<0><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+      if (L.d == 1) kb_trace<1><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+      if (L.d == 2) kb_trace<2><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
       break;
     case L_TRACE_T:
-      if (L.d == 0) kb_trace_row_x<<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 1) kb_trace_tile<1><<<g, BLOCK, 0, st>>>(B, bb, bf);
-      if (L.d == 2) kb_trace_tile<2><<<g, BLOCK, 0, st>>>(B, bb, bf);
+      if (L.d == 0) kb_trace_row_x<<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+      if (L.d == 1) kb_trace_tile<1><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
+      if (L.d == 2) kb_trace_tile<2><<<g, BLOCK, 0, st>>>(B, bb, bf, nb);
       break;
     case L_FLUX1:
-      if (p->einfeldt) launch_flux1<true>(L.d, g, B, bb, bf, st);
-      else launch_flux1<false>(L.d, g, B, bb, bf, st);
+      if (p->einfeldt) launch_flux1<true>(L.d, g, B, bb, bf, nb, st);
+      else launch_flux1<false>(L.d, g, B, bb, bf, nb, st);
       break;
     case L_FLUX2:
-      if (p->einfeldt) launch_flux2<true>(L.d, L.t, g, B, bb, bf, st);
-      else launch_flux2<false>(L.d, L.t, g, B, bb, bf, st);
+      if (p->einfeldt) launch_flux2<true>(L.d, L.t, g, B, bb, bf, nb, st);
+      else launch_flux2<false>(L.d, L.t, g, B, bb, bf, nb, st);
       break;
     case L_FLUX3:
-      if (p->einfeldt) launch_flux3<true>(L.d, p->dim, g, B, bb, bf, st);
-      else launch_flux3<false>(L.d, p->dim, g, B, bb, bf, st);
+      if (p->einfeldt) launch_flux3<true>(L.d, p->dim, g, B, bb, bf, nb, st);
+      else launch_flux3<false>(L.d, p->dim, g, B, bb, bf, nb, st);
       break;
-    case L_UPDATE: kb_update<<<g, BLOCK, 0, st>>>(B, bb, bf); break;
+    case L_UPDATE: kb_update<<<g, BLOCK, 0, st>>>(B, bb, bf, nb); break;
   }
 }
 
@@ -372,8 +396,10 @@ std::vector<LaunchSpec> launch_list(int dim) {
   return v;
 }
 
-// block tables of every launch for the given box descriptors (host)
-void build_maps(const std::vector<BatchBox>& boxes, std::vector<LaunchSpec>& L, std::vector<int>& maps) {
+// block tables of every launch for the given box descriptors (host): each
+// box's first block, and with `blocks` the box of every block
+void build_maps(const std::vector<BatchBox>& boxes, std::vector<LaunchSpec>& L, std::vector<int>& maps,
+                bool blocks = true) {
   const int nbox = (int)boxes.size();
   maps.clear();
   for (auto& l : L) {
@@ -386,6 +412,7 @@ void build_maps(const std::vector<BatchBox>& boxes, std::vector<LaunchSpec>& L, 
     }
     l.nblocks = (int)total;
     l.map_off = maps.size();
+    if (!blocks) continue;
     maps.resize(maps.size() + total);
     for (int b = 0; b < nbox; ++b) {
       long long nb = nblk(items_of(boxes[b], l.kind, l.d, l.t));
@@ -414,16 +441,18 @@ int ensure_batch_scratch(hydro_ctx* ctx, size_t bytes) {
   return HYDRO_OK;
 }
 
-// optional persisted tuning: "nd parts" lines in the file named by HYDRO_TUNE_CACHE
+// optional persisted tuning: "axis extent parts" lines in the file named by
+// HYDRO_TUNE_CACHE (parts: segments per pencil of the sweep, 0 for the warp
+// rows / tiles)
 void load_tuning(hydro_batch_state* S) {
   S->tune_loaded = true;
   const char* path = std::getenv("HYDRO_TUNE_CACHE");
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int nd, parts;
-  while (std::fscanf(f, "%d %d", &nd, &parts) == 2)
-    if (nd > 0 && parts >= 0 && parts <= 8) S->seg_parts[nd] = parts;
+  int d, nd, parts;
+  while (std::fscanf(f, "%d %d %d", &d, &nd, &parts) == 3)
+    if (d >= 0 && d < 3 && nd > 0 && nd < 65536 && parts >= 0 && parts <= 8) S->seg_parts[tune_key(d, nd)] = parts;
   std::fclose(f);
 }
 
@@ -432,20 +461,23 @@ void save_tuning(const hydro_batch_state* S) {
   if (!path) return;
   FILE* f = std::fopen(path, "w");
   if (!f) return;
-  for (auto& kv : S->seg_parts) std::fprintf(f, "%d %d\n", kv.first, kv.second);
+  for (auto& kv : S->seg_parts) std::fprintf(f, "%d %d %d\n", kv.first / 65536, kv.first % 65536, kv.second);
   std::fclose(f);
 }
 
-// Time the tracing stage over the boxes of each untuned size class for every
-// candidate (the sweep with 1-4 segments per pencil, the warp-row / tile
-// kernels) on the axes of that extent, keep the fastest.  Runs the primitive
-// stage first so the tracing reads real data; writes scratch only.
+// Time the tracing along each axis over the boxes of each untuned size class
+// (axis d, extent nd) for every candidate (the sweep with 1-4 segments per
+// pencil, the warp-row (x) / tile (y, z) kernels), keep the fastest.  Runs
+// the primitive stage first so the tracing reads real data; writes scratch
+// only.
 int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
   hydro_batch_state* S = ctx->batch;
-  std::map<int, std::vector<int>> cls;
+  std::map<int, std::vector<int>> cls;  // tune_key -> boxes
   for (int b = 0; b < (int)boxes.size(); ++b)
-    for (int d = 0; d < dim; ++d)
-      if (!S->seg_parts.count(boxes[b].in.n[d])) cls[boxes[b].in.n[d]].push_back(b);
+    for (int d = 0; d < dim; ++d) {
+      const int key = tune_key(d, boxes[b].in.n[d]);
+      if (!S->seg_parts.count(key)) cls[key].push_back(b);
+    }
   if (cls.empty()) return HYDRO_OK;
   cudaStream_t st = S->capture;
   cudaEvent_t e0, e1;
@@ -455,32 +487,27 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
   enqueue_launch(tmp, tmp->launches[0], st);
   int rc = HYDRO_OK;
   for (auto& kv : cls) {
-    const int nd = kv.first;
+    const int ad = kv.first / 65536, nd = kv.first % 65536;
     float best_ms = 1e30f;
     int best = 1;
     for (int parts : SEG_PARTS) {
       if (parts > 1 && (nd + 2 + parts - 1) / parts < 4) continue;
-      // a sub-batch of the class boxes with this candidate on their axes of this extent
+      // a sub-batch of the class boxes with this candidate along axis ad
       std::vector<BatchBox> sub;
       for (int b : kv.second) {
         BatchBox B = boxes[b];
-        for (int d = 0; d < dim; ++d) {
-          if (B.in.n[d] != nd) continue;
-          B.tmode[d] = parts == 0 ? 1 : 0;
-          if (parts == 0) continue;
-          B.tr[d].seg = (nd + 2 + parts - 1) / parts;
-          B.tr[d].nseg = (nd + 2 + B.tr[d].seg - 1) / B.tr[d].seg;
+        B.tmode[ad] = parts == 0 ? 1 : 0;
+        if (parts > 0) {
+          B.tr[ad].seg = (nd + 2 + parts - 1) / parts;
+          B.tr[ad].nseg = (nd + 2 + B.tr[ad].seg - 1) / B.tr[ad].seg;
         }
         sub.push_back(B);
       }
-      std::vector<LaunchSpec> L;
-      for (int d = 0; d < dim; ++d) {
-        L.push_back({L_TRACE, d, 0, 0, 0, 0});
-        L.push_back({L_TRACE_T, d, 0, 0, 0, 0});
-      }
+      std::vector<LaunchSpec> L = {{L_TRACE, ad, 0, 0, 0, 0}, {L_TRACE_T, ad, 0, 0, 0, 0}};
       std::vector<int> maps;
       build_maps(sub, L, maps);
       Plan p;
+      p.nbox = (int)sub.size();
       if (cudaMalloc(&p.d_boxes, sub.size() * sizeof(BatchBox)) != cudaSuccess ||
           cudaMalloc(&p.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -491,7 +518,6 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
       cudaMemcpyAsync(p.d_boxes, sub.data(), sub.size() * sizeof(BatchBox), cudaMemcpyHostToDevice, st);
       cudaMemcpyAsync(p.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, st);
       p.launches = L;
-      // only the tracing along axes of this extent changes; time all dims of the sub-batch
       for (int rep = 0; rep < 4; ++rep) {
         if (rep == 1) cudaEventRecord(e0, st);
         for (auto& l : p.launches) enqueue_launch(&p, l, st);
@@ -507,7 +533,7 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
       if (ms < best_ms) { best_ms = ms; best = parts; }
     }
     if (rc) break;
-    S->seg_parts[nd] = best;
+    S->seg_parts[kv.first] = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -571,6 +597,7 @@ static int build_boxes(hydro_ctx* ctx, const hydro_box_t* in, const hydro_box_t*
   if (tune) {
     // a throw-away plan holding only the primitive stage, for the tuner's input
     Plan tmp;
+    tmp.nbox = nbox;
     std::vector<LaunchSpec> L = {{L_PRIM, 0, 0, 0, 0, 0}};
     std::vector<int> maps;
     build_maps(boxes, L, maps);
@@ -633,13 +660,14 @@ static int run_direct(hydro_ctx* ctx, const hydro_box_t* in, const hydro_box_t* 
   std::vector<BatchBox> boxes;
   int rc = build_boxes(ctx, in, out, nbox, params, pstride, dim, tune, st, boxes);
   if (rc) return rc;
-  Plan p;  // launch list and block tables only; the buffers belong to S
+  Plan p;  // launch list and first blocks only; the buffers belong to S
   p.nbox = nbox;
   p.dim = dim;
+  p.tables = false;
   p.einfeldt = (params[0].flags & HYDRO_FLAG_EINFELDT) != 0;
   p.launches = launch_list(dim);
   std::vector<int> maps;
-  build_maps(boxes, p.launches, maps);
+  build_maps(boxes, p.launches, maps, false);
   if ((size_t)nbox > S->direct_box_cap || maps.size() > S->direct_map_cap) {
     if (S->d_direct_boxes) cudaFree(S->d_direct_boxes);
     if (S->d_direct_maps) cudaFree(S->d_direct_maps);
@@ -838,14 +866,15 @@ extern "C" int hydro_advance_box_steps(hydro_ctx_t* ctx, const hydro_box_t* a, c
   return HYDRO_OK;
 }
 
-extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* extent, int* segment, int nmax) {
-  if (!ctx || nmax < 0 || (nmax > 0 && (!extent || !segment))) return HYDRO_EINVAL;
+extern "C" int hydro_batch_tuning(hydro_ctx_t* ctx, int* axis, int* extent, int* segment, int nmax) {
+  if (!ctx || nmax < 0 || (nmax > 0 && (!axis || !extent || !segment))) return HYDRO_EINVAL;
   if (!ctx->batch) return 0;
   int k = 0;
   for (auto& kv : ctx->batch->seg_parts) {
     if (k < nmax) {
-      extent[k] = kv.first;
-      segment[k] = kv.second ? (kv.first + 2 + kv.second - 1) / kv.second : 0;
+      axis[k] = kv.first / 65536;
+      extent[k] = kv.first % 65536;
+      segment[k] = kv.second ? (extent[k] + 2 + kv.second - 1) / kv.second : 0;
     }
     ++k;
   }

@@ -82,7 +82,7 @@ def test_batch_equals_per_box_and_oracle(tune):
     single, dn1 = _run_single(ctx, Us, SIZES3, 3, dts, p)
     if tune:
         tuning = ctx.hydro_batch_tuning()
-        assert set(tuning) >= {16, 24, 32, 48}
+        assert {e for _, e in tuning} >= {16, 24, 32, 48} and {a for a, _ in tuning} == {0, 1, 2}
     ctx.close()
     for g, s1, U, s, d, nx in zip(got, single, Us, SIZES3, dts, dn):
         assert np.all(rel_linf(_interior(g, 3), _interior(s1, 3)) <= 1e-14)
@@ -109,15 +109,17 @@ def test_exact_batch_is_bitwise_equal_to_oracle():
 
 @pytest.mark.parametrize("mode", ["tiles", "sweeps", "mixed"])
 def test_exact_batch_with_each_tracing_kernel(mode, tmp_path, monkeypatch):
-    """The tracing kernel chosen per extent (the sweep with a given segment
-    length, or the warp-row / tile kernels), forced through the tuning cache
-    file: every choice gives the oracle's result bit for bit, in 3-D and 2-D."""
+    """The tracing kernel chosen per axis and extent (the sweep with a given
+    segment length, or the warp-row / tile kernels), forced through the
+    tuning cache file: every choice gives the oracle's result bit for bit,
+    in 3-D and 2-D."""
     sizes3 = SIZES3
     sizes2 = [(40, 24, 1), (16, 64, 1), (32, 32, 1)]
-    extents = sorted({e for s in sizes3 + sizes2 for e in s if e > 1})
-    pick = {"tiles": lambda e: 0, "sweeps": lambda e: 2, "mixed": lambda e: 0 if e % 16 else 3}[mode]
+    classes = sorted({(a, s[a]) for s in sizes3 for a in range(3)} | {(a, s[a]) for s in sizes2 for a in range(2)})
+    pick = {"tiles": lambda a, e: 0, "sweeps": lambda a, e: 2,
+            "mixed": lambda a, e: 0 if (a == 0) != (e % 16 == 0) else 3}[mode]
     cache = tmp_path / "tune.txt"
-    cache.write_text("".join(f"{e} {pick(e)}\n" for e in extents))
+    cache.write_text("".join(f"{a} {e} {pick(a, e)}\n" for a, e in classes))
     monkeypatch.setenv("HYDRO_TUNE_CACHE", str(cache))
     for dim, sizes in ((3, sizes3), (2, sizes2)):
         Us = _level(21 + dim, sizes, dim)
@@ -126,9 +128,10 @@ def test_exact_batch_with_each_tracing_kernel(mode, tmp_path, monkeypatch):
         got, _ = _run_batch(ctx, Us, sizes, dim, dts, hb.params(dim, gamma=5 / 3))
         tuning = ctx.hydro_batch_tuning()
         ctx.close()
-        for e in extents:
-            want = 0 if pick(e) == 0 else (e + 2 + pick(e) - 1) // pick(e)
-            assert tuning[e] == want
+        for a, e in classes:
+            if a < dim:
+                want = 0 if pick(a, e) == 0 else (e + 2 + pick(a, e) - 1) // pick(a, e)
+                assert tuning[a, e] == want
         for g, U, s, d in zip(got, Us, sizes, dts):
             P = oracle.params(dim, s[:dim], dx=(1 / s[0], 1 / s[1], 1 / s[2] if dim == 3 else 1.0),
                               bc=oracle.BC_PREFILLED, gamma=5 / 3)
