@@ -58,14 +58,35 @@ __device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __
   bool bad = false;
   cons_to_prim_flag(U, K, q, &inv, &bad);
   if (bad) atomicOr(&flags->bad, 1);
-  double c = dsqrt(mul_i(mul_i(K.gamma, q[4]), inv));
   long long id = sg.id(i, j, k);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Q[v * sg.sc + id] = q[v];
+  double c, rho_c, c_rho, inv_c2;
+#ifndef HYDRO_IEEE_DIV_SQRT
+  // product build: every sound-speed quantity from one refined
+  // y = 1/sqrt(gamma p rho): c = (gamma p) y, 1/c = rho y, rho/c = rho (rho y),
+  // c/rho = c (c y) with c y = 1/rho, 1/c^2 = (rho y)^2
+  const double gp = mul_i(K.gamma, q[4]);
+  const double x = gp * q[0];
+  if (__builtin_expect(newton_range(x), 1)) {
+    const double y = rsqrt_newton(x);
+    const double ry = q[0] * y;
+    c = gp * y;
+    rho_c = q[0] * ry;
+    c_rho = c * (c * y);
+    inv_c2 = ry * ry;
+  } else
+#endif
+  {
+    c = dsqrt(mul_i(mul_i(K.gamma, q[4]), inv));
+    rho_c = ddiv(q[0], c);
+    c_rho = ddiv(c, q[0]);
+    inv_c2 = drcp(mul_i(c, c));
+  }
   Q[QC * sg.sc + id] = c;
-  Q[QRC * sg.sc + id] = ddiv(q[0], c);
-  Q[QCR * sg.sc + id] = ddiv(c, q[0]);
-  Q[QIC2 * sg.sc + id] = drcp(mul_i(c, c));
+  Q[QRC * sg.sc + id] = rho_c;
+  Q[QCR * sg.sc + id] = c_rho;
+  Q[QIC2 * sg.sc + id] = inv_c2;
 }
 
 // ---- stage 3 of a zone: characteristic tracing from its parabolas
