@@ -208,7 +208,7 @@ real flat_tilde(const real* p, const real* un, int m, double small_pres) {
 }
 real flat_coef(const real* p, const real* un, double small_pres) {
   real dp1 = p[4] - p[2];
-  int s = (dp1 < 0.0) ? 1 : -1; /* the neighbour on the high-pressure side */
+  int s = (dp1 < 0.0) ? 1 : -1; /* the neighbour on the low-pressure side, into which a shock runs */
   return rmin(flat_tilde(p, un, 3, small_pres), flat_tilde(p, un, 3 + s, small_pres));
 }
 
@@ -353,7 +353,7 @@ void trace_pencil(const std::vector<real>* Q, long base, long st, int nd, int d,
     for (int j = -1; j <= nd; ++j) {
       int m = j + off;
       real dp1 = a[4][m + 1] - a[4][m - 1];
-      int s = (dp1 < 0.0) ? 1 : -1; /* the neighbour on the high-pressure side */
+      int s = (dp1 < 0.0) ? 1 : -1; /* the neighbour on the low-pressure side, into which a shock runs */
       chi[m] = rmin(chit[m], chit[m + s]);
     }
   }

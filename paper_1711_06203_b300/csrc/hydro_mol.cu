@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(BLOCK) km_flat(ScratchGeom sg, const double* _
   const double* un = Q + (QU + D) * sg.sc + id;
   double chi = 1.0;
   if (K.flatten) {
-    // the neighbour on the high-pressure side (p_{i+1} - p_{i-1} < 0 as an order comparison)
+    // the neighbour on the low-pressure side (p_{i+1} - p_{i-1} < 0 as an order comparison)
     const long long s = dless(p[st], p[-st]) ? st : -st;
     const double c0 = flat_tilde(p[-2 * st], p[-st], p[st], p[2 * st], un[-st], un[st], K.small_pres);
     const double c1 = flat_tilde(p[s - 2 * st], p[s - st], p[s + st], p[s + 2 * st], un[s - st], un[s + st],

@@ -218,6 +218,20 @@ class TestPPM:
             assert abs(oracle.integ([am, ap, a6], s, True) - (3.0 + 0.25 * (0.5 - s / 2))) < 1e-14
             assert abs(oracle.integ([am, ap, a6], s, False) - (3.0 - 0.25 * (0.5 - s / 2))) < 1e-14
 
+    def test_limited_slope_worked_example(self):
+        """The monotonised centred slope (CW84 eq. 1.8) where the one-sided
+        bound 2|a_i - a_{i-1}| is the active one.  Line (0, 0, 0.1, 0.2, 1.0,
+        1.8, 1.9), zone 3 (a = 0.2), worked by hand:
+          slopes: zone 2 (0, 0.1, 0.2) -> min(0.1, 0.2, 0.2) = 0.1;
+                  zone 3 (0.1, 0.2, 1.0) -> min(0.45, 2 x 0.1, 2 x 0.8) = 0.2;
+                  zone 4 (0.2, 1.0, 1.8) -> min(0.8, 1.6, 1.6) = 0.8;
+          interfaces: a_{2+1/2} = 0.15 - (0.2 - 0.1)/6 = 2/15,
+                      a_{3+1/2} = 0.6 - (0.8 - 0.2)/6 = 1/2;
+          limiter (eq. 1.10): D = 11/30, M = 0.2 - 19/60 = -7/60, D M < -D^2/6,
+          so a+ = 3 a - 2 a- = 1/3; a6 = 6 (0.2 - (2/15 + 1/3)/2) = -1/5."""
+        am, ap, a6 = oracle.ppm_parabola(np.array([0.0, 0.0, 0.1, 0.2, 1.0, 1.8, 1.9]))
+        assert abs(am - 2 / 15) < 1e-15 and abs(ap - 1 / 3) < 1e-15 and abs(a6 + 0.2) < 1e-15
+
     def test_cubic_zone_averages_give_exact_interface_values(self):
         # zone averages of a monotone cubic; the 4th-order interface formula is exact for cubics
         f = lambda x: 1.0 + x + 0.1 * x ** 2 + 0.01 * x ** 3
@@ -279,6 +293,14 @@ class TestPPM:
         # at i+1 dp1 = 1.8, dp2 = 2.2 -> z = 0.82 -> would give 0.3
         r = np.array([1.0, 1.0, 1.0, 1.2, 1.4, 3.0, 3.2])
         assert oracle.flatten_coef(r, u) == 1.0
+        # the shock test's threshold epsilon = 0.33 (CW84 App. A): the same
+        # profile shape with a jump |dp1| / min(p) of 0.30 is not a shock, of
+        # 0.40 it is (z = dp1 / dp2 = 0.8 -> chi~ = 1 - 10 (0.8 - 0.75) = 0.5)
+        for jump, want in ((0.30, 1.0), (0.40, 0.5)):
+            dp1 = jump * 1.0
+            s = np.array([1.0, 1.0, 1.0, 1.0 + 0.5 * dp1, 1.0 + dp1, 1.0 + 1.25 * dp1, 1.0 + 1.25 * dp1])
+            # neighbours: at i-1, dp1' = dp1/2 and dp2' = 1.25 dp1 -> z = 0.4 -> 1; so chi = chi~_i
+            assert abs(oracle.flatten_coef(s, u) - want) < 1e-12, jump
 
 
 # ---------------------------------------------------------------- characteristic tracing
@@ -322,12 +344,17 @@ class TestTracing:
         qm, _ = oracle.trace_lines(L, 0, self._P(), 0.3, 0.0)
         assert np.array_equal(qm, q0)
 
-    @pytest.mark.parametrize("d", [0, 1, 2])
-    def test_linearised_characteristics_are_exact(self, d):
+    @pytest.mark.parametrize("d,un", [(0, 0.3), (1, 0.3), (2, 0.3), (0, 2.0), (2, -2.0)])
+    def test_linearised_characteristics_are_exact(self, d, un):
         """With linear profiles made of waves that all reach a face, the traced
-        state is the exact linearised solution at the face at t = dt/2."""
+        state is the exact linearised solution at the face at t = dt/2.
+        Subsonic (u = 0.3, c = 1.18): the entropy and fast wave reach the high
+        face, the slow wave the low one.  Supersonic (|u| = 2): all three
+        reach the downstream face, so the two waves that are not the
+        reference one both enter through their wave strengths (the
+        eigenvector coefficients rho/(2c) and 1/(2c^2))."""
         g = self.g
-        rho, un, p = 1.0, 0.3, 1.0
+        rho, p = 1.0, 1.0
         c = np.sqrt(g * p / rho)
         # eigenvectors of the (rho, un, p) system, written out here independently
         r = {"-": np.array([1.0, -c / rho, c * c]), "0": np.array([1.0, 0.0, 0.0]), "+": np.array([1.0, c / rho, c * c])}
@@ -335,16 +362,20 @@ class TestTracing:
         dtdx = 0.4 / (abs(un) + c)
         t1 = 1 if d == 0 else 0
         t2 = 1 if d == 2 else 2
-        for face, waves in (("p", ("0", "+")), ("m", ("-",))):
+        if abs(un) < c:
+            cases = (("p", ("0", "+")), ("m", ("-",)))
+        else:
+            cases = ((("p" if un > 0 else "m"), ("-", "0", "+")),)
+        for face, waves in cases:
             amp = {"-": 0.0, "0": 0.0, "+": 0.0}
-            for w, a in zip(waves, (2e-4, -3e-4)):
+            for w, a in zip(waves, (2e-4, -3e-4, 1.5e-4)):
                 amp[w] = a
             s3 = sum(amp[w] * r[w] for w in amp)
             slope_t = 1e-4  # transverse velocity rides the entropy wave
             q0 = np.zeros(5); sl = np.zeros(5)
             q0[0], q0[1 + d], q0[4] = rho, un, p
             sl[0], sl[1 + d], sl[4] = s3
-            if face == "p":
+            if "0" in waves:
                 sl[1 + t1] = slope_t
             L = np.zeros((6, 7))
             m = np.arange(-3, 4)
@@ -357,8 +388,39 @@ class TestTracing:
             exact = np.array([rho, un, p]) + sum(amp[w] * (xf - lam[w] * dtdx / 2) * r[w] for w in amp)
             got = qp if face == "p" else qm
             assert np.allclose([got[0], got[1 + d], got[4]], exact, rtol=0, atol=1e-15), (face, d)
-            if face == "p":
-                assert abs(got[1 + t1] - slope_t * (0.5 - un * dtdx / 2)) < 1e-15
+            if "0" in waves:
+                assert abs(got[1 + t1] - slope_t * (xf - un * dtdx / 2)) < 1e-15
+
+
+def test_step_traced_states_equal_the_seven_point_tracing():
+    """The step forms each pencil's flattening coefficients, slopes and
+    interface values once and shares them between zones; the seven-point
+    tracing of a single zone forms them from that zone's own stencil.  On a
+    box with strong compressions and pressure jumps, where the flattening
+    neighbour rule matters, the two give the same traced states bit for bit
+    on every zone the step traces (zones [-1, n] on every axis)."""
+    rng = np.random.default_rng(31)
+    n = (9, 8, 7)
+    dx = (1 / 9, 1 / 8, 1 / 7)
+    U = inputs.random_box(rng, n, 3, gamma=1.4, sigma_rho=0.8, sigma_u=0.8, sigma_p=1.0)
+    P = oracle.params(3, n, dx=dx, gamma=1.4, grav=(0.2, -0.4, 0.3))
+    d, _ = oracle.dt(U, P)
+    _, rc, dbg = oracle.step(U, P, d, debug=True)
+    Q = dbg["prim"]
+    flattened = 0
+    for ax in range(3):
+        for k in range(-1, n[2] + 1):
+            for j in range(-1, n[1] + 1):
+                for i in range(-1, n[0] + 1):
+                    z = [k + 4, j + 4, i + 4]
+                    sl = [z[0], z[1], z[2]]
+                    sl[2 - ax] = slice(z[2 - ax] - 3, z[2 - ax] + 4)
+                    L = Q[(slice(None),) + tuple(sl)]
+                    flattened += oracle.flatten_coef(L[4], L[1 + ax]) < 1.0
+                    qm, qp = oracle.trace_lines(L, ax, P, d / dx[ax], d)
+                    assert np.array_equal(qm, dbg["trace_m"][ax][(slice(None),) + tuple(z)]), (ax, i, j, k)
+                    assert np.array_equal(qp, dbg["trace_p"][ax][(slice(None),) + tuple(z)]), (ax, i, j, k)
+    assert flattened > 50
 
 
 # ---------------------------------------------------------------- EOS
@@ -539,6 +601,68 @@ def test_free_fall_under_constant_gravity():
     assert np.allclose(E, E0 + rho * g * (w0 + 0.5 * g * dt) * dt, rtol=1e-14)
 
 
+def _falling_profile():
+    """2-D periodic box: density 1.5 + 0.4 sin(2 pi x) advected at u = 0.8
+    along x, at rest along y, uniform pressure, gravity -3 along y."""
+    n, dx, g, gam = (24, 8), (1 / 24, 1 / 8, 1.0), (0.0, -3.0, 0.0), 1.4
+    X = inputs.zone_centres(n + (1,), 2, dx)
+    rho = 1.5 + 0.4 * np.sin(2 * np.pi * X[0])
+    U = inputs.conserved(rho, 0.8 + 0 * rho, 0 * rho, 0 * rho, 1.0 + 0 * rho, gam)
+    P = oracle.params(2, n, dx=dx, bc=oracle.BC_PERIODIC, gamma=gam, grav=g)
+    d, _ = oracle.dt(U, P)
+    U1, rc = oracle.step(U, P, d)
+    assert rc == 0
+    inner = lambda V: V[:, 0, 4:-4, 4:-4]
+    return inner(U), inner(U1), g[1], d
+
+
+def test_falling_advected_profile_momentum_is_new_density_times_g_dt():
+    """The momentum source is time-centred in the density, dt g (rho^n +
+    rho^{n+1}) / 2 (Step 10).  The y-momentum carried along x is the mass flux
+    times the traced v = g dt / 2, whose divergence is (rho^{n+1} - rho^n) g
+    dt / 2; the two add up to (rho v)^{n+1} = rho^{n+1} g dt exactly, zone by
+    zone, while the density itself changes by O(dt)."""
+    U0, U1, g, d = _falling_profile()
+    assert np.abs(U1[0] - U0[0]).max() > 1e-2
+    assert np.abs(U1[2] - U1[0] * g * d).max() <= 1e-15
+
+
+def test_falling_advected_profile_gains_half_g2_dt2_mass():
+    """The energy source is dt g . ((rho v)^n + (rho v)^{n+1}) / 2 (Step 10):
+    over a periodic box the fluxes cancel and the total energy rises by
+    g^2 dt^2 / 2 times the (conserved) total mass."""
+    U0, U1, g, d = _falling_profile()
+    mass = U0[0].sum()
+    assert abs(U1[0].sum() - mass) <= 1e-13 * mass
+    gain = U1[4].sum() - U0[4].sum()
+    want = 0.5 * g * g * d * d * mass
+    assert abs(gain - want) <= 1e-9 * want, (gain, want)
+
+
+def test_periodic_box_momentum_and_energy_budget_under_gravity():
+    """Over a periodic box the flux differences cancel, so the totals follow
+    the sources of Step 10 alone: each momentum component gains dt g_a M
+    (M the conserved mass) and the energy gains dt sum_a g_a (P_a^n +
+    P_a^{n+1}) / 2 = dt sum_a g_a (P_a^n + dt g_a M / 2), P_a the total
+    momentum, for any state."""
+    rng = np.random.default_rng(77)
+    n = (10, 9, 8)
+    g = (0.6, -0.9, 1.3)
+    U = inputs.random_box(rng, n, 3, gamma=1.4, sigma_u=0.4)
+    P = oracle.params(3, n, bc=oracle.BC_PERIODIC, gamma=1.4, grav=g)
+    d, _ = oracle.dt(U, P)
+    U1, rc = oracle.step(U, P, d)
+    assert rc == 0
+    A, B = U[I3], U1[I3]
+    M = A[0].sum()
+    assert abs(B[0].sum() - M) <= 1e-13 * M
+    for a in range(3):
+        assert abs(B[1 + a].sum() - (A[1 + a].sum() + d * g[a] * M)) <= 1e-13 * M
+    gain = B[4].sum() - A[4].sum()
+    want = d * sum(g[a] * (A[1 + a].sum() + 0.5 * d * g[a] * M) for a in range(3))
+    assert abs(gain - want) <= 1e-13 * np.abs(A[4]).sum(), (gain, want)
+
+
 def test_hydrostatic_atmosphere_stays_near_rest():
     """Unperturbed isothermal atmosphere (rho = exp(-z/H), p = rho g H) with
     periodic x and reflecting z.  Away from the walls (whose mirrored ghost
@@ -563,6 +687,31 @@ def test_hydrostatic_atmosphere_stays_near_rest():
         p = (5 / 3 - 1) * (q[4] - 0.5 * rho * vel ** 2)
         machs.append((vel / np.sqrt(5 / 3 * p / rho)).max())
     assert machs[0] < 1e-3 and machs[1] < machs[0] / 2.0, machs
+
+
+def test_time_step_closed_form_and_brute_force():
+    """dt = cfl min over zones and directions of dx_d / (|u_d| + c) (Step 11):
+    a uniform state gives the closed form, a random box the minimum taken zone
+    by zone from its own primitive variables."""
+    gam, cfl, dx = 1.4, 0.45, (0.1, 0.05, 0.07)
+    n = (6, 5, 4)
+    shape = inputs.grown_shape(n, 3)
+    rho, vel, p = 1.3, (0.4, -0.7, 0.2), 0.8
+    U = inputs.conserved(np.full(shape, rho), *vel, np.full(shape, p), gam)
+    P = oracle.params(3, n, dx=dx, gamma=gam, cfl=cfl)
+    c = np.sqrt(gam * p / rho)
+    want = cfl * min(h / (abs(v) + c) for h, v in zip(dx, vel))
+    got, rc = oracle.dt(U, P)
+    assert rc == 0 and abs(got - want) <= 1e-15 * want
+    U = inputs.random_box(np.random.default_rng(12), n, 3, gamma=gam, sigma_u=0.8)
+    Z = U[:, 4:-4, 4:-4, 4:-4]
+    r = Z[0]
+    v = Z[1:4] / r
+    pr = (gam - 1) * (Z[4] - 0.5 * r * (v * v).sum(0))
+    cs = np.sqrt(gam * pr / r)
+    want = cfl * min((h / (np.abs(v[a]) + cs)).min() for a, h in enumerate(dx))
+    got, rc = oracle.dt(U, P)
+    assert rc == 0 and abs(got - want) <= 1e-13 * want
 
 
 def test_ghost_fill_kinds_and_corner_composition():
@@ -596,6 +745,16 @@ def test_ghost_fill_kinds_and_corner_composition():
         assert W[c, z(-2), y(1), x(-1)] == U[c, z(-2), y(1), x(0)]
         assert W[c, z(0), y(-2), x(7)] == sgn * U[c, z(0), y(3), x(4)]
         assert W[c, z(9), y(-1), x(-2)] == U[c, z(6), y(4), x(0)]
+    # reflect on the low faces: ghost -m mirrors interior zone m - 1
+    bc2 = ((oracle.BC_REFLECT, oracle.BC_OUTFLOW), (oracle.BC_REFLECT, oracle.BC_OUTFLOW),
+           (oracle.BC_REFLECT, oracle.BC_OUTFLOW))
+    W2 = oracle.fill_ghosts(U, oracle.params(3, n, bc=bc2))
+    for c in range(5):
+        for m in (1, 2, 4):
+            for a, idx, src in ((0, (z(2), y(1), x(-m)), (z(2), y(1), x(m - 1))),
+                                (1, (z(2), y(-m), x(1)), (z(2), y(m - 1), x(1))),
+                                (2, (z(-m), y(1), x(1)), (z(m - 1), y(1), x(1)))):
+                assert W2[(c,) + idx] == (-1 if c == 1 + a else 1) * U[(c,) + src]
 
 
 # ---------------------------------------------------------------- options beyond the base step
