@@ -277,25 +277,29 @@ __global__ void k_selftest_intpipe(const double* __restrict__ x, const double* _
   prod[i] = mul_i(x[i], y[i]);
   sum[i] = add_i(x[i], y[i]);
 }
-// z-chunks of the overlapped host-buffer step (Sedov 128^3 per call: 6.10 ms
-// with 4, 5.94 with 6, 5.87 with 8, 5.88 with 12, 5.92 with 16)
-constexpr int PIPE_CHUNKS = 8;
+// z-chunks of the overlapped host-buffer step, and planes per piece of the
+// last chunk's final fluxes and update (Sedov 128^3 per call, 4.51 ms on the
+// device alone: 5.38 ms with 6 chunks, 5.30 with 8, 5.39 with 10; pieces of
+// 4 planes against one piece, 5.30 against 5.45)
+constexpr int PIPE_CHUNKS = 8, PIPE_PIECE = 4;
 
-// copy streams and events of the overlapped host-buffer step
+// copy and back-stage streams and events of the overlapped host-buffer step
 int ensure_pipe(hydro_ctx* ctx) {
   if (ctx->pipe_ready) return HYDRO_OK;
   bool ok = cudaStreamCreateWithFlags(&ctx->pipe_h2d, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&ctx->pipe_d2h, cudaStreamNonBlocking) == cudaSuccess;
+            cudaStreamCreateWithFlags(&ctx->pipe_d2h, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&ctx->pipe_back, cudaStreamNonBlocking) == cudaSuccess;
   for (auto& e : ctx->pipe_events) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     if (ctx->pipe_h2d) cudaStreamDestroy(ctx->pipe_h2d);
     if (ctx->pipe_d2h) cudaStreamDestroy(ctx->pipe_d2h);
+    if (ctx->pipe_back) cudaStreamDestroy(ctx->pipe_back);
     for (auto& e : ctx->pipe_events) {
       if (e) cudaEventDestroy(e);
       e = nullptr;
     }
-    ctx->pipe_h2d = ctx->pipe_d2h = nullptr;
+    ctx->pipe_h2d = ctx->pipe_d2h = ctx->pipe_back = nullptr;
     return HYDRO_ENOMEM;
   }
   ctx->pipe_ready = true;
@@ -359,6 +363,7 @@ void hydro_ctx_destroy(hydro_ctx_t* ctx) {
   if (ctx->host_stage) cudaFree(ctx->host_stage);
   if (ctx->pipe_h2d) cudaStreamDestroy(ctx->pipe_h2d);
   if (ctx->pipe_d2h) cudaStreamDestroy(ctx->pipe_d2h);
+  if (ctx->pipe_back) cudaStreamDestroy(ctx->pipe_back);
   for (auto& e : ctx->pipe_events)
     if (e) cudaEventDestroy(e);
   if (ctx->faces) cudaFree(ctx->faces);
@@ -544,13 +549,17 @@ int hydro_advance_box_host(hydro_ctx_t* ctx, const hydro_box_t* in, const hydro_
     hp.field = field;
     hp.plane = plane;
     hp.nchunk = (int)std::min<long long>(PIPE_CHUNKS, in->n[2]);
+    hp.piece = PIPE_PIECE;
     hp.h2d = ctx->pipe_h2d;
     hp.d2h = ctx->pipe_d2h;
+    hp.back = ctx->pipe_back;
     hp.start = ctx->pipe_events[0];
     hp.d2h_done = ctx->pipe_events[1];
+    hp.back_done = ctx->pipe_events[2];
     for (int k = 0; k < PIPE_MAX_CHUNKS; ++k) {
-      hp.h2d_done[k] = ctx->pipe_events[2 + k];
-      hp.upd_done[k] = ctx->pipe_events[2 + PIPE_MAX_CHUNKS + k];
+      hp.h2d_done[k] = ctx->pipe_events[3 + k];
+      hp.front_done[k] = ctx->pipe_events[3 + PIPE_MAX_CHUNKS + k];
+      hp.upd_done[k] = ctx->pipe_events[3 + 2 * PIPE_MAX_CHUNKS + k];
     }
     if (launch_step_host_piped(a, hp, st, &ctx->launches) != cudaSuccess) return HYDRO_ECUDA;
     if (ctx->record_faces) {

@@ -25,9 +25,9 @@ struct hydro_ctx {
   long long stage_calls = 0;
   double* host_stage = nullptr;   // device in/out boxes of hydro_advance_box_host (grown on demand)
   size_t host_stage_bytes = 0;
-  // copy streams and events of the overlapped host-buffer step (made on first use)
-  cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
-  cudaEvent_t pipe_events[2 * hydro::PIPE_MAX_CHUNKS + 2] = {};
+  // copy and back-stage streams and events of the overlapped host-buffer step (made on first use)
+  cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr, pipe_back = nullptr;
+  cudaEvent_t pipe_events[3 * hydro::PIPE_MAX_CHUNKS + 3] = {};
   bool pipe_ready = false;
   // final fluxes through the outer faces of the last recorded box step
   int record_faces = 0;

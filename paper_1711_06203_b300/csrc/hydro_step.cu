@@ -213,6 +213,7 @@ int launch_flux1_ranges(const StepArgs& a, const Range r[3], unsigned dirs, cuda
     S.r[d] = r[d];
     S.first[d + 1] = S.first[d] + (((dirs >> d) & 1u) ? blocks_for(S.r[d].count()) : 0u);
   }
+  if (S.first[3] == 0) return 0;
   if (a.K.einfeldt) k_flux1<true><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   else k_flux1<false><<<S.first[3], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
   return 1;
@@ -232,20 +233,16 @@ int launch_flux1_all(const StepArgs& a, const Range& rt, unsigned dirs, cudaStre
   return launch_flux1_ranges(a, r, dirs, st);
 }
 
-// final fluxes through d-faces [0, n_d] of every active direction d, over
-// transverse zones [0, n) except the z range [zlo, zlo + zext) (in 3-D), one launch
-int launch_flux3_all(const StepArgs& a, int dim, int zlo, int zext, cudaStream_t st) {
-  const int* n = a.in.n;
+// final fluxes of the active directions d over the face ranges r[d], one launch
+int launch_flux3_ranges(const StepArgs& a, int dim, const Range r[3], cudaStream_t st) {
   DirSets S;
   S.first[0] = 0;
   for (int d = 0; d < 3; ++d) {
-    Range& r = S.r[d];
-    for (int ax = 0; ax < 3; ++ax) { r.lo[ax] = 0; r.ext[ax] = (ax < dim) ? n[ax] : 1; }
-    if (dim == 3) { r.lo[2] = zlo; r.ext[2] = zext; }
-    r.ext[d] += 1;
-    S.first[d + 1] = S.first[d] + ((d < dim) ? blocks_for(r.count()) : 0u);
+    S.r[d] = r[d];
+    S.first[d + 1] = S.first[d] + ((d < dim) ? blocks_for(r[d].count()) : 0u);
   }
   const unsigned g = S.first[3];
+  if (g == 0) return 0;
   if (a.K.einfeldt) {
     if (dim == 3) k_flux3<true, true><<<g, BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
     else k_flux3<false, true><<<g, BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
@@ -256,35 +253,66 @@ int launch_flux3_all(const StepArgs& a, int dim, int zlo, int zext, cudaStream_t
   return 1;
 }
 
+// final fluxes through d-faces [0, n_d] of every active direction d, over
+// transverse zones [0, n) except the z range [zlo, zlo + zext) (in 3-D), one launch
+int launch_flux3_all(const StepArgs& a, int dim, int zlo, int zext, cudaStream_t st) {
+  const int* n = a.in.n;
+  Range r[3];
+  for (int d = 0; d < 3; ++d) {
+    for (int ax = 0; ax < 3; ++ax) { r[d].lo[ax] = 0; r[d].ext[ax] = (ax < dim) ? n[ax] : 1; }
+    if (dim == 3) { r[d].lo[2] = zlo; r[d].ext[2] = zext; }
+    r[d].ext[d] += 1;
+  }
+  return launch_flux3_ranges(a, dim, r, st);
+}
+
 // 3-D intermediate fluxes F^{d|t}: d-faces [0, n_d] x t in [0, n_t) x third
 // axis [-1, n], restricted along z to the interior planes [zlo, zlo + zext)
 // of a slab (the ranges grow by the faces and zones the slab's final fluxes
 // read: F^{x|y}, F^{y|x} on planes [zlo - 1, zlo + zext], F^{z|x}, F^{z|y} on
 // z-faces [zlo, zlo + zext], F^{x|z}, F^{y|z} on the slab's planes)
+// the six sets (d, t) in the order (0,1), (0,2), (1,0), (1,2), (2,0), (2,1)
+// over the ranges r[c], one launch
+int launch_flux2_ranges(const StepArgs& a, const Range r[6], cudaStream_t st) {
+  Flux2Sets S;
+  S.first[0] = 0;
+  for (int c = 0; c < 6; ++c) {
+    S.r[c] = r[c];
+    S.first[c + 1] = S.first[c] + blocks_for(r[c].count());
+  }
+  if (S.first[6] == 0) return 0;
+  if (a.K.einfeldt) k_flux2<true><<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  else k_flux2<false><<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
+  return 1;
+}
+
+// the range of set (d, t) with a z extent [zlo, zhi) of faces (d = z), zones
+// (t = z) or planes of the third axis (neither)
+Range flux2_range(const int n[3], int d, int t, int zlo, int zhi) {
+  const int o = 3 - d - t;
+  Range r;
+  r.lo[d] = 0; r.ext[d] = n[d] + 1;
+  r.lo[t] = 0; r.ext[t] = n[t];
+  r.lo[o] = -1; r.ext[o] = n[o] + 2;
+  r.lo[2] = zlo; r.ext[2] = std::max(0, zhi - zlo);
+  return r;
+}
+
 int launch_flux2_all(const StepArgs& a, cudaStream_t st, int zlo = 0, int zext = -1) {
   const int* n = a.in.n;
   if (zext < 0) zext = n[2];
-  Flux2Sets S;
-  S.first[0] = 0;
+  Range r[6];
   int c = 0;
   for (int d = 0; d < 3; ++d)
     for (int t = 0; t < 3; ++t) {
       if (t == d) continue;
-      int o = 3 - d - t;
-      Range& r = S.r[c];
-      r.lo[d] = 0; r.ext[d] = n[d] + 1;
-      r.lo[t] = 0; r.ext[t] = n[t];
-      r.lo[o] = -1; r.ext[o] = n[o] + 2;
       // the z extent: faces, zones or the widened range of the slab
-      if (d == 2) { r.lo[2] = zlo; r.ext[2] = zext + 1; }
-      else if (t == 2) { r.lo[2] = zlo; r.ext[2] = zext; }
-      else { r.lo[2] = zlo - 1; r.ext[2] = zext + 2; }
-      S.first[c + 1] = S.first[c] + blocks_for(r.count());
+      if (d == 2) r[c] = flux2_range(n, d, t, zlo, zlo + zext + 1);
+      else if (t == 2) r[c] = flux2_range(n, d, t, zlo, zlo + zext);
+      else r[c] = flux2_range(n, d, t, zlo - 1, zlo + zext + 1);
       ++c;
     }
-  if (a.K.einfeldt) k_flux2<true><<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
-  else k_flux2<false><<<S.first[6], BLOCK, 0, st>>>(a.sg, a.s, a.K, S);
-  return 1;
+  return launch_flux2_ranges(a, r, st);
 }
 
 }  // namespace
@@ -424,30 +452,41 @@ cudaError_t launch_step_slabs(const StepArgs& a, int T, double* faces, cudaStrea
 
 cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t st, long long* launches) {
   const int* n = a.in.n;
+  const int nz = n[2];
   const ScratchGeom& sg = a.sg;
   const Scratch& s = a.s;
   const int C = p.nchunk;
   long long nl = 0;
-  auto zc = [&](int k) { return (int)((long long)n[2] * k / C); };  // first interior plane of chunk k
+  auto zc = [&](int k) { return (int)((long long)nz * k / C); };  // first interior plane of chunk k
   const size_t plane_bytes = (size_t)p.plane * sizeof(double);
-  // input planes, chunk by chunk, after the work already queued on the
-  // compute stream (which may still read the staging box)
-  if (cudaEventRecord(p.start, st) != cudaSuccess) return cudaGetLastError();
-  if (cudaStreamWaitEvent(p.h2d, p.start, 0) != cudaSuccess) return cudaGetLastError();
   // of each plane, the interior rows: one contiguous run of n_y rows
   const long long row = p.plane / (n[1] + 2 * NG), rows_off = NG * row;
   const size_t rows_bytes = (size_t)(n[1] * row) * sizeof(double);
-  for (int k = 0; k < C; ++k) {
-    const long long off = (long long)(zc(k) + NG) * p.plane + rows_off;
-    const size_t planes = (size_t)(zc(k + 1) - zc(k));
+  auto copy = [&](double* dst, const double* src, int z0, int z1, cudaMemcpyKind kind, cudaStream_t cs) {
+    const long long off = (long long)(z0 + NG) * p.plane + rows_off;
     for (int c = 0; c < 5; ++c)
-      if (cudaMemcpy2DAsync(a.in.u + c * p.field + off, plane_bytes, p.h_in + c * p.field + off, plane_bytes,
-                            rows_bytes, planes, cudaMemcpyHostToDevice, p.h2d) != cudaSuccess)
-        return cudaGetLastError();
-    if (cudaEventRecord(p.h2d_done[k], p.h2d) != cudaSuccess) return cudaGetLastError();
-  }
+      if (cudaMemcpy2DAsync(dst + c * p.field + off, plane_bytes, src + c * p.field + off, plane_bytes, rows_bytes,
+                            (size_t)(z1 - z0), kind, cs) != cudaSuccess)
+        return false;
+    return true;
+  };
+  // input planes, chunk by chunk, after the work already queued on the
+  // compute stream (which may still read the staging box).  A periodic low
+  // face takes its ghost planes from the top NG interior planes: those go
+  // first, so that the bottom of the box can start with chunk 0.
+  const int bclo = a.in.bc[2][0];  // 0 outflow, 1 reflect, 2 periodic
+  const int pre = (bclo == 2) ? nz - NG : nz;
   k_reset_step<<<1, 32, 0, st>>>(a.flags);
   nl += 1;
+  if (cudaEventRecord(p.start, st) != cudaSuccess) return cudaGetLastError();
+  if (cudaStreamWaitEvent(p.h2d, p.start, 0) != cudaSuccess) return cudaGetLastError();
+  if (cudaStreamWaitEvent(p.back, p.start, 0) != cudaSuccess) return cudaGetLastError();
+  if (pre < nz && !copy(a.in.u, p.h_in, pre, nz, cudaMemcpyHostToDevice, p.h2d)) return cudaGetLastError();
+  for (int k = 0; k < C; ++k) {
+    const int z1 = std::min(zc(k + 1), pre);
+    if (z1 > zc(k) && !copy(a.in.u, p.h_in, zc(k), z1, cudaMemcpyHostToDevice, p.h2d)) return cudaGetLastError();
+    if (cudaEventRecord(p.h2d_done[k], p.h2d) != cudaSuccess) return cudaGetLastError();
+  }
   auto prim = [&](int zlo, int zext) {
     Range r;
     r.lo[0] = -NG; r.ext[0] = n[0] + 2 * NG;
@@ -456,89 +495,117 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     k_prim<<<blocks_for(r.count()), BLOCK, 0, st>>>(a.in, sg, s.Q, a.K, r, a.flags);
     nl += 1;
   };
-  // each landed chunk: primitive state and the x and y sweeps of its planes.
-  // The ghost planes below 0 copy interior plane 0 (outflow), planes [0, NG)
-  // (reflect) or [n-NG, n) (periodic), and those above n-1 likewise.  When
-  // the first (last) chunk holds those planes, the ghost planes are formed
-  // right after it and plane -1 (n) joins that chunk's sweeps; otherwise
-  // they come after all chunks, with sweeps of their own (a one-plane sweep
-  // launch costs nearly as much as a chunk's).
-  // the first x and y fluxes of a slab of planes need only its own x and y
-  // sweeps, so they fill the wait for the next input chunk
-  auto flux1_xy = [&](int zlo, int zext) {
-    Range rt;
-    for (int ax = 0; ax < 2; ++ax) { rt.lo[ax] = -1; rt.ext[ax] = n[ax] + 2; }
-    rt.lo[2] = zlo; rt.ext[2] = zext;
-    return launch_flux1_all(a, rt, 3u, st);
-  };
-  const int bclo = a.in.bc[2][0], bchi = a.in.bc[2][1];  // 0 outflow, 1 reflect, 2 periodic
-  const bool low_early = bclo == 0 || (bclo == 1 && zc(1) >= NG);
-  const bool high_early = bchi == 0 || (bchi == 1 && zc(C - 1) <= n[2] - NG);
+  // Every stage runs chunk by chunk over the planes whose inputs are ready,
+  // each zone and face exactly once, with the kernels of launch_step (so the
+  // result is bitwise the same).  With the primitive state on planes
+  // [-NG, q) the frontiers (exclusive upper bounds) are:
+  //   x and y tracing, their first fluxes, F^{x|y}, F^{y|x}: planes [-1, q)
+  //   z tracing: zones [-1, q - 3) (its stencil reaches 3 planes up)
+  //   first z fluxes, F^{z|x}, F^{z|y}, final z fluxes: z-faces f with zones
+  //     f - 1 and f traced (and the x/y quantities of planes f - 1, f)
+  //   F^{x|z}, F^{y|z}: zones k with z-faces k and k + 1 of the first fluxes
+  //   final x and y fluxes: planes k with F^{x|z}, F^{y|z} on k and
+  //     F^{z|y}, F^{z|x} on faces k, k + 1
+  //   update: planes k with the final z fluxes on faces k and k + 1
+  // and each chunk's updated planes go back while the next chunk computes.
+  // The front stages of a chunk (through the first fluxes) run on `st`, its
+  // back stages on p.back once the front stages are done; the front stages
+  // of later chunks write only planes and faces above those the back stages
+  // of earlier chunks read, so the two streams run side by side.
+  auto low_ready = [&](int L) { return bclo == 2 || (bclo == 0 && L >= 1) || (bclo == 1 && L >= NG); };
+  bool low_done = false;
+  int xy = -1, tz = -1, f1z = 0, f2xz = 0, f2z = 0, f3xy = 0, f3z = 0, upd = 0;  // done up to
   for (int k = 0; k < C; ++k) {
     if (cudaStreamWaitEvent(st, p.h2d_done[k], 0) != cudaSuccess) return cudaGetLastError();
-    int z0 = zc(k), ze = zc(k + 1) - zc(k);
-    prim(z0, ze);
-    if (low_early && k == 0) {
+    const bool last = k == C - 1;
+    const int L = zc(k + 1);
+    prim(zc(k), L - zc(k));
+    if (!low_done && low_ready(L)) {
       prim(-NG, NG);
-      z0 -= 1;
-      ze += 1;
+      low_done = true;
     }
-    if (high_early && k == C - 1) {
-      prim(n[2], NG);
-      ze += 1;
+    if (last) prim(nz, NG);  // the high ghost planes: every source plane has landed
+    const int q = !low_done ? -NG : last ? nz + NG : L;
+    // targets
+    const int xy1 = std::max(xy, std::min(q, nz + 1));
+    int tz1 = std::max(tz, std::min(q - 3, nz + 1));
+    if (!last) tz1 = tz + (tz1 - tz) / TILE_ZONES * TILE_ZONES;  // whole tiles until the last chunk
+    const int f1z1 = std::max(f1z, std::min(tz1, nz + 1));
+    const int f2xz1 = std::max(f2xz, std::min(f1z1 - 1, nz));
+    const int f2z1 = std::max(f2z, std::min(std::min(tz1, xy1), nz + 1));
+    const int f3xy1 = std::max(f3xy, std::min(std::min(f2xz1, f2z1 - 1), nz));
+    const int f3z1 = std::max(f3z, std::min(std::min(xy1, tz1), nz + 1));
+    const int upd1 = std::max(upd, std::min(std::min(f3xy1, f3z1 - 1), nz));
+    // tracing
+    if (xy1 > xy) {
+      launch_trace(0, a, xy, xy1 - xy, st);
+      launch_trace(1, a, xy, xy1 - xy, st);
+      nl += 2;
     }
-    launch_trace(0, a, z0, ze, st);
-    launch_trace(1, a, z0, ze, st);
-    nl += 2 + flux1_xy(z0, ze);
+    if (tz1 > tz) {
+      launch_trace_range(2, a, -1, n[1] + 2, tz, tz1 - 1, st);
+      nl += 1;
+    }
+    // first fluxes: x- and y-faces on planes [xy, xy1), z-faces [f1z, f1z1)
+    {
+      Range r[3];
+      for (int d = 0; d < 3; ++d) {
+        for (int ax = 0; ax < 2; ++ax) { r[d].lo[ax] = -1; r[d].ext[ax] = n[ax] + 2; }
+        r[d].lo[2] = xy; r[d].ext[2] = xy1 - xy;
+        if (d < 2) { r[d].lo[d] = 0; r[d].ext[d] = n[d] + 1; }
+      }
+      r[2].lo[2] = f1z; r[2].ext[2] = f1z1 - f1z;
+      nl += launch_flux1_ranges(a, r, 7u, st);
+    }
+    if (cudaEventRecord(p.front_done[k], st) != cudaSuccess) return cudaGetLastError();
+    if (cudaStreamWaitEvent(p.back, p.front_done[k], 0) != cudaSuccess) return cudaGetLastError();
+    // intermediate fluxes, sets (0,1), (0,2), (1,0), (1,2), (2,0), (2,1)
+    {
+      Range r[6] = {flux2_range(n, 0, 1, xy, xy1),   flux2_range(n, 0, 2, f2xz, f2xz1),
+                    flux2_range(n, 1, 0, xy, xy1),   flux2_range(n, 1, 2, f2xz, f2xz1),
+                    flux2_range(n, 2, 0, f2z, f2z1), flux2_range(n, 2, 1, f2z, f2z1)};
+      nl += launch_flux2_ranges(a, r, p.back);
+    }
+    // final fluxes (x- and y-faces on planes [f3xy, f3xy1), z-faces [f3z,
+    // f3z1)) and the update of planes [upd, upd1); after the last chunk in
+    // pieces of p.piece planes, each going back while the next computes
+    const int step = last ? std::max(p.piece, 1) : nz + 1;
+    for (int u0 = upd, a3 = f3xy, z3 = f3z; u0 < upd1 || a3 < f3xy1 || z3 < f3z1;) {
+      const int u1 = std::min(upd1, u0 + step);
+      const int b3 = std::max(a3, last ? std::min(f3xy1, u1) : f3xy1);
+      const int w3 = std::max(z3, last ? std::min(f3z1, u1 + 1) : f3z1);
+      Range r[3];
+      for (int d = 0; d < 3; ++d) {
+        for (int ax = 0; ax < 2; ++ax) { r[d].lo[ax] = 0; r[d].ext[ax] = n[ax]; }
+        r[d].lo[2] = a3; r[d].ext[2] = b3 - a3;
+        if (d < 2) r[d].ext[d] += 1;
+      }
+      r[2].lo[2] = z3; r[2].ext[2] = w3 - z3;
+      nl += launch_flux3_ranges(a, 3, r, p.back);
+      if (u1 > u0) {
+        Range ru;
+        ru.lo[0] = 0; ru.ext[0] = n[0];
+        ru.lo[1] = 0; ru.ext[1] = n[1];
+        ru.lo[2] = u0; ru.ext[2] = u1 - u0;
+        k_update<<<blocks_for(ru.count()), BLOCK, 0, p.back>>>(a.in, a.out, sg, s.F3[0], s.F3[1], s.F3[2], a.K, ru,
+                                                               a.flags);
+        nl += 1;
+        // an event may be recorded again once a wait on it is enqueued
+        if (cudaEventRecord(p.upd_done[k], p.back) != cudaSuccess) return cudaGetLastError();
+        if (cudaStreamWaitEvent(p.d2h, p.upd_done[k], 0) != cudaSuccess) return cudaGetLastError();
+        if (!copy(p.h_out, a.out.u, u0, u1, cudaMemcpyDeviceToHost, p.d2h)) return cudaGetLastError();
+      }
+      u0 = u1; a3 = b3; z3 = w3;
+    }
+    xy = xy1; tz = tz1; f1z = f1z1; f2xz = f2xz1; f2z = f2z1; f3xy = f3xy1; f3z = f3z1; upd = upd1;
   }
-  if (!low_early) {
-    prim(-NG, NG);
-    launch_trace(0, a, -1, 1, st);
-    launch_trace(1, a, -1, 1, st);
-    nl += 2 + flux1_xy(-1, 1);
-  }
-  if (!high_early) {
-    prim(n[2], NG);
-    launch_trace(0, a, n[2], 1, st);
-    launch_trace(1, a, n[2], 1, st);
-    nl += 2 + flux1_xy(n[2], 1);
-  }
-  // the z sweep
-  launch_trace(2, a, -1, n[1] + 2, st);
+  // the CFL estimate after every update; the caller's stream then waits for
+  // the back stages and the last output copy
+  k_dt_final<<<1, 1, 0, p.back>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], 3, a.cfl);
   nl += 1;
-  // first z fluxes on z-faces [0, n_z] x transverse [-1, n], intermediate fluxes F^{d|t}
-  {
-    Range rt;
-    for (int ax = 0; ax < 3; ++ax) { rt.lo[ax] = -1; rt.ext[ax] = n[ax] + 2; }
-    nl += launch_flux1_all(a, rt, 4u, st);
-  }
-  nl += launch_flux2_all(a, st);
-  // final fluxes and update chunk by chunk; each chunk's output planes go
-  // back while the next chunk computes.  A chunk computes z-faces
-  // [z0, z0 + ze], so the face it shares with the next chunk is formed by
-  // both, with the same value.  (Chunking the intermediate fluxes as well was
-  // measured: their duplicated planes and extra launches cost about what the
-  // longer overlap saves.)
-  for (int k = 0; k < C; ++k) {
-    const int z0 = zc(k), ze = zc(k + 1) - zc(k);
-    nl += launch_flux3_all(a, 3, z0, ze, st);
-    Range ru;
-    ru.lo[0] = 0; ru.ext[0] = n[0];
-    ru.lo[1] = 0; ru.ext[1] = n[1];
-    ru.lo[2] = z0; ru.ext[2] = ze;
-    k_update<<<blocks_for(ru.count()), BLOCK, 0, st>>>(a.in, a.out, sg, s.F3[0], s.F3[1], s.F3[2], a.K, ru, a.flags);
-    nl += 1;
-    if (cudaEventRecord(p.upd_done[k], st) != cudaSuccess) return cudaGetLastError();
-    if (cudaStreamWaitEvent(p.d2h, p.upd_done[k], 0) != cudaSuccess) return cudaGetLastError();
-    const long long off = (long long)(z0 + NG) * p.plane + rows_off;
-    for (int c = 0; c < 5; ++c)
-      if (cudaMemcpy2DAsync(p.h_out + c * p.field + off, plane_bytes, a.out.u + c * p.field + off, plane_bytes,
-                            rows_bytes, (size_t)ze, cudaMemcpyDeviceToHost, p.d2h) != cudaSuccess)
-        return cudaGetLastError();
-  }
-  k_dt_final<<<1, 1, 0, st>>>(a.flags, a.dx[0], a.dx[1], a.dx[2], 3, a.cfl);
-  nl += 1;
+  if (cudaEventRecord(p.back_done, p.back) != cudaSuccess) return cudaGetLastError();
   if (cudaEventRecord(p.d2h_done, p.d2h) != cudaSuccess) return cudaGetLastError();
+  if (cudaStreamWaitEvent(st, p.back_done, 0) != cudaSuccess) return cudaGetLastError();
   if (cudaStreamWaitEvent(st, p.d2h_done, 0) != cudaSuccess) return cudaGetLastError();
   if (launches) *launches += nl;
   return cudaGetLastError();

@@ -120,21 +120,28 @@ cudaError_t launch_record_faces(const StepArgs& a, int zlo, int zhi, double* fac
 
 // A 3-D step whose input arrives from, and whose output returns to, host
 // memory, with the copies overlapping the kernels: the interior z-planes
-// arrive in chunks on one copy stream, each chunk's primitive state and x/y
-// tracing sweeps start as soon as it has landed, and the final fluxes and the
-// update run chunk by chunk, each chunk's planes going back on a second copy
-// stream while the next chunk computes.  Every face has a derived boundary
-// (ghost zones come from interior zones).  Same kernels and per-zone
-// arithmetic as launch_step, so the result is bitwise the same.
-constexpr int PIPE_MAX_CHUNKS = 8;
+// arrive in chunks on one copy stream; after each chunk every stage runs
+// over the planes whose inputs have become ready (the z stencils trail the
+// landed planes by a few planes), and the planes it finishes go back on a
+// second copy stream while the next chunk computes.  The front stages
+// (primitive state, tracing, first fluxes) run on the caller's stream and
+// the back stages (intermediate and final fluxes, update) on a second
+// compute stream, one chunk behind, so that the two fill each other's
+// launch tails; they touch disjoint planes.  Every face has a derived
+// boundary (ghost zones come from interior zones).  Every zone and face is
+// computed once, by the kernels and per-zone arithmetic of launch_step, so
+// the result is bitwise the same.
+constexpr int PIPE_MAX_CHUNKS = 16;
 struct HostPipe {
   const double* h_in;            // host grown boxes in the natural layout
   double* h_out;
   long long field, plane;        // elements per field and per z-plane of the grown box
   int nchunk;                    // z-chunks of the interior, 1..PIPE_MAX_CHUNKS
+  int piece;                     // planes per piece of the last chunk's final fluxes and update
   cudaStream_t h2d, d2h;         // copy streams
-  cudaEvent_t start, d2h_done;
-  cudaEvent_t h2d_done[PIPE_MAX_CHUNKS], upd_done[PIPE_MAX_CHUNKS];
+  cudaStream_t back;             // compute stream of the back stages
+  cudaEvent_t start, d2h_done, back_done;
+  cudaEvent_t h2d_done[PIPE_MAX_CHUNKS], front_done[PIPE_MAX_CHUNKS], upd_done[PIPE_MAX_CHUNKS];
 };
 cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t stream, long long* launches);
 // enqueue a CFL estimate of the interior of a box into flags->dt_next

@@ -378,9 +378,11 @@ def test_reciprocal_square_root_error_bound():
 def test_host_buffer_step_matches_device_step():
     """hydro_advance_box_host on pageable and pinned host buffers gives the
     device path's result bit for bit: 3-D boxes with derived faces (interior
-    planes only cross the host link, in z-chunks that overlap the kernels;
-    4 to 44 planes, every z boundary kind), a prefilled face (the whole input
-    box crosses) and 2-D; a non-physical input is reported.
+    planes only cross the host link, in z-chunks that overlap the kernels,
+    every stage running over the planes whose inputs have landed, on two
+    compute streams; 4 to 100 planes, every z boundary kind), a prefilled
+    face (the whole input box crosses) and 2-D; a non-physical input is
+    reported.
     It writes none of the output's ghost planes along the slowest axis and
     refuses non-natural layouts."""
     rng = np.random.default_rng(12)
@@ -395,6 +397,10 @@ def test_host_buffer_step_matches_device_step():
         # reflecting z faces with chunks thinner than a ghost layer, and periodic z
         (3, (10, 8, 6), ((hb.BC_OUTFLOW,) * 2, (hb.BC_OUTFLOW,) * 2, (hb.BC_REFLECT,) * 2)),
         (3, (9, 12, 20), ((hb.BC_REFLECT,) * 2, (hb.BC_OUTFLOW,) * 2, (hb.BC_PERIODIC,) * 2)),
+        # chunks of 12-13 planes: the z tracing advances by whole tiles between
+        # chunks, and the last chunk's final fluxes and update go in pieces
+        (3, (24, 20, 100), ((hb.BC_OUTFLOW,) * 2, (hb.BC_REFLECT,) * 2, (hb.BC_PERIODIC,) * 2)),
+        (3, (16, 18, 77), ((hb.BC_PERIODIC,) * 2, (hb.BC_OUTFLOW,) * 2, (hb.BC_REFLECT, hb.BC_OUTFLOW))),
     ]
     for dim, n, bc in cases:
         U = inputs.random_box(rng, n, dim)
