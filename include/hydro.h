@@ -223,8 +223,10 @@ int hydro_batch_tuning(hydro_ctx_t* ctx, int* axis, int* extent, int* segment, i
  * output comes back the same way; the host output's ghost zones outside the
  * copied rows and planes are not written, and those inside are unspecified.
  * In 3-D with no prefilled face the copies run on two context-owned copy
- * streams in z-chunks that overlap the kernels on `stream` (fully so with
- * pinned host buffers); otherwise everything runs on `stream`.
+ * streams in z-chunks that overlap the kernels (fully so with pinned host
+ * buffers): the front stages run on `stream`, the back stages on a third
+ * context-owned stream, and `stream` waits for all of them before the call
+ * returns; otherwise everything runs on `stream`.
  * dt_next_host (nullable) receives the CFL step of the result; a
  * non-physical state returns HYDRO_EBADSTATE.  HYDRO_EINVAL for other
  * layouts or overlapping host buffers. */
