@@ -109,11 +109,26 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
   // low face, lambda_+ toward the high face), else the zone average.
   // o0 / o1: the low / high face's edge state (rho, un, ut1, ut2, p).
   const bool fast_lo = lt0(lam[0]), fast_hi = gt0(lam[2]);
-  double o0[5], o1[5];
+  // Flat parabolas (a+ - a- and a6 both +0, as the limiter leaves a zone at
+  // rest or at an extremum): the swept-volume term (+-)s/2 (da +- t a6) is
+  // +0 for any s, so I- is a- + (+0) = pz(a-) and I+ is a+ - (+0) = a+,
+  // bit for bit in either build; the integrals are skipped.
+  bool flat = true;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    o0[v] = fast_lo ? integ_minus(am[v], ap[v], dap[v], a6[v], sig[0]) : zone[v];
-    o1[v] = fast_hi ? integ_plus(am[v], ap[v], dap[v], a6[v], sig[2]) : zone[v];
+  for (int v = 0; v < 5; ++v) flat = flat && !ine(dbits(dap[v]) | dbits(a6[v]), 0LL);
+  double o0[5], o1[5];
+  if (flat) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      o0[v] = fast_lo ? pz(am[v]) : zone[v];
+      o1[v] = fast_hi ? ap[v] : zone[v];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      o0[v] = fast_lo ? integ_minus(am[v], ap[v], dap[v], a6[v], sig[0]) : zone[v];
+      o1[v] = fast_hi ? integ_plus(am[v], ap[v], dap[v], a6[v], sig[2]) : zone[v];
+    }
   }
   // Edge state = ref - sum of beta_nu r_nu over the waves that reach the
   // face: s_rho = ref - ((bm + b0) + bp), s_un = ref - (bm (-c/rho) + bp c/rho),
