@@ -327,6 +327,47 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
 // through shuffles.  The loads of a warp are consecutive doubles (the
 // sequential sweep along x reads with lanes along y, a cache line per lane).
 constexpr int ROW_ZONES = 30;
+
+// Zones at rest.  When, in every variable, a zone's average equals one of
+// its neighbours' (bit for bit), one of its one-sided differences is +0, so
+// every monotonised slope is +0 -- what mc_slope_d returns for them -- and
+// the differences are not formed.  When two neighbours are equal with equal
+// slopes in every variable, the interface value between them is the zone
+// value: (a + a)/2 - (s - s)/6 = a - (+0) = a, bit for bit with or without
+// contraction.  In a region at rest whole warps take these paths.
+__device__ __forceinline__ bool slopes_vanish(const double am1[5], const double a0[5], const double ap1[5]) {
+  bool z = true;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) z = z && (!ine(dbits(am1[v]), dbits(a0[v])) || !ine(dbits(a0[v]), dbits(ap1[v])));
+  return z;
+}
+__device__ __forceinline__ void zone_slopes(const double am1[5], const double a0[5], const double ap1[5], double sl[5]) {
+  if (slopes_vanish(am1, a0, ap1)) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sl[v] = 0.0;
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sl[v] = mc_slope_d(a0[v] - am1[v], ap1[v] - a0[v], am1[v], ap1[v]);
+  }
+}
+__device__ __forceinline__ bool faces_trivial(const double a0[5], const double a1[5], const double s0[5],
+                                              const double s1[5]) {
+  bool z = true;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) z = z && !ine(dbits(a0[v]), dbits(a1[v])) && !ine(dbits(s0[v]), dbits(s1[v]));
+  return z;
+}
+__device__ __forceinline__ void zone_faces(const double a0[5], const double a1[5], const double s0[5],
+                                           const double s1[5], double fp[5]) {
+  if (faces_trivial(a0, a1, s0, s1)) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fp[v] = a0[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fp[v] = face_value(a0[v], a1[v], s0[v], s1[v]);
+  }
+}
+
 __device__ __forceinline__ double shfl_up1(double x) { return __shfl_up_sync(0xffffffffu, x, 1); }
 __device__ __forceinline__ double shfl_dn1(double x) { return __shfl_down_sync(0xffffffffu, x, 1); }
 
@@ -360,13 +401,13 @@ __device__ __forceinline__ void trace_row_x_item(ScratchGeom sg, const double* _
   }
   // this zone's slope and flattening coefficient
   double sl[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) sl[v] = mc_slope_d(a0[v] - am1[v], ap1[v] - a0[v], am1[v], ap1[v]);
+  zone_slopes(am1, a0, ap1, sl);
   const double ct0 = K.flatten ? flat_tilde(pm2, am1[4], ap1[4], pp2, am1[1], ap1[1], K.small_pres) : 1.0;
   // the interface value at the high face, from the next zone's slope
-  double fp[5], fm[5];
+  double fp[5], fm[5], sn[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) fp[v] = face_value(a0[v], ap1[v], sl[v], shfl_dn1(sl[v]));
+  for (int v = 0; v < 5; ++v) sn[v] = shfl_dn1(sl[v]);
+  zone_faces(a0, ap1, sl, sn, fp);
 #pragma unroll
   for (int v = 0; v < 5; ++v) fm[v] = shfl_up1(fp[v]);
   const double ctm = shfl_up1(ct0), ctp = shfl_dn1(ct0);
@@ -433,8 +474,10 @@ __device__ __forceinline__ void trace_tile_item(ScratchGeom sg, const double* __
         a0[v] = qv[v][id];
         ap1[v] = qv[v][id + st];
       }
+      double sl[5];
+      zone_slopes(am1, a0, ap1, sl);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sm.sl[v][r][threadIdx.x & 31] = mc_slope_d(a0[v] - am1[v], ap1[v] - a0[v], am1[v], ap1[v]);
+      for (int v = 0; v < 5; ++v) sm.sl[v][r][threadIdx.x & 31] = sl[v];
       sm.ct[r][threadIdx.x & 31] =
           K.flatten ? flat_tilde(qv[4][id - 2 * st], am1[4], ap1[4], qv[4][id + 2 * st], am1[1], ap1[1], K.small_pres)
                     : 1.0;
@@ -446,10 +489,18 @@ __device__ __forceinline__ void trace_tile_item(ScratchGeom sg, const double* __
     const int i = t0 - 1 + r;
     if (cvalid && i <= R.nd) {
       const long long id = id0 + (long long)(r - 1) * st;
+      const int l = threadIdx.x & 31;
+      double a0[5], a1[5], s0[5], s1[5], fp[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v)
-        sm.fp[v][r][threadIdx.x & 31] =
-            face_value(qv[v][id], qv[v][id + st], sm.sl[v][r][threadIdx.x & 31], sm.sl[v][r + 1][threadIdx.x & 31]);
+      for (int v = 0; v < 5; ++v) {
+        a0[v] = qv[v][id];
+        a1[v] = qv[v][id + st];
+        s0[v] = sm.sl[v][r][l];
+        s1[v] = sm.sl[v][r + 1][l];
+      }
+      zone_faces(a0, a1, s0, s1, fp);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.fp[v][r][l] = fp[v];
     }
   }
   __syncthreads();
