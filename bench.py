@@ -1026,7 +1026,12 @@ def run_ours(args):
                                   "the hardware's issued operations: an FMA counts 2, a divide or square root 1 "
                                   "although it issues 4-9 FP64 instructions"},
         "step_fp64": {"algorithmic_gflops": step_gflops, "frac_of_derived": step_gflops / FP64_PEAK_GFLOPS,
-                      "frac_of_measured": step_gflops / fp64_measured},
+                      "frac_of_measured": step_gflops / fp64_measured,
+                      "note": "the oracle's operation count per unit, which forms every slope, interface value and "
+                              "swept-volume integral; the tracing kernels skip those of zones at rest (flat data, "
+                              "bit-identical results), so on a blast in a quiescent box this rate counts work the "
+                              "GPU does not issue.  The roofline's dominant stage (intermediate solves) skips "
+                              "nothing."},
         "hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
                 "nominal_peak_gbs": 7700.0, "frac_of_nominal": step_gbs / 7700.0,
                 "note": "algorithmic bytes of the whole step (read grown box, write interior) / step time, of measured"},
