@@ -565,8 +565,32 @@ __device__ __forceinline__ void flux1_item(ScratchGeom sg, double* __restrict__ 
   store5(F1, sg.sc, id, F);
 }
 
+// U <- U - c (F[hi] - F[lo]), five components.  Where the two fluxes are
+// equal bit for bit in every component (a region at rest), each difference
+// is +0 and U - c (+0) is U with or without contraction, so the arithmetic
+// is skipped; whole warps take that path outside a blast.
+__device__ __forceinline__ void sub_flux_difference(double U[5], double c, const double* __restrict__ F,
+                                                    long long sc, long long hi, long long lo) {
+  double fh[5], fl[5];
+  bool same = true;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    fh[k] = F[k * sc + hi];
+    fl[k] = F[k * sc + lo];
+    same = same && !ine(dbits(fh[k]), dbits(fl[k]));
+  }
+  if (!same) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k] = U[k] - c * (fh[k] - fl[k]);
+  }
+}
+
 // transverse correction of a traced state (conserved form at T[.., id]) by
-// one or two flux differences, back to a face state
+// one or two flux differences, back to a face state.  SKIP: skip the
+// differences of equal fluxes (the final solves); the intermediate solves'
+// integer pipe is the busier one, and there the equality tests cost more
+// than they save.
+template <bool SKIP>
 __device__ __forceinline__ void correct(const double* __restrict__ T, long long id, const StepConst& K, double ca,
                                         const double* Fa, long long sc, long long ida_hi, long long ida_lo,
                                         double cb, const double* Fb, long long idb_hi, long long idb_lo,
@@ -577,10 +601,15 @@ __device__ __forceinline__ void correct(const double* __restrict__ T, long long 
   U[2] = T[(TS_MOM + 1) * sc + id];
   U[3] = T[(TS_MOM + 2) * sc + id];
   U[4] = T[TS_E * sc + id];
+  if (SKIP) {
+    sub_flux_difference(U, ca, Fa, sc, ida_hi, ida_lo);
+    if (Fb) sub_flux_difference(U, cb, Fb, sc, idb_hi, idb_lo);
+  } else {
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    U[c] = U[c] - ca * (Fa[c * sc + ida_hi] - Fa[c * sc + ida_lo]);
-    if (Fb) U[c] = U[c] - cb * (Fb[c * sc + idb_hi] - Fb[c * sc + idb_lo]);
+    for (int c = 0; c < 5; ++c) {
+      U[c] = U[c] - ca * (Fa[c * sc + ida_hi] - Fa[c * sc + ida_lo]);
+      if (Fb) U[c] = U[c] - cb * (Fb[c * sc + idb_hi] - Fb[c * sc + idb_lo]);
+    }
   }
   state_from_cons(U, K, s);
 }
@@ -597,8 +626,8 @@ __device__ __forceinline__ void flux2_item(ScratchGeom sg, const double* __restr
   const long long id = sg.id(i, j, k), zl = id - sd;
   const double coef = K.dtdx[T] * THIRD;
   double sL[NS], sR[NS], F[5];
-  correct(TP, zl, K, coef, F1t, sg.sc, zl + stt, zl, 0.0, nullptr, 0, 0, sL);
-  correct(TM, id, K, coef, F1t, sg.sc, id + stt, id, 0.0, nullptr, 0, 0, sR);
+  correct<false>(TP, zl, K, coef, F1t, sg.sc, zl + stt, zl, 0.0, nullptr, 0, 0, sL);
+  correct<false>(TM, id, K, coef, F1t, sg.sc, id + stt, id, 0.0, nullptr, 0, 0, sR);
   hllc_flux<EINF>(sL, sR, D, K, F);
   store5(F2, sg.sc, id, F);
 }
@@ -619,8 +648,8 @@ __device__ __forceinline__ void flux3_item(ScratchGeom sg, const double* __restr
   const long long id = sg.id(i, j, k), zl = id - sd;
   const double ca = 0.5 * K.dtdx[T1], cb = 0.5 * K.dtdx[T2];
   double sL[NS], sR[NS], F[5];
-  correct(TP, zl, K, ca, Fa, sg.sc, zl + s1, zl, cb, Fb, zl + s2, zl, sL);
-  correct(TM, id, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
+  correct<true>(TP, zl, K, ca, Fa, sg.sc, zl + s1, zl, cb, Fb, zl + s2, zl, sL);
+  correct<true>(TM, id, K, ca, Fa, sg.sc, id + s1, id, cb, Fb, id + s2, id, sR);
   hllc_flux<EINF>(sL, sR, D, K, F);
   store5(F3, sg.sc, id, F);
 }
@@ -657,13 +686,11 @@ __device__ __forceinline__ void update_item(BoxGeom in, BoxGeom out, ScratchGeom
 #pragma unroll
     for (int c = 0; c < 5; ++c) u0[c] = in.u[c * in.sc + ii];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double v = u0[c];
+    for (int c = 0; c < 5; ++c) u1[c] = u0[c];
+    // direction by direction, each component in the order d = 0, 1, 2
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        if (d < K.dim) v = v - K.dtdx[d] * (F[d][c * sg.sc + id + st[d]] - F[d][c * sg.sc + id]);
-      u1[c] = v;
-    }
+    for (int d = 0; d < 3; ++d)
+      if (d < K.dim) sub_flux_difference(u1, K.dtdx[d], F[d], sg.sc, id + st[d], id);
     if (K.has_grav) {
       double rho_mid = dhalf(u0[0] + u1[0]);
       const double dtr = mul_i(K.dt, rho_mid);
