@@ -520,6 +520,22 @@ int hydro_selftest_divsqrt(const double* x, const double* y, double* rcp, double
  * them bit for bit with the IEEE operations (round to nearest even). */
 int hydro_selftest_intpipe(const double* x, const double* y, double* prod, double* sum, long long n, void* stream);
 
+/* Diagnostics (no counterpart in the paper; host only, no device needed):
+ * the schedule hydro_advance_box_host runs for a 3-D box of nz interior
+ * planes with derived faces, input copied in nchunk z-chunks
+ * (1 <= nchunk <= min(nz, 16), nz >= 4), low z face of kind bc_low
+ * (HYDRO_BC_OUTFLOW, _REFLECT or _PERIODIC).  Writes *pre_lo (interior
+ * planes [*pre_lo, nz) are copied ahead of the chunks) and, per chunk k,
+ * 22 ints at out[22 k]: ten half-open [lo, hi) ranges along z -- interior
+ * planes copied in, interior planes whose primitive state is formed, then
+ * planes of the x/y tracing, first x/y fluxes and F^{x|y}, F^{y|x} (from
+ * -1), zones of the z tracing (from -1), z-faces of the first z fluxes,
+ * planes of F^{x|z}, F^{y|z}, z-faces of F^{z|x}, F^{z|y}, planes of the
+ * final x/y fluxes, z-faces of the final z fluxes, planes of the update --
+ * then two flags: the low and the high ghost planes' primitive state is
+ * formed with this chunk.  HYDRO_EINVAL for other arguments. */
+int hydro_pipe_plan(int nz, int nchunk, int bc_low, int* pre_lo, int* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -161,6 +161,8 @@ def lib(variant="default"):
     L.hydro_advance_box_steps.argtypes = [vp, ctypes.POINTER(hydro_box_t), ctypes.POINTER(hydro_box_t),
                                           ctypes.POINTER(hydro_params_t), ctypes.c_int, vp, vp, vp]
     L.hydro_ctx_face_flux.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.hydro_pipe_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
     _LIBS[variant] = L
     return L
 
@@ -219,6 +221,26 @@ def hydro_selftest_scale2(x, variant="default", stream=None):
     if rc:
         raise HydroError(rc, "hydro_selftest_scale2")
     return t, h
+
+
+PIPE_RANGES = ("h2d", "prim", "xy", "tz", "f1z", "f2xz", "f2z", "f3xy", "f3z", "upd")
+
+
+def hydro_pipe_plan(nz, nchunk, bc_low):
+    """The host-buffer step's chunk schedule (host only): (pre_lo, [per chunk
+    {range name: (lo, hi)} plus "ghosts_low", "ghosts_high"])."""
+    pre = ctypes.c_int(0)
+    out = (ctypes.c_int * (22 * max(nchunk, 1)))()
+    rc = lib().hydro_pipe_plan(int(nz), int(nchunk), int(bc_low), ctypes.byref(pre), out)
+    if rc:
+        raise HydroError(rc, "hydro_pipe_plan")
+    chunks = []
+    for k in range(nchunk):
+        o = out[22 * k: 22 * k + 22]
+        c = {name: (o[2 * r], o[2 * r + 1]) for r, name in enumerate(PIPE_RANGES)}
+        c["ghosts_low"], c["ghosts_high"] = bool(o[20]), bool(o[21])
+        chunks.append(c)
+    return pre.value, chunks
 
 
 def hydro_selftest_rsqrt(x, variant="default", stream=None):

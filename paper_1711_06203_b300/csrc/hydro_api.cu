@@ -676,6 +676,22 @@ int hydro_selftest_rsqrt(const double* x, double* out, long long n, void* stream
   return cudaGetLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 
+int hydro_pipe_plan(int nz, int nchunk, int bc_low, int* pre_lo, int* out) {
+  if (!pre_lo || !out || nchunk < 1 || nchunk > PIPE_MAX_CHUNKS) return HYDRO_EINVAL;
+  PipeChunk plan[PIPE_MAX_CHUNKS];
+  if (!pipe_plan(nz, nchunk, bc_low, pre_lo, plan)) return HYDRO_EINVAL;
+  for (int k = 0; k < nchunk; ++k) {
+    int* o = out + 22 * k;
+    for (int r = 0; r < PR_COUNT; ++r) {
+      o[2 * r] = plan[k].lo[r];
+      o[2 * r + 1] = plan[k].hi[r];
+    }
+    o[20] = plan[k].ghosts_low;
+    o[21] = plan[k].ghosts_high;
+  }
+  return HYDRO_OK;
+}
+
 int hydro_selftest_fp64_rate(double* out, int nblocks, int iters, void* stream) {
   if (!out || nblocks < 1 || iters < 1) return HYDRO_EINVAL;
   k_selftest_fp64_rate<<<(unsigned)nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(out, iters, 0.999999,

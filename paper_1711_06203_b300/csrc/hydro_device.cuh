@@ -375,13 +375,11 @@ __device__ __forceinline__ void state_from_cons(const double U[5], const StepCon
 // chi~ of zone j from p_{j-2..j+2} and the normal velocities u_{j-1}, u_{j+1}
 __device__ __forceinline__ double flat_tilde(double pm2, double pm1, double pp1, double pp2, double um1, double up1,
                                              double small_pres) {
-  // u_{j-1} - u_{j+1} > 0 as an order comparison (a rounded difference has
-  // the sign of the exact one and vanishes only for equal operands), taken
-  // before any pressure difference is formed
-  if (!dless(up1, um1)) return 1.0;
   double dp1 = pp1 - pm1;
-  if (abs_gt(dp1, mul_i(FLAT_EPS, dmin_nn(pp1, pm1)))) {
-    double dp2 = pp2 - pm2;
+  double dp2 = pp2 - pm2;
+  // u_{j-1} - u_{j+1} > 0 as an order comparison (a rounded difference has
+  // the sign of the exact one and vanishes only for equal operands)
+  if (dless(up1, um1) && abs_gt(dp1, mul_i(FLAT_EPS, dmin_nn(pp1, pm1)))) {
     double z = dabs(dp1) / dmax_nn(dabs(dp2), small_pres);
     double f = dmax(0.0, dmin(1.0, mul_i(FLAT_OMEGA2, z - FLAT_OMEGA1)));
     return 1.0 - f;

@@ -92,7 +92,11 @@ __device__ __forceinline__ void prim_item(BoxGeom in, ScratchGeom sg, double* __
 // ---- stage 3 of a zone: characteristic tracing from its parabolas
 // am/ap/dap (= ap - am)/a6/zone: (rho, un, ut1, ut2, p); outputs the zone's low- and high-face
 // states to TM/TP at id in absolute component order.
-template <int D>
+// SKIP_FLAT: test for flat parabolas and skip their integrals (below); the
+// sequential sweep leaves it off: on data where every zone moves the test's
+// branch cost its launches 11 % (the row and tile kernels 4-5 %, which the
+// zones at rest of a blast repay several times over)
+template <int D, bool SKIP_FLAT = true>
 __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5], const double dap[5],
                                            const double a6[5], const double zone[5], double c, double rho_c,
                                            double c_rho, double inv_c2, const StepConst& K, double* __restrict__ TM,
@@ -113,11 +117,11 @@ __device__ __forceinline__ void trace_zone(const double am[5], const double ap[5
   // rest or at an extremum): the swept-volume term (+-)s/2 (da +- t a6) is
   // +0 for any s, so I- is a- + (+0) = pz(a-) and I+ is a+ - (+0) = a+,
   // bit for bit in either build; the integrals are skipped.
-  bool flat = true;
+  long long nonflat = 0;  // OR of the bit patterns: 0 only if every one is +0
 #pragma unroll
-  for (int v = 0; v < 5; ++v) flat = flat && !ine(dbits(dap[v]) | dbits(a6[v]), 0LL);
+  for (int v = 0; v < 5; ++v) nonflat |= dbits(dap[v]) | dbits(a6[v]);
   double o0[5], o1[5];
-  if (flat) {
+  if (SKIP_FLAT && !ine(nonflat, 0LL)) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       o0[v] = fast_lo ? pz(am[v]) : zone[v];
@@ -302,7 +306,7 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
       sl[v] = s1;
       fm[v] = fp;
     }
-    trace_zone<D>(am, ap, dap, a6, zone, cz[0], cz[1], cz[2], cz[3], K, TM, TP, sc, id);
+    trace_zone<D, false>(am, ap, dap, a6, zone, cz[0], cz[1], cz[2], cz[3], K, TM, TP, sc, id);
     // slide the windows one zone
     pm2 = pm1;
     pm1 = a0[4];
@@ -328,18 +332,19 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
 // sequential sweep along x reads with lanes along y, a cache line per lane).
 constexpr int ROW_ZONES = 30;
 
-// Zones at rest.  When, in every variable, a zone's average equals one of
-// its neighbours' (bit for bit), one of its one-sided differences is +0, so
-// every monotonised slope is +0 -- what mc_slope_d returns for them -- and
-// the differences are not formed.  When two neighbours are equal with equal
+// Zones at rest.  When, in every variable, a zone's average equals its
+// neighbours' (bit for bit), its one-sided differences are +0, so every
+// monotonised slope is +0 -- what mc_slope_d returns for them -- and the
+// differences are not formed.  When two neighbours are equal with equal
 // slopes in every variable, the interface value between them is the zone
 // value: (a + a)/2 - (s - s)/6 = a - (+0) = a, bit for bit with or without
-// contraction.  In a region at rest whole warps take these paths.
+// contraction.  Each test is one OR of the operands' bit differences; in a
+// region at rest whole warps take these paths.
 __device__ __forceinline__ bool slopes_vanish(const double am1[5], const double a0[5], const double ap1[5]) {
-  bool z = true;
+  long long diff = 0;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) z = z && (!ine(dbits(am1[v]), dbits(a0[v])) || !ine(dbits(a0[v]), dbits(ap1[v])));
-  return z;
+  for (int v = 0; v < 5; ++v) diff |= (dbits(am1[v]) ^ dbits(a0[v])) | (dbits(a0[v]) ^ dbits(ap1[v]));
+  return !ine(diff, 0LL);
 }
 __device__ __forceinline__ void zone_slopes(const double am1[5], const double a0[5], const double ap1[5], double sl[5]) {
   if (slopes_vanish(am1, a0, ap1)) {
@@ -352,10 +357,10 @@ __device__ __forceinline__ void zone_slopes(const double am1[5], const double a0
 }
 __device__ __forceinline__ bool faces_trivial(const double a0[5], const double a1[5], const double s0[5],
                                               const double s1[5]) {
-  bool z = true;
+  long long diff = 0;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) z = z && !ine(dbits(a0[v]), dbits(a1[v])) && !ine(dbits(s0[v]), dbits(s1[v]));
-  return z;
+  for (int v = 0; v < 5; ++v) diff |= (dbits(a0[v]) ^ dbits(a1[v])) | (dbits(s0[v]) ^ dbits(s1[v]));
+  return !ine(diff, 0LL);
 }
 __device__ __forceinline__ void zone_faces(const double a0[5], const double a1[5], const double s0[5],
                                            const double s1[5], double fp[5]) {

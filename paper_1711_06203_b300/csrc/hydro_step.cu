@@ -450,14 +450,70 @@ cudaError_t launch_step_slabs(const StepArgs& a, int T, double* faces, cudaStrea
   return cudaGetLastError();
 }
 
+// With the primitive state on planes [-NG, q) the frontiers (exclusive upper
+// bounds) are:
+//   x and y tracing, their first fluxes, F^{x|y}, F^{y|x}: planes [-1, q)
+//   z tracing: zones [-1, q - 3) (its stencil reaches 3 planes up), in whole
+//     tiles until the last chunk
+//   first z fluxes, F^{z|x}, F^{z|y}, final z fluxes: z-faces f with zones
+//     f - 1 and f traced (and the x/y quantities of planes f - 1, f)
+//   F^{x|z}, F^{y|z}: zones k with z-faces k and k + 1 of the first fluxes
+//   final x and y fluxes: planes k with F^{x|z}, F^{y|z} on k and
+//     F^{z|y}, F^{z|x} on faces k, k + 1
+//   update: planes k with the final z fluxes on faces k and k + 1
+bool pipe_plan(int nz, int C, int bclo, int* pre_lo, PipeChunk* out) {
+  if (nz < NG || C < 1 || C > nz || bclo < 0 || bclo > 2 || !pre_lo || !out) return false;
+  auto zc = [&](int k) { return (int)((long long)nz * k / C); };  // first interior plane of chunk k
+  // a periodic low face takes its ghost planes from the top NG interior
+  // planes: those are copied first, so that the bottom can start with chunk 0
+  const int pre = (bclo == 2) ? nz - NG : nz;
+  *pre_lo = pre;
+  auto low_ready = [&](int L) { return bclo == 2 || (bclo == 0 && L >= 1) || (bclo == 1 && L >= NG); };
+  bool low_done = false;
+  int done[PR_COUNT] = {};  // done up to
+  done[PR_XY] = -1;
+  done[PR_TZ] = -1;
+  for (int k = 0; k < C; ++k) {
+    PipeChunk& c = out[k];
+    const bool last = k == C - 1;
+    const int L = zc(k + 1);
+    c.lo[PR_H2D] = zc(k);
+    c.hi[PR_H2D] = std::max(zc(k), std::min(L, pre));
+    c.lo[PR_PRIM] = zc(k);
+    c.hi[PR_PRIM] = L;
+    c.ghosts_low = !low_done && low_ready(L);
+    low_done = low_done || c.ghosts_low;
+    c.ghosts_high = last;  // every source plane has landed
+    const int q = !low_done ? -NG : last ? nz + NG : L;
+    int t[PR_COUNT];
+    t[PR_XY] = std::max(done[PR_XY], std::min(q, nz + 1));
+    t[PR_TZ] = std::max(done[PR_TZ], std::min(q - 3, nz + 1));
+    if (!last) t[PR_TZ] = done[PR_TZ] + (t[PR_TZ] - done[PR_TZ]) / TILE_ZONES * TILE_ZONES;
+    t[PR_F1Z] = std::max(done[PR_F1Z], std::min(t[PR_TZ], nz + 1));
+    t[PR_F2XZ] = std::max(done[PR_F2XZ], std::min(t[PR_F1Z] - 1, nz));
+    t[PR_F2Z] = std::max(done[PR_F2Z], std::min(std::min(t[PR_TZ], t[PR_XY]), nz + 1));
+    t[PR_F3XY] = std::max(done[PR_F3XY], std::min(std::min(t[PR_F2XZ], t[PR_F2Z] - 1), nz));
+    t[PR_F3Z] = std::max(done[PR_F3Z], std::min(std::min(t[PR_XY], t[PR_TZ]), nz + 1));
+    t[PR_UPD] = std::max(done[PR_UPD], std::min(std::min(t[PR_F3XY], t[PR_F3Z] - 1), nz));
+    for (int r = PR_XY; r < PR_COUNT; ++r) {
+      c.lo[r] = done[r];
+      c.hi[r] = t[r];
+      done[r] = t[r];
+    }
+  }
+  return true;
+}
+
 cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t st, long long* launches) {
   const int* n = a.in.n;
   const int nz = n[2];
   const ScratchGeom& sg = a.sg;
   const Scratch& s = a.s;
   const int C = p.nchunk;
+  PipeChunk plan[PIPE_MAX_CHUNKS];
+  int pre = nz;
+  if (C > PIPE_MAX_CHUNKS || !pipe_plan(nz, C, a.in.bc[2][0], &pre, plan)) return cudaErrorInvalidValue;
   long long nl = 0;
-  auto zc = [&](int k) { return (int)((long long)nz * k / C); };  // first interior plane of chunk k
   const size_t plane_bytes = (size_t)p.plane * sizeof(double);
   // of each plane, the interior rows: one contiguous run of n_y rows
   const long long row = p.plane / (n[1] + 2 * NG), rows_off = NG * row;
@@ -471,11 +527,7 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     return true;
   };
   // input planes, chunk by chunk, after the work already queued on the
-  // compute stream (which may still read the staging box).  A periodic low
-  // face takes its ghost planes from the top NG interior planes: those go
-  // first, so that the bottom of the box can start with chunk 0.
-  const int bclo = a.in.bc[2][0];  // 0 outflow, 1 reflect, 2 periodic
-  const int pre = (bclo == 2) ? nz - NG : nz;
+  // compute stream (which may still read the staging box)
   k_reset_step<<<1, 32, 0, st>>>(a.flags);
   nl += 1;
   if (cudaEventRecord(p.start, st) != cudaSuccess) return cudaGetLastError();
@@ -483,8 +535,10 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
   if (cudaStreamWaitEvent(p.back, p.start, 0) != cudaSuccess) return cudaGetLastError();
   if (pre < nz && !copy(a.in.u, p.h_in, pre, nz, cudaMemcpyHostToDevice, p.h2d)) return cudaGetLastError();
   for (int k = 0; k < C; ++k) {
-    const int z1 = std::min(zc(k + 1), pre);
-    if (z1 > zc(k) && !copy(a.in.u, p.h_in, zc(k), z1, cudaMemcpyHostToDevice, p.h2d)) return cudaGetLastError();
+    const PipeChunk& c = plan[k];
+    if (c.hi[PR_H2D] > c.lo[PR_H2D] &&
+        !copy(a.in.u, p.h_in, c.lo[PR_H2D], c.hi[PR_H2D], cudaMemcpyHostToDevice, p.h2d))
+      return cudaGetLastError();
     if (cudaEventRecord(p.h2d_done[k], p.h2d) != cudaSuccess) return cudaGetLastError();
   }
   auto prim = [&](int zlo, int zext) {
@@ -495,58 +549,31 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
     k_prim<<<blocks_for(r.count()), BLOCK, 0, st>>>(a.in, sg, s.Q, a.K, r, a.flags);
     nl += 1;
   };
-  // Every stage runs chunk by chunk over the planes whose inputs are ready,
-  // each zone and face exactly once, with the kernels of launch_step (so the
-  // result is bitwise the same).  With the primitive state on planes
-  // [-NG, q) the frontiers (exclusive upper bounds) are:
-  //   x and y tracing, their first fluxes, F^{x|y}, F^{y|x}: planes [-1, q)
-  //   z tracing: zones [-1, q - 3) (its stencil reaches 3 planes up)
-  //   first z fluxes, F^{z|x}, F^{z|y}, final z fluxes: z-faces f with zones
-  //     f - 1 and f traced (and the x/y quantities of planes f - 1, f)
-  //   F^{x|z}, F^{y|z}: zones k with z-faces k and k + 1 of the first fluxes
-  //   final x and y fluxes: planes k with F^{x|z}, F^{y|z} on k and
-  //     F^{z|y}, F^{z|x} on faces k, k + 1
-  //   update: planes k with the final z fluxes on faces k and k + 1
-  // and each chunk's updated planes go back while the next chunk computes.
-  // The front stages of a chunk (through the first fluxes) run on `st`, its
-  // back stages on p.back once the front stages are done; the front stages
-  // of later chunks write only planes and faces above those the back stages
-  // of earlier chunks read, so the two streams run side by side.
-  auto low_ready = [&](int L) { return bclo == 2 || (bclo == 0 && L >= 1) || (bclo == 1 && L >= NG); };
-  bool low_done = false;
-  int xy = -1, tz = -1, f1z = 0, f2xz = 0, f2z = 0, f3xy = 0, f3z = 0, upd = 0;  // done up to
+  // After each chunk every stage runs over the ranges of the plan (each zone
+  // and face once, with the kernels of launch_step, so the result is bitwise
+  // the same).  The front stages of a chunk (through the first fluxes) run
+  // on `st`, its back stages on p.back once the front stages are done; the
+  // front stages of later chunks write only planes and faces above those
+  // the back stages of earlier chunks read, so the two streams run side by
+  // side; each chunk's updated planes go back while the next computes.
   for (int k = 0; k < C; ++k) {
-    if (cudaStreamWaitEvent(st, p.h2d_done[k], 0) != cudaSuccess) return cudaGetLastError();
+    const PipeChunk& c = plan[k];
     const bool last = k == C - 1;
-    const int L = zc(k + 1);
-    prim(zc(k), L - zc(k));
-    if (!low_done && low_ready(L)) {
-      prim(-NG, NG);
-      low_done = true;
-    }
-    if (last) prim(nz, NG);  // the high ghost planes: every source plane has landed
-    const int q = !low_done ? -NG : last ? nz + NG : L;
-    // targets
-    const int xy1 = std::max(xy, std::min(q, nz + 1));
-    int tz1 = std::max(tz, std::min(q - 3, nz + 1));
-    if (!last) tz1 = tz + (tz1 - tz) / TILE_ZONES * TILE_ZONES;  // whole tiles until the last chunk
-    const int f1z1 = std::max(f1z, std::min(tz1, nz + 1));
-    const int f2xz1 = std::max(f2xz, std::min(f1z1 - 1, nz));
-    const int f2z1 = std::max(f2z, std::min(std::min(tz1, xy1), nz + 1));
-    const int f3xy1 = std::max(f3xy, std::min(std::min(f2xz1, f2z1 - 1), nz));
-    const int f3z1 = std::max(f3z, std::min(std::min(xy1, tz1), nz + 1));
-    const int upd1 = std::max(upd, std::min(std::min(f3xy1, f3z1 - 1), nz));
-    // tracing
+    if (cudaStreamWaitEvent(st, p.h2d_done[k], 0) != cudaSuccess) return cudaGetLastError();
+    prim(c.lo[PR_PRIM], c.hi[PR_PRIM] - c.lo[PR_PRIM]);
+    if (c.ghosts_low) prim(-NG, NG);
+    if (c.ghosts_high) prim(nz, NG);
+    const int xy = c.lo[PR_XY], xy1 = c.hi[PR_XY];
     if (xy1 > xy) {
       launch_trace(0, a, xy, xy1 - xy, st);
       launch_trace(1, a, xy, xy1 - xy, st);
       nl += 2;
     }
-    if (tz1 > tz) {
-      launch_trace_range(2, a, -1, n[1] + 2, tz, tz1 - 1, st);
+    if (c.hi[PR_TZ] > c.lo[PR_TZ]) {
+      launch_trace_range(2, a, -1, n[1] + 2, c.lo[PR_TZ], c.hi[PR_TZ] - 1, st);
       nl += 1;
     }
-    // first fluxes: x- and y-faces on planes [xy, xy1), z-faces [f1z, f1z1)
+    // first fluxes: x- and y-faces on planes [xy, xy1), z-faces of PR_F1Z
     {
       Range r[3];
       for (int d = 0; d < 3; ++d) {
@@ -554,23 +581,24 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
         r[d].lo[2] = xy; r[d].ext[2] = xy1 - xy;
         if (d < 2) { r[d].lo[d] = 0; r[d].ext[d] = n[d] + 1; }
       }
-      r[2].lo[2] = f1z; r[2].ext[2] = f1z1 - f1z;
+      r[2].lo[2] = c.lo[PR_F1Z]; r[2].ext[2] = c.hi[PR_F1Z] - c.lo[PR_F1Z];
       nl += launch_flux1_ranges(a, r, 7u, st);
     }
     if (cudaEventRecord(p.front_done[k], st) != cudaSuccess) return cudaGetLastError();
     if (cudaStreamWaitEvent(p.back, p.front_done[k], 0) != cudaSuccess) return cudaGetLastError();
     // intermediate fluxes, sets (0,1), (0,2), (1,0), (1,2), (2,0), (2,1)
     {
-      Range r[6] = {flux2_range(n, 0, 1, xy, xy1),   flux2_range(n, 0, 2, f2xz, f2xz1),
-                    flux2_range(n, 1, 0, xy, xy1),   flux2_range(n, 1, 2, f2xz, f2xz1),
-                    flux2_range(n, 2, 0, f2z, f2z1), flux2_range(n, 2, 1, f2z, f2z1)};
+      const int a2 = c.lo[PR_F2XZ], b2 = c.hi[PR_F2XZ], z2 = c.lo[PR_F2Z], w2 = c.hi[PR_F2Z];
+      Range r[6] = {flux2_range(n, 0, 1, xy, xy1), flux2_range(n, 0, 2, a2, b2), flux2_range(n, 1, 0, xy, xy1),
+                    flux2_range(n, 1, 2, a2, b2),  flux2_range(n, 2, 0, z2, w2), flux2_range(n, 2, 1, z2, w2)};
       nl += launch_flux2_ranges(a, r, p.back);
     }
-    // final fluxes (x- and y-faces on planes [f3xy, f3xy1), z-faces [f3z,
-    // f3z1)) and the update of planes [upd, upd1); after the last chunk in
-    // pieces of p.piece planes, each going back while the next computes
+    // final fluxes (x- and y-faces on the planes of PR_F3XY, z-faces of
+    // PR_F3Z) and the update; after the last chunk in pieces of p.piece
+    // planes, each going back while the next computes
     const int step = last ? std::max(p.piece, 1) : nz + 1;
-    for (int u0 = upd, a3 = f3xy, z3 = f3z; u0 < upd1 || a3 < f3xy1 || z3 < f3z1;) {
+    const int f3xy1 = c.hi[PR_F3XY], f3z1 = c.hi[PR_F3Z], upd1 = c.hi[PR_UPD];
+    for (int u0 = c.lo[PR_UPD], a3 = c.lo[PR_F3XY], z3 = c.lo[PR_F3Z]; u0 < upd1 || a3 < f3xy1 || z3 < f3z1;) {
       const int u1 = std::min(upd1, u0 + step);
       const int b3 = std::max(a3, last ? std::min(f3xy1, u1) : f3xy1);
       const int w3 = std::max(z3, last ? std::min(f3z1, u1 + 1) : f3z1);
@@ -597,7 +625,6 @@ cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStr
       }
       u0 = u1; a3 = b3; z3 = w3;
     }
-    xy = xy1; tz = tz1; f1z = f1z1; f2xz = f2xz1; f2z = f2z1; f3xy = f3xy1; f3z = f3z1; upd = upd1;
   }
   // the CFL estimate after every update; the caller's stream then waits for
   // the back stages and the last output copy

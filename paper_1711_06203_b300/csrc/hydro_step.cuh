@@ -144,6 +144,35 @@ struct HostPipe {
   cudaEvent_t h2d_done[PIPE_MAX_CHUNKS], front_done[PIPE_MAX_CHUNKS], upd_done[PIPE_MAX_CHUNKS];
 };
 cudaError_t launch_step_host_piped(const StepArgs& a, const HostPipe& p, cudaStream_t stream, long long* launches);
+
+// The plan of launch_step_host_piped: what runs after each input chunk.
+// Half-open ranges along z, of planes (x/y quantities, z tracing zones,
+// F^{x|z}, F^{y|z}, final x/y fluxes, update) or of z-faces (first,
+// intermediate and final z fluxes).  Front stages: primitive state,
+// tracing, first fluxes; back stages: intermediate and final fluxes,
+// update.
+enum PipeRange {
+  PR_H2D,   // interior planes copied in with the chunk
+  PR_PRIM,  // interior planes whose primitive state is formed
+  PR_XY,    // x/y tracing, first x/y fluxes, F^{x|y}, F^{y|x}: planes from -1
+  PR_TZ,    // z tracing: zones from -1
+  PR_F1Z,   // first z fluxes: z-faces
+  PR_F2XZ,  // F^{x|z}, F^{y|z}: planes
+  PR_F2Z,   // F^{z|x}, F^{z|y}: z-faces
+  PR_F3XY,  // final x and y fluxes: planes
+  PR_F3Z,   // final z fluxes: z-faces
+  PR_UPD,   // update: planes
+  PR_COUNT
+};
+struct PipeChunk {
+  int lo[PR_COUNT], hi[PR_COUNT];
+  int ghosts_low, ghosts_high;  // 1: the low (high) ghost planes' primitive state is formed with this chunk
+};
+// Fills out[0..nchunk) and *pre_lo (the interior planes [pre_lo, nz) are
+// copied ahead of chunk 0: the sources of a periodic low face's ghost
+// planes).  nz >= NG, 1 <= nchunk <= nz, bc_low in {0 outflow, 1 reflect,
+// 2 periodic}.  Returns false on other arguments.
+bool pipe_plan(int nz, int nchunk, int bc_low, int* pre_lo, PipeChunk* out);
 // enqueue a CFL estimate of the interior of a box into flags->dt_next
 cudaError_t launch_dt(const BoxGeom& box, const StepConst& K, const double dx[3], double cfl, DevFlags* flags,
                       cudaStream_t stream, long long* launches);
