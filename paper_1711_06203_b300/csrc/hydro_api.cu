@@ -278,9 +278,10 @@ __global__ void k_selftest_intpipe(const double* __restrict__ x, const double* _
   sum[i] = add_i(x[i], y[i]);
 }
 // z-chunks of the overlapped host-buffer step, and planes per piece of the
-// last chunk's final fluxes and update (Sedov 128^3 per call, 4.51 ms on the
-// device alone: 5.38 ms with 6 chunks, 5.30 with 8, 5.39 with 10; pieces of
-// 4 planes against one piece, 5.30 against 5.45)
+// last chunk's final fluxes and update (Sedov 128^3 initial state per call,
+// 3.59 ms on the device alone: 4.56 ms with 6 chunks, 4.49 with 8, 4.62
+// with 10, 4.81 with 12; pieces of 2, 4, 8 planes with 8 chunks: 4.51,
+// 4.49, 4.50; one piece, before the at-rest shortcuts: +0.15 ms)
 constexpr int PIPE_CHUNKS = 8, PIPE_PIECE = 4;
 
 // copy and back-stage streams and events of the overlapped host-buffer step
