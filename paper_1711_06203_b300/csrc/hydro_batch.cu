@@ -465,11 +465,63 @@ void save_tuning(const hydro_batch_state* S) {
   std::fclose(f);
 }
 
-// Time the tracing along each axis over the boxes of each untuned size class
-// (axis d, extent nd) for every candidate (the sweep with 1-4 segments per
-// pencil, the warp-row (x) / tile (y, z) kernels), keep the fastest.  Runs
-// the primitive stage first so the tracing reads real data; writes scratch
-// only.
+// time the tracing along axis ad over the boxes of sub (one warm-up pass,
+// then three), with each box's own choice of kernel along ad
+int time_tracing(const std::vector<BatchBox>& sub, int ad, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                 float* ms) {
+  std::vector<BatchBox> boxes = sub;
+  std::vector<LaunchSpec> L = {{L_TRACE, ad, 0, 0, 0, 0}, {L_TRACE_T, ad, 0, 0, 0, 0}};
+  std::vector<int> maps;
+  build_maps(boxes, L, maps);
+  Plan p;
+  p.nbox = (int)boxes.size();
+  if (cudaMalloc(&p.d_boxes, boxes.size() * sizeof(BatchBox)) != cudaSuccess ||
+      cudaMalloc(&p.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (p.d_boxes) cudaFree(p.d_boxes);
+    p.d_boxes = nullptr;
+    return HYDRO_ENOMEM;
+  }
+  cudaMemcpyAsync(p.d_boxes, boxes.data(), boxes.size() * sizeof(BatchBox), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(p.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  p.launches = L;
+  for (int rep = 0; rep < 4; ++rep) {
+    if (rep == 1) cudaEventRecord(e0, st);
+    for (auto& l : p.launches) enqueue_launch(&p, l, st);
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  *ms = 0.f;
+  cudaEventElapsedTime(ms, e0, e1);
+  cudaFree(p.d_boxes);
+  cudaFree(p.d_maps);
+  p.d_boxes = nullptr;
+  p.d_maps = nullptr;
+  return HYDRO_OK;
+}
+
+// the box with tracing kernel `parts` along axis ad (0: warp rows / tiles,
+// else the sweep with its pencils cut into that many segments)
+BatchBox with_tracing(BatchBox B, int ad, int parts) {
+  const int nd = B.in.n[ad];
+  B.tmode[ad] = parts == 0 ? 1 : 0;
+  if (parts > 0) {
+    B.tr[ad].seg = (nd + 2 + parts - 1) / parts;
+    B.tr[ad].nseg = (nd + 2 + B.tr[ad].seg - 1) / B.tr[ad].seg;
+  }
+  return B;
+}
+
+// Choose the tracing kernel per (axis d, extent nd) class of untuned boxes.
+// The sweep's segment count is timed per class (1-4 segments per pencil).
+// The choice between the sweep and the warp-row (x) / tile (y, z) kernels
+// is then made per axis, timing all of the axis's untuned boxes both ways:
+// a class alone can be a launch of one or two waves, whose tail ranks the
+// kernels differently from the step's launch, where all classes run
+// together (on the 64-box level the per-class timing kept the sweep for
+// y/z classes where the tiles are 20-30 % faster per zone-direction).
+// Runs the primitive stage first so the tracing reads real data; writes
+// scratch only.
 int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
   hydro_batch_state* S = ctx->batch;
   std::map<int, std::vector<int>> cls;  // tune_key -> boxes
@@ -486,54 +538,40 @@ int autotune(hydro_ctx* ctx, std::vector<BatchBox>& boxes, Plan* tmp, int dim) {
   // primitive state of every box (the plan's first launch)
   enqueue_launch(tmp, tmp->launches[0], st);
   int rc = HYDRO_OK;
+  std::map<int, int> sweep_parts;  // tune_key -> best segment count of the sweep
   for (auto& kv : cls) {
     const int ad = kv.first / 65536, nd = kv.first % 65536;
     float best_ms = 1e30f;
     int best = 1;
     for (int parts : SEG_PARTS) {
-      if (parts > 1 && (nd + 2 + parts - 1) / parts < 4) continue;
-      // a sub-batch of the class boxes with this candidate along axis ad
+      if (parts == 0 || (parts > 1 && (nd + 2 + parts - 1) / parts < 4)) continue;
       std::vector<BatchBox> sub;
-      for (int b : kv.second) {
-        BatchBox B = boxes[b];
-        B.tmode[ad] = parts == 0 ? 1 : 0;
-        if (parts > 0) {
-          B.tr[ad].seg = (nd + 2 + parts - 1) / parts;
-          B.tr[ad].nseg = (nd + 2 + B.tr[ad].seg - 1) / B.tr[ad].seg;
-        }
-        sub.push_back(B);
-      }
-      std::vector<LaunchSpec> L = {{L_TRACE, ad, 0, 0, 0, 0}, {L_TRACE_T, ad, 0, 0, 0, 0}};
-      std::vector<int> maps;
-      build_maps(sub, L, maps);
-      Plan p;
-      p.nbox = (int)sub.size();
-      if (cudaMalloc(&p.d_boxes, sub.size() * sizeof(BatchBox)) != cudaSuccess ||
-          cudaMalloc(&p.d_maps, maps.size() * sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        if (p.d_boxes) cudaFree(p.d_boxes);
-        rc = HYDRO_ENOMEM;
-        break;
-      }
-      cudaMemcpyAsync(p.d_boxes, sub.data(), sub.size() * sizeof(BatchBox), cudaMemcpyHostToDevice, st);
-      cudaMemcpyAsync(p.d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-      p.launches = L;
-      for (int rep = 0; rep < 4; ++rep) {
-        if (rep == 1) cudaEventRecord(e0, st);
-        for (auto& l : p.launches) enqueue_launch(&p, l, st);
-      }
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
+      for (int b : kv.second) sub.push_back(with_tracing(boxes[b], ad, parts));
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      cudaFree(p.d_boxes);
-      cudaFree(p.d_maps);
-      p.d_boxes = nullptr;
-      p.d_maps = nullptr;
+      rc = time_tracing(sub, ad, st, e0, e1, &ms);
+      if (rc) break;
       if (ms < best_ms) { best_ms = ms; best = parts; }
     }
     if (rc) break;
-    S->seg_parts[kv.first] = best;
+    sweep_parts[kv.first] = best;
+  }
+  for (int ad = 0; ad < dim && rc == HYDRO_OK; ++ad) {
+    std::vector<BatchBox> sweep, rows;
+    std::vector<int> keys;
+    for (auto& kv : cls) {
+      if (kv.first / 65536 != ad) continue;
+      keys.push_back(kv.first);
+      for (int b : kv.second) {
+        sweep.push_back(with_tracing(boxes[b], ad, sweep_parts[kv.first]));
+        rows.push_back(with_tracing(boxes[b], ad, 0));
+      }
+    }
+    if (keys.empty()) continue;
+    float ms_sweep = 0.f, ms_rows = 0.f;
+    rc = time_tracing(sweep, ad, st, e0, e1, &ms_sweep);
+    if (rc == HYDRO_OK) rc = time_tracing(rows, ad, st, e0, e1, &ms_rows);
+    if (rc) break;
+    for (int key : keys) S->seg_parts[key] = (ms_rows < ms_sweep) ? 0 : sweep_parts[key];
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
