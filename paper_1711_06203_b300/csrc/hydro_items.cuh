@@ -593,8 +593,10 @@ __device__ __forceinline__ void sub_flux_difference(double U[5], double c, const
 // transverse correction of a traced state (conserved form at T[.., id]) by
 // one or two flux differences, back to a face state.  SKIP: skip the
 // differences of equal fluxes (the final solves); the intermediate solves
-// ran 3 % slower with it (1.686 against 1.643 ms per Sedov 128^3 step),
-// their integer pipe being the busier one, so they keep the plain form.
+// ran 3 % slower with it (1.686 against 1.643 ms per Sedov 128^3 step: the
+// test gathers all ten flux values before any arithmetic, and its integer
+// work joins the third of their products already on the integer pipe), so
+// they keep the plain form.
 template <bool SKIP>
 __device__ __forceinline__ void correct(const double* __restrict__ T, long long id, const StepConst& K, double ca,
                                         const double* Fa, long long sc, long long ida_hi, long long ida_lo,
