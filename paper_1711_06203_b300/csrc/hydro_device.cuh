@@ -344,8 +344,9 @@ __device__ __forceinline__ void state_from_prim_c(const double q[5], const StepC
   for (int v = 0; v < 5; ++v) s[v] = q[v];
   s[S_E] = energy_of(q, K);
 #ifndef HYDRO_IEEE_DIV_SQRT
-  // (the three products after gamma p run on the FP64 pipe: the first-solve
-  // kernel's integer pipes are the busier ones, measured 7 % faster so)
+  // (the three products after gamma p run on the FP64 pipe: measured 7 %
+  // faster in the first solves than on the integer pipe, which there already
+  // carries the sign tests and the other moved products, 60 % busy)
   const double gp = mul_i(K.gamma, q[4]);
   const double x = gp * q[0];
   if (__builtin_expect(newton_range(x), 1)) {
