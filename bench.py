@@ -1051,6 +1051,10 @@ def run_ours(args):
         "early_window": early_window,
         "sod2d": sod,
         "moving_state": moving,
+        "at_rest_note": ("every zone is traced and every face solved each step; in zones at rest (the ambient gas "
+                         "around the blast) the kernels skip arithmetic whose terms are exactly zero (flat "
+                         "parabolas, vanishing slopes, equal fluxes), with bit-identical results; moving_state "
+                         "is the rate where no zone is at rest"),
         "roofline": {"bound": "alu", "kernel": f"{dom} stage ({LAUNCHES_PER_STEP_3D[dom]} launches/step)",
                      "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                      "frac": achieved / FP64_PEAK_GFLOPS,
