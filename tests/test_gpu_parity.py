@@ -396,6 +396,30 @@ def test_reciprocal_square_root_error_bound():
         assert _ulps(got, want).max() <= bound, (variant, _ulps(got, want).max())
 
 
+def test_host_buffer_step_exact_build_is_the_oracle():
+    """The overlapped host-buffer step in the contraction-free build against
+    the oracle directly, bit for bit: tall boxes, so that every stage runs in
+    many chunks on both compute streams, with every z boundary kind."""
+    rng = np.random.default_rng(77)
+    ctx = hb.Context(0, "exact")
+    for n, bc in (((12, 10, 64), ((O, R), (PER, PER), (O, O))),
+                  ((10, 9, 53), ((R, R), (O, O), (PER, PER))),
+                  ((9, 11, 40), ((PER, PER), (O, R), (R, O)))):
+        U = inputs.random_box(rng, n, 3)
+        dx = (0.05, 0.06, 0.04)
+        P = oracle_params(3, n, dx, bc, 5 / 3)
+        d, _ = oracle.dt(U, P)
+        ref, rc = oracle.step(U, P, d)
+        assert rc == 0
+        hin = torch.from_numpy(U.copy()).pin_memory()
+        hout = torch.full_like(hin, float("nan")).pin_memory()
+        dn = ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), hb.params(3, gamma=5 / 3), d,
+                                        want_dt_next=True)
+        assert np.array_equal(interior(hout.numpy(), 3), interior(ref, 3)), (n, bc)
+        assert dn == oracle.dt(ref, P)[0]
+    ctx.close()
+
+
 def test_host_buffer_step_matches_device_step():
     """hydro_advance_box_host on pageable and pinned host buffers gives the
     device path's result bit for bit: 3-D boxes with derived faces (interior
