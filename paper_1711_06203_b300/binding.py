@@ -547,7 +547,7 @@ class Server:
         out["state"] = self._bufs.pop(rid, None)
         return out
 
-    def serve_set_policy(self, policy, quantum_ms=10.0):
+    def serve_set_policy(self, policy, quantum_ms=5.0):
         """HYDRO_SERVE_ALL (0) or HYDRO_SERVE_RESPONSE_RATIO (1, the default) with
         its per-iteration quantum; only while the server is idle."""
         rc = self.L.serve_set_policy(self.h, int(policy), float(quantum_ms))
