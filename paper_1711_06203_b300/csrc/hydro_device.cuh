@@ -484,9 +484,15 @@ __device__ __forceinline__ bool hllc_flux_c(const double sL[NS], const double sR
     sl = dmin(ul - cl, ur - cr);
     sr = dmax(ul + cl, ur + cr);
   } else {  // Einfeldt: Roe-averaged normal velocity and sound speed
+#ifdef HYDRO_IEEE_DIV_SQRT
     double ql = dsqrt(rl), qr = dsqrt(rr);
     double iw = drcp(ql + qr);
     double wl = mul_i(ql, iw), wr = mul_i(qr, iw);
+#else
+    // the Roe weights sqrt(rl)/(sqrt(rl) + sqrt(rr)) = 1/(1 + sqrt(rr/rl))
+    // and 1 minus it: one square root and one reciprocal instead of two and one
+    const double wl = drcp(1.0 + dsqrt(mul_i(rr, sL[S_INV]))), wr = 1.0 - wl;
+#endif
     double ut0 = wl * sL[1] + mul_i(wr, sR[1]), ut1 = wl * sL[2] + mul_i(wr, sR[2]);
     double ut2 = wl * sL[3] + mul_i(wr, sR[3]);
     double hl = mul_i(sL[S_E] + pl, sL[S_INV]), hr = mul_i(sR[S_E] + pr, sR[S_INV]);
