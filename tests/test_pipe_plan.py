@@ -8,8 +8,14 @@ chunk read (the two run side by side on two streams)."""
 import pytest
 
 from paper_1711_06203_b300 import binding as hb
+from paper_1711_06203_b300 import build as hbuild
 
 NG = 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    hbuild.build()  # compiles only when a source is newer than the library
 SRC_LOW = {0: lambda nz, m: [0], 1: lambda nz, m: [m - 1], 2: lambda nz, m: [nz - m]}
 
 
