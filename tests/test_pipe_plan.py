@@ -16,6 +16,8 @@ NG = 4
 @pytest.fixture(scope="module", autouse=True)
 def built():
     hbuild.build()  # compiles only when a source is newer than the library
+
+
 SRC_LOW = {0: lambda nz, m: [0], 1: lambda nz, m: [m - 1], 2: lambda nz, m: [nz - m]}
 
 
