@@ -132,6 +132,23 @@ def test_poll_and_budget_semantics():
     srv.close()
 
 
+def test_poll_with_a_bounded_wait_times_out():
+    """A poll whose wait runs out returns HYDRO_ETIMEDOUT after about that
+    wait, leaves the request alive, and a later poll collects it."""
+    import ctypes
+    srv = hb.Server(0)
+    rid = srv.serve_submit(kind=hb.PROB_SEDOV, n=128, steps=100)  # a few hundred ms of GPU work
+    res = hb.hydro_result_t()
+    t0 = time.perf_counter()
+    rc = srv.L.serve_poll(srv.h, ctypes.c_uint64(rid), ctypes.byref(res), 20)
+    waited = time.perf_counter() - t0
+    assert rc == hb.HYDRO_ETIMEDOUT
+    assert 0.015 <= waited < 2.0, waited
+    r = srv.serve_poll(rid, timeout_ms=120000)
+    assert r["status"] == hb.HYDRO_OK and r["steps_done"] == 100
+    srv.close()
+
+
 def test_slot_limit_queues_requests():
     srv = hb.Server(0, max_slots=1)
     ids = [srv.serve_submit(kind=hb.PROB_SOD, n=16, steps=4) for _ in range(3)]
