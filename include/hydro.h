@@ -463,6 +463,16 @@ long long hydro_ctx_launches(const hydro_ctx_t* ctx);
  * meet.  0: never slab.  Default 16 GiB.  Takes effect at the next step. */
 int hydro_ctx_set_scratch_limit(hydro_ctx_t* ctx, size_t bytes);
 
+/* Diagnostics (no counterpart in the paper): fault injection on the host.
+ * While enabled, the context's large device allocations -- the step scratch,
+ * the host-buffer step's staging boxes, the batched level's scratch pool and
+ * the two-level temporaries -- fail as if the device were out of memory, so
+ * callers can test their HYDRO_ENOMEM handling: a call that needs one of
+ * them returns HYDRO_ENOMEM and enqueues no step.  Memory the context
+ * already holds is still used.
+ * Disabling restores normal allocation; the context stays usable. */
+int hydro_ctx_fail_allocations(hydro_ctx_t* ctx, int enable);
+
 /* ---- boundary fluxes of a box step (paper Sec. 3: a level's coarse-fine
  * synchronisation corrects coarse zones with the fluxes of the fine level, so
  * the fluxes through a box's outer faces are part of what a step produces;

@@ -156,6 +156,7 @@ def lib(variant="default"):
     L.hydro_ctx_launches.restype = ctypes.c_longlong
     L.hydro_ctx_record_face_fluxes.argtypes = [vp, ctypes.c_int]
     L.hydro_ctx_set_scratch_limit.argtypes = [vp, ctypes.c_size_t]
+    L.hydro_ctx_fail_allocations.argtypes = [vp, ctypes.c_int]
     L.hydro_selftest_fp64_rate.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.hydro_selftest_rsqrt.argtypes = [vp, vp, ctypes.c_longlong, vp]
     L.hydro_advance_box_steps.argtypes = [vp, ctypes.POINTER(hydro_box_t), ctypes.POINTER(hydro_box_t),
@@ -490,6 +491,12 @@ class Context:
         rc = self.L.hydro_ctx_set_scratch_limit(self.h, int(nbytes))
         if rc:
             raise HydroError(rc, "hydro_ctx_set_scratch_limit")
+
+    def hydro_ctx_fail_allocations(self, enable=True):
+        """Fault injection: make the context's large device allocations fail (HYDRO_ENOMEM)."""
+        rc = self.L.hydro_ctx_fail_allocations(self.h, 1 if enable else 0)
+        if rc:
+            raise HydroError(rc, "hydro_ctx_fail_allocations")
 
     def hydro_ctx_record_face_fluxes(self, enable=True):
         rc = self.L.hydro_ctx_record_face_fluxes(self.h, 1 if enable else 0)

@@ -632,6 +632,12 @@ int hydro_ctx_set_scratch_limit(hydro_ctx_t* ctx, size_t bytes) {
   return HYDRO_OK;
 }
 
+int hydro_ctx_fail_allocations(hydro_ctx_t* ctx, int enable) {
+  if (!ctx) return HYDRO_EINVAL;
+  ctx->fail_alloc = enable ? 1 : 0;
+  return HYDRO_OK;
+}
+
 int hydro_ctx_record_face_fluxes(hydro_ctx_t* ctx, int enable) {
   if (!ctx) return HYDRO_EINVAL;
   ctx->record_faces = enable ? 1 : 0;

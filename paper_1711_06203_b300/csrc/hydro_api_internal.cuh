@@ -14,7 +14,7 @@ struct hydro_ctx {
   double* scratch = nullptr;      // staged-step intermediates (grown on demand)
   size_t scratch_bytes = 0;
   hydro::DevFlags* flags = nullptr;
-  int fail_alloc = 0;             // test hook: make the next scratch allocation fail
+  int fail_alloc = 0;             // hydro_ctx_fail_allocations: every scratch allocation fails while set
   hydro_batch_state* batch = nullptr;
   hydro_level_state* level = nullptr;
   hydro_amr_state* amr = nullptr;

@@ -239,6 +239,43 @@ def test_bad_state_is_reported():
     ctx.close()
 
 
+def test_injected_allocation_failure_is_reported_and_recoverable():
+    """Fault injection on the host: with the context's allocations made to
+    fail, a step that needs scratch (single box, host buffers, a batched
+    level) returns HYDRO_ENOMEM and writes nothing; with allocation restored
+    the same context steps, bitwise as a fresh one."""
+    rng = np.random.default_rng(5)
+    n, dx, bc = (20, 18, 16), (0.05,) * 3, ((O, O), (R, R), (PER, PER))
+    U = inputs.random_box(rng, n, 3)
+    p = hb.params(3, gamma=5 / 3)
+    d, _ = oracle.dt(U, oracle_params(3, n, dx, bc, 5 / 3))
+    ctx = hb.Context(0)
+    ctx.hydro_ctx_fail_allocations(True)
+    a = to_dev(U)
+    b = torch.full_like(a, float("nan"))
+    rc, _ = ctx.hydro_advance_box(hb.box(a, n, dx, bc), hb.box(b, n, dx, bc), p, d, want_dt_next=True,
+                                  raise_on_error=False)
+    assert rc == hb.HYDRO_ENOMEM
+    torch.cuda.synchronize()
+    assert torch.isnan(b).all()
+    hin = torch.from_numpy(U.copy()).pin_memory()
+    hout = torch.full_like(hin, float("nan")).pin_memory()
+    with pytest.raises(hb.HydroError) as e:
+        ctx.hydro_advance_box_host(hb.box(hin, n, dx, bc), hb.box(hout, n, dx, bc), p, d)
+    assert e.value.status == hb.HYDRO_ENOMEM
+    assert torch.isnan(hout).all()
+    dt_dev = torch.full((1,), d, dtype=torch.float64, device="cuda")
+    with pytest.raises(hb.HydroError) as e:
+        ctx.hydro_advance_batch([hb.box(a, n, dx, PRE)], [hb.box(b, n, dx, PRE)], p, dt_dev)
+    assert e.value.status == hb.HYDRO_ENOMEM
+    ctx.hydro_ctx_fail_allocations(False)
+    got = ctx.hydro_advance_box(hb.box(a, n, dx, bc), hb.box(b, n, dx, bc), p, d, want_dt_next=True)
+    ctx.close()
+    ref, ref_dt = gpu_steps(U, 3, n, dx, bc, 5 / 3, [d])
+    assert np.array_equal(interior(b.cpu().numpy(), 3), interior(ref, 3))
+    assert got == ref_dt[0]
+
+
 def test_invalid_arguments_are_rejected():
     ctx = hb.Context(0)
     U = inputs.random_box(np.random.default_rng(0), (8, 8, 8), 3)
