@@ -57,7 +57,8 @@ typedef enum {
   HYDRO_EAGAIN = -5,     /* result not ready yet (serve_poll) */
   HYDRO_ETIMEDOUT = -6,  /* a bounded wait ran out */
   HYDRO_ENOTIMPL = -7,   /* not supported by this build */
-  HYDRO_ETOOBIG = -8     /* box larger than the fixed storage of hydro_advance_box_noalloc */
+  HYDRO_ETOOBIG = -8,    /* box larger than the fixed storage of hydro_advance_box_noalloc */
+  HYDRO_ECANCELED = -9   /* a served request was cancelled (serve_cancel) */
 } hydro_status;
 
 /* boundary kind of one face of a box */
@@ -386,6 +387,13 @@ int serve_submit(serve_t* s, const hydro_request_t* req, uint64_t* id);
  * HYDRO_OK: *res filled and the handle released; HYDRO_EAGAIN (timeout 0) or
  * HYDRO_ETIMEDOUT: not finished yet; HYDRO_EINVAL: unknown handle. */
 int serve_poll(serve_t* s, uint64_t id, hydro_result_t* res, int timeout_ms);
+/* Cancel request `id`.  A request still queued leaves the queue at once; an
+ * admitted one is retired before the scheduler's next iteration (its memory
+ * freed, the steps done so far reported); either way its result, collected
+ * by serve_poll as usual, carries status HYDRO_ECANCELED and no state is
+ * copied to result_host.  A request that has already finished keeps its
+ * result.  HYDRO_EINVAL: unknown (or already collected) handle. */
+int serve_cancel(serve_t* s, uint64_t id);
 /* Snapshot of the server's counters. */
 int serve_stats(serve_t* s, hydro_serve_stats_t* st);
 /* Choose the scheduling policy while the server is idle (nothing queued or

@@ -15,6 +15,7 @@ LIBDIR = os.path.join(HERE, "_build")
 HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA = 0, -1, -2, -3
 HYDRO_EBADSTATE, HYDRO_EAGAIN, HYDRO_ETIMEDOUT, HYDRO_ENOTIMPL = -4, -5, -6, -7
 HYDRO_ETOOBIG = -8
+HYDRO_ECANCELED = -9
 NOALLOC_MAX_ZONES = 64000
 BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_PREFILLED = 0, 1, 2, 3
 MOL_MAX_SPECIES = 32  # HYDRO_MOL_MAX_SPECIES
@@ -148,6 +149,7 @@ def lib(variant="default"):
     L.serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hydro_result_t), ctypes.c_int]
     L.serve_stats.argtypes = [vp, ctypes.POINTER(hydro_serve_stats_t)]
     L.serve_set_policy.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    L.serve_cancel.argtypes = [vp, ctypes.c_uint64]
     L.serve_destroy.argtypes = [vp]
     L.serve_destroy.restype = None
     L.hydro_ctx_set_profiling.argtypes = [vp, ctypes.c_int]
@@ -553,6 +555,13 @@ class Server:
         out = {k: getattr(res, k) for k, _ in hydro_result_t._fields_}
         out["state"] = self._bufs.pop(rid, None)
         return out
+
+    def serve_cancel(self, rid):
+        """Cancel a request: its result (collected by serve_poll) carries HYDRO_ECANCELED
+        unless it had already finished."""
+        rc = self.L.serve_cancel(self.h, ctypes.c_uint64(rid))
+        if rc:
+            raise HydroError(rc, "serve_cancel")
 
     def serve_set_policy(self, policy, quantum_ms=5.0):
         """HYDRO_SERVE_ALL (0) or HYDRO_SERVE_RESPONSE_RATIO (1, the default) with

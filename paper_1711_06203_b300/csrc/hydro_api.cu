@@ -322,6 +322,7 @@ const char* hydro_strerror(int s) {
     case HYDRO_ETIMEDOUT: return "timed out";
     case HYDRO_ENOTIMPL: return "not implemented";
     case HYDRO_ETOOBIG: return "box exceeds the fixed storage of the allocation-free step (HYDRO_NOALLOC_MAX_ZONES)";
+    case HYDRO_ECANCELED: return "cancelled";
     default: return "unknown status";
   }
 }

@@ -87,6 +87,7 @@ struct Req {
   Clock::time_point submitted, admitted;
   hydro_result_t result{};
   bool done = false;
+  bool cancel = false;  // serve_cancel on an admitted request: retire at the next iteration
 };
 
 size_t grown_zones(int n) { return (size_t)(n + 2 * NG) * (n + 2 * NG) * (n + 2 * NG); }
@@ -273,6 +274,15 @@ void serve::run() {
       std::lock_guard<std::mutex> lock(mu);
       active.push_back(r);
     }
+    // requests cancelled since the last iteration leave before it
+    std::vector<Req*> cancelled;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      std::vector<Req*> still;
+      for (Req* r : active) (r->cancel ? cancelled : still).push_back(r);
+      active.swap(still);
+    }
+    for (Req* r : cancelled) retire(r, HYDRO_ECANCELED);
     if (active.empty()) continue;
 
     // the set that steps this iteration
@@ -441,6 +451,32 @@ int serve_submit(serve_t* s, const hydro_request_t* req, uint64_t* id) {
   s->reqs[r->id] = r;
   s->pending.push_back(r);
   *id = r->id;
+  s->cv_work.notify_all();
+  return HYDRO_OK;
+}
+
+int serve_cancel(serve_t* s, uint64_t id) {
+  if (!s) return HYDRO_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return HYDRO_EINVAL;
+  Req* r = it->second;
+  if (r->done) return HYDRO_OK;  // finished first: the result stands
+  auto q = std::find(s->pending.begin(), s->pending.end(), r);
+  if (q != s->pending.end()) {  // never admitted: it leaves the queue now
+    s->pending.erase(q);
+    const auto now = Clock::now();
+    r->result.status = HYDRO_ECANCELED;
+    r->result.steps_done = 0;
+    r->result.t_final = 0.0;
+    r->result.latency_ms = ms_between(r->submitted, now);
+    r->result.queue_ms = r->result.latency_ms;
+    r->result.zone_updates = 0;
+    r->done = true;
+    s->cv_done.notify_all();
+    return HYDRO_OK;
+  }
+  r->cancel = true;  // admitted: the scheduler retires it before its next iteration
   s->cv_work.notify_all();
   return HYDRO_OK;
 }

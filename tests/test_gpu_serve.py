@@ -149,6 +149,42 @@ def test_poll_with_a_bounded_wait_times_out():
     srv.close()
 
 
+def _wait_for(cond, limit_s=60.0):
+    t0 = time.perf_counter()
+    while not cond():
+        assert time.perf_counter() - t0 < limit_s
+        time.sleep(0.005)
+
+
+def test_cancel_queued_running_and_finished_requests():
+    """A queued request leaves the queue at once; a running one is retired
+    before the scheduler's next iteration with the steps it has done; one
+    that finished first keeps its result; the server serves on."""
+    srv = hb.Server(0, max_slots=1)
+    long_id = srv.serve_submit(kind=hb.PROB_SEDOV, n=128, steps=400)  # about 1.5 s of steps alone
+    queued = srv.serve_submit(kind=hb.PROB_SOD, n=32, steps=10)  # waits for the only slot
+    srv.serve_cancel(queued)
+    r = srv.serve_poll(queued, timeout_ms=60000)
+    assert r["status"] == hb.HYDRO_ECANCELED and r["steps_done"] == 0
+    _wait_for(lambda: srv.serve_stats()["zone_updates"] > 0)  # the long request is stepping
+    srv.serve_cancel(long_id)
+    r = srv.serve_poll(long_id, timeout_ms=60000)
+    assert r["status"] == hb.HYDRO_ECANCELED and 0 < r["steps_done"] < 400
+    rid = srv.serve_submit(kind=hb.PROB_SOD, n=32, steps=10)
+    r = srv.serve_poll(rid, timeout_ms=60000)
+    assert r["status"] == hb.HYDRO_OK and r["steps_done"] == 10
+    rid = srv.serve_submit(kind=hb.PROB_SOD, n=32, steps=5)
+    done = srv.serve_stats()["completed"] + 1
+    _wait_for(lambda: srv.serve_stats()["completed"] >= done)
+    srv.serve_cancel(rid)  # finished first: the result stands
+    r = srv.serve_poll(rid, timeout_ms=0)
+    assert r["status"] == hb.HYDRO_OK and r["steps_done"] == 5
+    with pytest.raises(hb.HydroError) as e:
+        srv.serve_cancel(rid)  # collected: unknown handle
+    assert e.value.status == hb.HYDRO_EINVAL
+    srv.close()
+
+
 def test_slot_limit_queues_requests():
     srv = hb.Server(0, max_slots=1)
     ids = [srv.serve_submit(kind=hb.PROB_SOD, n=16, steps=4) for _ in range(3)]
