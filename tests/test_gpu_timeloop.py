@@ -85,6 +85,23 @@ def test_time_loop_equals_stepping_one_call_at_a_time():
     assert t == t_ref
 
 
+def test_checkpoint_and_resume_through_host_memory():
+    """Checkpoint/resume: the state is the caller's box plus the time step, so
+    twenty steps of the device loop equal ten steps, a copy of the state and
+    the next dt to host memory and back into fresh buffers (a new context),
+    and ten more -- bit for bit."""
+    rng = np.random.default_rng(8)
+    n, dx, bc = (18, 14, 12), (0.05, 0.06, 0.07), ((O, R), (PER, PER), (R, O))
+    U = inputs.random_box(rng, n, 3)
+    p = hb.params(3, gamma=5 / 3, grav=(0.0, 0.0, -0.4))
+    whole, t_whole, _ = _loop("default", U, n, dx, bc, p, 20)
+    half, t_half, dt_next = _loop("default", U, n, dx, bc, p, 10)
+    saved = np.array(half, copy=True)  # the checkpoint: the state and the next dt, in host memory
+    rest, t_rest, _ = _loop("default", saved, n, dx, bc, p, 10, dt0=dt_next)
+    assert np.array_equal(interior(rest, 3), interior(whole, 3))
+    assert t_half + t_rest == pytest.approx(t_whole, rel=1e-15)
+
+
 def test_time_loop_refuses_prefilled_faces():
     n = (8, 8, 8)
     U = inputs.random_box(np.random.default_rng(0), n, 3)
