@@ -57,3 +57,22 @@ def rel_linf(a, b):
     den = np.abs(b).max(axis=1)
     num = np.abs(a - b).max(axis=1)
     return np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
+
+
+def blocky_state(rng, n, dim, gamma):
+    """Piecewise-constant blocks of 3 zones: a few shared states (so neighbouring
+    blocks are often equal bit for bit, and zones sit at rest), velocities
+    drawn from +0, -0 and +-0.3, densities and pressures lognormal."""
+    shape = inputs.grown_shape(tuple(n) + (1,) * (3 - len(n)), dim)
+    pal = []
+    for _ in range(4):
+        vel = [rng.choice([0.0, -0.0, 0.3, -0.3]) for _ in range(3)]
+        pal.append((rng.lognormal(0, 0.6), *vel, rng.lognormal(0, 0.6)))
+    blocks = [(s + 2) // 3 for s in shape]
+    pick = rng.integers(0, len(pal), size=blocks)
+    idx = np.indices(shape)
+    ids = pick[tuple(i // 3 for i in idx)]
+    q = np.array(pal)[ids]  # (..., 5): rho, u, v, w, p
+    if dim == 2:
+        q[..., 3] = 0.0
+    return inputs.conserved(q[..., 0], q[..., 1], q[..., 2], q[..., 3], q[..., 4], gamma)

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import rel_linf
+from gpu_helpers import blocky_state, rel_linf
 from paper_1711_06203_b300 import binding as hb
 from paper_1711_06203_b300 import inputs
 
@@ -108,11 +108,14 @@ def test_exact_batch_is_bitwise_equal_to_oracle():
 
 
 @pytest.mark.parametrize("mode", ["tiles", "sweeps", "mixed"])
-def test_exact_batch_with_each_tracing_kernel(mode, tmp_path, monkeypatch):
+@pytest.mark.parametrize("data", ["random", "blocky"])
+def test_exact_batch_with_each_tracing_kernel(mode, data, tmp_path, monkeypatch):
     """The tracing kernel chosen per axis and extent (the sweep with a given
     segment length, or the warp-row / tile kernels), forced through the
     tuning cache file: every choice gives the oracle's result bit for bit,
-    in 3-D and 2-D."""
+    in 3-D and 2-D, on random states and on piecewise-constant ones (zones
+    at rest, equal neighbours, signed zero velocities: the kernels'
+    exact-zero paths)."""
     sizes3 = SIZES3
     sizes2 = [(40, 24, 1), (16, 64, 1), (32, 32, 1)]
     classes = sorted({(a, s[a]) for s in sizes3 for a in range(3)} | {(a, s[a]) for s in sizes2 for a in range(2)})
@@ -122,7 +125,11 @@ def test_exact_batch_with_each_tracing_kernel(mode, tmp_path, monkeypatch):
     cache.write_text("".join(f"{a} {e} {pick(a, e)}\n" for a, e in classes))
     monkeypatch.setenv("HYDRO_TUNE_CACHE", str(cache))
     for dim, sizes in ((3, sizes3), (2, sizes2)):
-        Us = _level(21 + dim, sizes, dim)
+        if data == "random":
+            Us = _level(21 + dim, sizes, dim)
+        else:
+            rng = np.random.default_rng(31 + dim)
+            Us = [blocky_state(rng, s[:dim], dim, 5 / 3) for s in sizes]
         dts = [1e-3 * (1 + 0.1 * k) for k in range(len(sizes))]
         ctx = hb.Context(0, "exact")
         got, _ = _run_batch(ctx, Us, sizes, dim, dts, hb.params(dim, gamma=5 / 3))

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import gpu_steps, interior, oracle_params, rel_linf, to_dev
+from gpu_helpers import blocky_state, gpu_steps, interior, oracle_params, rel_linf, to_dev
 from paper_1711_06203_b300 import binding as hb
 from paper_1711_06203_b300 import inputs
 
@@ -91,25 +91,6 @@ def test_one_step_parity(name):
     assert abs(nxt[0] - dref) <= 1e-10 * dref
 
 
-def _blocky_state(rng, n, dim, gamma):
-    """Piecewise-constant blocks of 3 zones: a few shared states (so neighbouring
-    blocks are often equal bit for bit, and zones sit at rest), velocities
-    drawn from +0, -0 and +-0.3, densities and pressures lognormal."""
-    shape = inputs.grown_shape(tuple(n) + (1,) * (3 - len(n)), dim)
-    pal = []
-    for _ in range(4):
-        vel = [rng.choice([0.0, -0.0, 0.3, -0.3]) for _ in range(3)]
-        pal.append((rng.lognormal(0, 0.6), *vel, rng.lognormal(0, 0.6)))
-    blocks = [(s + 2) // 3 for s in shape]
-    pick = rng.integers(0, len(pal), size=blocks)
-    idx = np.indices(shape)
-    ids = pick[tuple(i // 3 for i in idx)]
-    q = np.array(pal)[ids]  # (..., 5): rho, u, v, w, p
-    if dim == 2:
-        q[..., 3] = 0.0
-    return inputs.conserved(q[..., 0], q[..., 1], q[..., 2], q[..., 3], q[..., 4], gamma)
-
-
 @pytest.mark.parametrize("seed", range(8))
 def test_exact_build_bitwise_on_blocky_states(seed):
     """Adversarial inputs for the kernels' exact-zero paths (flat parabolas,
@@ -127,7 +108,7 @@ def test_exact_build_bitwise_on_blocky_states(seed):
     grav = (0.0, 0.0, 0.0) if seed % 2 else (0.2, -0.3, 0.1 if dim == 3 else 0.0)
     gamma = 1.4
     dx = (1 / 13, 1 / 11, 1 / 9)
-    U = _blocky_state(rng, n, dim, gamma)
+    U = blocky_state(rng, n, dim, gamma)
     P = oracle_params(dim, n, dx, bc, gamma, grav=grav)
     ref, got = U, U
     ctx = hb.Context(0, "exact")
