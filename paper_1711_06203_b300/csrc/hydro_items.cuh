@@ -9,6 +9,13 @@ namespace hydro {
 namespace {
 
 constexpr int BLOCK = 128;
+// Resident blocks per SM of the single-box solver kernels (launch bound):
+// with the Davis speeds the first, intermediate and final solves fit 56
+// registers and run at nine blocks per SM (1.0 % faster per Sedov 128^3
+// step than at eight with 64 registers; 66-70 registers at seven were 1-3 %
+// slower); the Einfeldt speeds keep eight.  (The batched level's solver
+// kernels measured the same at nine, with small spills, and keep theirs.)
+__host__ __device__ constexpr int solver_blocks(bool einf) { return einf ? 8 : 9; }
 
 __device__ __forceinline__ bool range_zone(const Range& R, long long t, int& i, int& j, int& k) {
   long long e0 = R.ext[0], e1 = R.ext[1];

@@ -45,10 +45,9 @@ __device__ __forceinline__ int dir_of(unsigned f1, unsigned f2, long long& t) {
   t = (long long)(b - f) * BLOCK + threadIdx.x;
   return d;
 }
-// (first and intermediate solves held to 64 registers, eight blocks per SM:
-// 66-70 registers at seven measured 1-3 % slower)
+// (resident blocks per SM: solver_blocks)
 template <bool EINF>
-__global__ void __launch_bounds__(BLOCK, 8) k_flux1(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
+__global__ void __launch_bounds__(BLOCK, solver_blocks(EINF)) k_flux1(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
   long long t;
   switch (dir_of(S.first[1], S.first[2], t)) {
     case 0: flux1_item<0, EINF>(sg, s.TP[0], s.TM[0], s.F1[0], K, S.r[0], t); break;
@@ -66,7 +65,7 @@ struct Flux2Sets {
   unsigned first[7];
 };
 template <bool EINF>
-__global__ void __launch_bounds__(BLOCK, 8) k_flux2(ScratchGeom sg, Scratch s, StepConst K, Flux2Sets S) {
+__global__ void __launch_bounds__(BLOCK, solver_blocks(EINF)) k_flux2(ScratchGeom sg, Scratch s, StepConst K, Flux2Sets S) {
   const unsigned b = blockIdx.x;
   int c = 0;
   unsigned f = 0;
@@ -86,10 +85,10 @@ __global__ void __launch_bounds__(BLOCK, 8) k_flux2(ScratchGeom sg, Scratch s, S
 
 // final fluxes: in 3-D from the intermediate fluxes of the two other
 // directions, in 2-D from the first fluxes of the other direction
-// (held to 64 registers: the three-operand form otherwise takes 94 and halves
-// the resident warps)
+// (held to the solver bound: the three-operand form otherwise takes 94
+// registers and halves the resident warps)
 template <bool THREE, bool EINF>
-__global__ void __launch_bounds__(BLOCK, 65536 / (64 * BLOCK))
+__global__ void __launch_bounds__(BLOCK, solver_blocks(EINF))
     k_flux3(ScratchGeom sg, Scratch s, StepConst K, DirSets S) {
   long long t;
   switch (dir_of(S.first[1], S.first[2], t)) {
