@@ -73,8 +73,10 @@ __global__ void __launch_bounds__(BLOCK) kb_prim(BatchBox* boxes, const int* __r
   prim_item(B.in, B.sg, B.s.Q, B.K, B.rp, &B.flags, item_of(box_first, b));
 }
 
+// (three blocks per SM: 168 registers and a few bytes of spills, against
+// 195 registers at two; the 512-box level's step 76.6 -> 75.6 ms)
 template <int D>
-__global__ void __launch_bounds__(BLOCK) kb_trace(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
+__global__ void __launch_bounds__(BLOCK, 3) kb_trace(const BatchBox* __restrict__ boxes, const int* __restrict__ blk_box,
                                                   const int* __restrict__ box_first, int nbox) {
   const int b = box_of_block(blk_box, box_first, nbox);
   const BatchBox& B = boxes[b];
