@@ -276,6 +276,7 @@ def bench_moving(args, dev, stream, n=128, steps=20):
     dt = 0.5 * ctx.hydro_dt(box(a), p, stream)
     for _ in range(3):
         ctx.hydro_advance_box(box(a), box(b), p, dt, stream=stream)
+    ctx.hydro_ctx_set_profiling(True)  # per-stage events, as in the Sedov run
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
@@ -285,10 +286,12 @@ def bench_moving(args, dev, stream, n=128, steps=20):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    stage_ms, calls = ctx.hydro_ctx_stage_times()
     physical = ctx.hydro_ctx_check() == hb.HYDRO_OK  # no zone met a non-physical state
     ctx.close()
     return {"workload": f"random-state {n}^3 periodic box (every zone moving), fixed dt", "steps": steps,
             "ms_per_step": ms, "zone_updates_per_s": n ** 3 / (ms * 1e-3), "physical": physical,
+            "stages_ms_per_step": {k: v / calls for k, v in stage_ms.items()} if calls else None,
             "note": "no zone at rest: the tracing and final-solve shortcuts for gas at rest never apply"}
 
 
@@ -1123,6 +1126,8 @@ def main():
                     help="run only the method-of-lines leg at --n and print its JSON (for profiling)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched-level leg and print its JSON (for profiling)")
+    ap.add_argument("--moving-only", action="store_true",
+                    help="run only the every-zone-moving 128^3 leg and print its JSON (for profiling)")
     ap.add_argument("--batch-profile", type=int, default=0, metavar="NBOX",
                     help="only batched steps of the first NBOX boxes of the level, no per-box comparison "
                          "(a small case for ncu)")
@@ -1140,13 +1145,18 @@ def main():
         with torch.cuda.device(dev):
             print(json.dumps(bench_serve(args, dev, args.serve_plain_rate)), flush=True)
         return 0
-    if args.mol_only or args.batch_only:
+    if args.mol_only or args.batch_only or args.moving_only:
         import torch
 
         dev = torch.device("cuda", 0)
         with torch.cuda.device(dev):
             stream = torch.cuda.current_stream(dev)
-            leg = bench_mol(args, dev, stream, cpu_sample=False) if args.mol_only else bench_batch(args, dev, stream)
+            if args.mol_only:
+                leg = bench_mol(args, dev, stream, cpu_sample=False)
+            elif args.batch_only:
+                leg = bench_batch(args, dev, stream)
+            else:
+                leg = bench_moving(args, dev, stream)
             print(json.dumps(leg), flush=True)
         return 0
     return run_ours(args)
