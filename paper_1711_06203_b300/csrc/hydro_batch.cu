@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kb_trace(const BatchBox* __restrict_
   trace_item<D>(B.sg, B.s.Q, B.s.TM[D], B.s.TP[D], B.K, B.tr[D], item_of(box_first, b));
 }
 
-// the x tracing by warp rows (one warp per ROW_ZONES zones of a pencil)
+// the x tracing by warp rows (one warp per ROW_ZONES positions of the pencils laid end to end)
 __global__ void __launch_bounds__(BLOCK) kb_trace_row_x(const BatchBox* __restrict__ boxes,
                                                         const int* __restrict__ blk_box,
                                                         const int* __restrict__ box_first, int nbox) {
@@ -291,7 +291,7 @@ void fill_ranges(BatchBox& B, int dim, hydro_batch_state* S) {
 long long tile_items(const BatchBox& B, int d) {
   const SweepRange& R = B.tr[d];
   if (d == 0) {
-    const long long warps = (long long)((R.nd - R.lod + ROW_ZONES) / ROW_ZONES) * R.ext1 * R.ext2;
+    const long long warps = row_warps(R);
     return (warps + BLOCK / 32 - 1) / (BLOCK / 32) * BLOCK;
   }
   const long long ngroup = ((long long)R.ext1 * R.ext2 + 31) / 32;

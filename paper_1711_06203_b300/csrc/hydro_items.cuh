@@ -328,16 +328,29 @@ __device__ __forceinline__ void trace_item(ScratchGeom sg, const double* __restr
   }
 }
 
-// ---- stages 2-3 along x with the lanes of a warp along the pencil.  A warp
-// takes ROW_ZONES consecutive zones [t0, t0 + ROW_ZONES) of one x-pencil
-// (t0 = lod + ROW_ZONES * tile); lane l holds zone t0 - 1 + l, so lanes 0 and
-// 31 only supply the slope, the flattening coefficient and the interface value
-// their neighbours need.  Every quantity of a zone is the tracing sweep's, by
-// the same expressions: the slope and the flattening coefficient of each zone
-// once, the interface value at its high face once, the neighbours' values
-// through shuffles.  The loads of a warp are consecutive doubles (the
-// sequential sweep along x reads with lanes along y, a cache line per lane).
+// ---- stages 2-3 along x with the lanes of a warp along the pencils.  The
+// pencils' zones lie end to end in one sequence of positions, each pencil
+// holding its zones [lod - 1, nd + 1]: the traced zones and one zone beyond
+// each end.  Warp w takes positions [ROW_ZONES w - 1, ROW_ZONES w + 31); lane l
+// holds position ROW_ZONES w - 1 + l and traces it when l is in
+// [1, ROW_ZONES] and the position is a traced zone, so lanes 0 and 31 and the
+// zones beyond a pencil's ends only supply the slope, the flattening
+// coefficient and the interface value their neighbours need.  A warp may
+// cover the end of one pencil and the start of the next: the two positions
+// between them are those beyond-the-end zones, so every traced zone's
+// neighbours are of its own pencil.  Every quantity of a zone is the
+// tracing sweep's, by the same expressions: the slope and the flattening
+// coefficient of each zone once, the interface value at its high face once,
+// the neighbours' values through shuffles.  The loads of a warp are
+// consecutive doubles (the sequential sweep along x reads with lanes along
+// y, a cache line per lane).
 constexpr int ROW_ZONES = 30;
+// positions of one pencil, and warps for a range
+__host__ __device__ __forceinline__ int row_positions(const SweepRange& R) { return R.nd - R.lod + 3; }
+__host__ __device__ __forceinline__ long long row_warps(const SweepRange& R) {
+  const long long npos = (long long)row_positions(R) * R.ext1 * R.ext2;
+  return (npos + ROW_ZONES - 1) / ROW_ZONES;
+}
 
 // Zones at rest.  When, in every variable, a zone's average equals its
 // neighbours' (bit for bit), its one-sided differences are +0, so every
@@ -387,19 +400,22 @@ __device__ __forceinline__ double shfl_dn1(double x) { return __shfl_down_sync(0
 __device__ __forceinline__ void trace_row_x_item(ScratchGeom sg, const double* __restrict__ Q,
                                                  double* __restrict__ TM, double* __restrict__ TP, StepConst K,
                                                  SweepRange R, long long w) {
-  const int ntile = (R.nd - R.lod + ROW_ZONES) / ROW_ZONES;  // zones [lod, nd]
-  const long long r = w / ntile;
-  if (r >= (long long)R.ext1 * R.ext2) return;  // uniform over the warp
+  const int L = row_positions(R);
+  const long long npos = (long long)L * R.ext1 * R.ext2;
+  const long long p0 = w * ROW_ZONES - 1;  // the warp's first position
+  if (p0 >= npos) return;  // uniform over the warp
   const int lane = threadIdx.x & 31;
-  const int tile = (int)(w - r * ntile);
+  const long long pos = p0 + lane;
+  // positions in the range hold zones lod - 1 .. nd + 1 of their pencil,
+  // whose stencils stay in the grown box; the others load nothing
+  const bool live = pos >= 0 && pos < npos;
+  const long long r = live ? pos / L : 0;
+  const int q = live ? (int)(pos - r * L) : 0;
   const int j = R.lo1 + (int)(r % R.ext1), k = R.lo2 + (int)(r / R.ext1);
-  const int t0 = R.lod + tile * ROW_ZONES;
-  const int i = t0 - 1 + lane;
+  const int i = R.lod - 1 + q;
   const long long sc = sg.sc;
   const long long id = sg.id(i, j, k);
   const double* __restrict__ qv[5] = {Q + QRHO * sc, Q + QU * sc, Q + QV * sc, Q + QW * sc, Q + QP * sc};
-  // zones up to nd + 1 supply slopes and flattening; their stencil stays in the grown box
-  const bool live = i <= R.nd + 1;
   double am1[5], a0[5], ap1[5], pm2 = 0.0, pp2 = 0.0;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -423,7 +439,7 @@ __device__ __forceinline__ void trace_row_x_item(ScratchGeom sg, const double* _
 #pragma unroll
   for (int v = 0; v < 5; ++v) fm[v] = shfl_up1(fp[v]);
   const double ctm = shfl_up1(ct0), ctp = shfl_dn1(ct0);
-  if (lane == 0 || lane > ROW_ZONES || i > R.nd) return;
+  if (lane == 0 || lane > ROW_ZONES || !live || q < 1 || q > L - 2) return;
   double chi = 1.0;
   if (K.flatten) chi = dless(ap1[4], am1[4]) ? dmin(ct0, ctp) : dmin(ct0, ctm);
   double am[5], ap[5], dap[5], a6[5];

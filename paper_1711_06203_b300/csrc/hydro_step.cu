@@ -139,11 +139,10 @@ void launch_trace_tile(const ScratchGeom& sg, const Scratch& s, const StepConst&
   k_trace_tile<D><<<(unsigned)(ngroup * ntile), TILE_W * 32, 0, st>>>(sg, s.Q, s.TM[D], s.TP[D], K, sw);
 }
 
-// the x tracing over the pencils and zones of sw: one warp per row segment of ROW_ZONES zones
+// the x tracing over the pencils and zones of sw: one warp per ROW_ZONES positions of the pencils laid end to end
 void launch_trace_row_x(const ScratchGeom& sg, const Scratch& s, const StepConst& K, const SweepRange& sw,
                         cudaStream_t st) {
-  const long long ntile = (sw.nd - sw.lod + ROW_ZONES) / ROW_ZONES;
-  const long long warps = ntile * sw.ext1 * sw.ext2;
+  const long long warps = row_warps(sw);
   k_trace_row_x<<<(unsigned)((warps + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, st>>>(sg, s.Q, s.TM[0], s.TP[0], K,
                                                                                        sw);
 }
