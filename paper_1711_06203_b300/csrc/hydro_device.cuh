@@ -224,7 +224,11 @@ __device__ __forceinline__ double add_i(double a, double b) {
 // multiply-adds, against about 5.7, 8.6 and 8.6 issue slots measured for the
 // IEEE operations; the results stay within 2 ulp (a GPU test bounds the error).
 // Arguments outside [2^-959, 2^960], zero, negative or non-finite take the
-// IEEE path.
+// IEEE path.  Both refinements are the truncated-series (higher-order
+// Newton-Raphson) corrections of an approximate reciprocal and reciprocal
+// square root, as described for FMA hardware in J.-M. Muller et al.,
+// "Handbook of Floating-Point Arithmetic", 2nd ed. (Birkhaeuser, 2018), in its
+// treatment of division and square root by Newton-Raphson iterations.
 #ifdef HYDRO_IEEE_DIV_SQRT
 __device__ __forceinline__ double drcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
