@@ -843,7 +843,7 @@ def bench_serve(args, dev, zone_rate):
     Sedov, two-state; sides 32..256; 10-100 steps) arriving as a Poisson
     process at 0.7 x the measured plain capacity (requests/s), served by the
     continuous-batching server with state resident on the device, under the
-    scheduling policy --serve-policy (default: response ratio, 5 ms
+    scheduling policy --serve-policy (default: response ratio, 2.5 ms
     quantum).  Beside the latency percentiles: the slowdown of each request
     (its latency over its own steps' cost alone on the GPU, at the server's
     measured cost per zone), and the host time spent choosing sets and
@@ -1116,7 +1116,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200, help="served request prefix (0 skips the leg)")
     ap.add_argument("--serve-policy", choices=("ratio", "all"), default="ratio",
                     help="serving policy: response ratio within a quantum (default) or every request every iteration")
-    ap.add_argument("--serve-quantum-ms", type=float, default=5.0)
+    ap.add_argument("--serve-quantum-ms", type=float, default=2.5)
     ap.add_argument("--serve-plain-rate", type=float, default=4.35e8,
                     help="--serve-only: plain zone-updates/s that sets the arrival rate (0.7 x capacity)")
     ap.add_argument("--serve-only", action="store_true",

@@ -406,7 +406,7 @@ int serve_stats(serve_t* s, hydro_serve_stats_t* st);
  * reserve is the largest box's scratch plus what a quantum can hold.
  * HYDRO_SERVE_ALL: every admitted request steps every iteration (quantum_ms
  * ignored) and the reserve is the scratch of every admitted request.  The
- * default is HYDRO_SERVE_RESPONSE_RATIO with a 5 ms quantum.  Either way a
+ * default is HYDRO_SERVE_RESPONSE_RATIO with a 2.5 ms quantum.  Either way a
  * request's result does not depend on the policy or on the other requests. */
 int serve_set_policy(serve_t* s, int policy, double quantum_ms);
 /* Stop the scheduler (the step in flight completes), release everything;

@@ -563,7 +563,7 @@ class Server:
         if rc:
             raise HydroError(rc, "serve_cancel")
 
-    def serve_set_policy(self, policy, quantum_ms=5.0):
+    def serve_set_policy(self, policy, quantum_ms=2.5):
         """HYDRO_SERVE_ALL (0) or HYDRO_SERVE_RESPONSE_RATIO (1, the default) with
         its per-iteration quantum; only while the server is idle."""
         rc = self.L.serve_set_policy(self.h, int(policy), float(quantum_ms))

@@ -155,9 +155,10 @@ struct serve {
   double* dt_next_dev = nullptr;
   // scheduling
   int policy = HYDRO_SERVE_RESPONSE_RATIO;
-  // 5 ms (200-request prefix: p99 slowdown 59 against 78 at 10 ms and 42 at
-  // 2.5 ms, p50 and p99 latency within 2 % of each other, same throughput)
-  double quantum_ms = 5.0;
+  // 2.5 ms (200-request prefix at 0.7 x capacity, two runs each: p99
+  // slowdown 39 against 59 at 5 ms and 78 at 10 ms, p50 latency 4 % lower
+  // than at 5 ms, p99 latency and throughput the same within 1 %)
+  double quantum_ms = 2.5;
   double ms_per_unit = 2.1e-6;  // measured cost of a step per step_units (running average)
   // statistics
   long long iterations = 0, zone_updates = 0, admitted = 0, completed = 0, box_steps = 0;
