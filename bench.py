@@ -1117,7 +1117,7 @@ def main():
     ap.add_argument("--serve-policy", choices=("ratio", "all"), default="ratio",
                     help="serving policy: response ratio within a quantum (default) or every request every iteration")
     ap.add_argument("--serve-quantum-ms", type=float, default=2.5)
-    ap.add_argument("--serve-plain-rate", type=float, default=4.35e8,
+    ap.add_argument("--serve-plain-rate", type=float, default=5.6e8,
                     help="--serve-only: plain zone-updates/s that sets the arrival rate (0.7 x capacity)")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving leg (at the plain rate measured by a short Sedov run) and print it")
@@ -1126,6 +1126,8 @@ def main():
                     help="run only the method-of-lines leg at --n and print its JSON (for profiling)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched-level leg and print its JSON (for profiling)")
+    ap.add_argument("--sod-only", action="store_true",
+                    help="run only the 2-D Sod 64^2 leg and print its JSON (for profiling)")
     ap.add_argument("--moving-only", action="store_true",
                     help="run only the every-zone-moving 128^3 leg and print its JSON (for profiling)")
     ap.add_argument("--batch-profile", type=int, default=0, metavar="NBOX",
@@ -1145,7 +1147,7 @@ def main():
         with torch.cuda.device(dev):
             print(json.dumps(bench_serve(args, dev, args.serve_plain_rate)), flush=True)
         return 0
-    if args.mol_only or args.batch_only or args.moving_only:
+    if args.mol_only or args.batch_only or args.moving_only or args.sod_only:
         import torch
 
         dev = torch.device("cuda", 0)
@@ -1155,6 +1157,8 @@ def main():
                 leg = bench_mol(args, dev, stream, cpu_sample=False)
             elif args.batch_only:
                 leg = bench_batch(args, dev, stream)
+            elif args.sod_only:
+                leg = bench_sod(args, dev, stream)
             else:
                 leg = bench_moving(args, dev, stream)
             print(json.dumps(leg), flush=True)
